@@ -1,0 +1,445 @@
+"""Pins of the CPU oracle against facts fixed outside it: published known-answer vectors,
+hand-worked sequences of Alg. 2 and Alg. 3, exact integer arithmetic, error bounds, brute force
+on tiny inputs, the history-independence theorem (Sec. 3) and the invariants of Alg. 5."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U = 2.0 ** -24  # binary32 unit roundoff
+
+
+# --------------------------------------------------------------------------------------------
+# Philox4x32-10: the published known-answer vectors
+# --------------------------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(x, 16) for x in r]
+        out = oracle.philox4x32_10(w[0:4], w[4:6])
+        assert out.tolist() == w[6:10]
+
+
+# --------------------------------------------------------------------------------------------
+# Dissimilarity (Sec. 2): exact for bytes, within the binary32 error bound for floats
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", [synth.U8, synth.I8])
+def test_dissimilarity_bytes_exact(dtype):
+    X = synth.uniform_points(300, 128, dtype, seed=11)
+    a = np.arange(300) % 300
+    b = (np.arange(300) * 7 + 3) % 300
+    got = oracle.dissimilarity(X, a, b)
+    ref = ((X[a].astype(np.int64) - X[b].astype(np.int64)) ** 2).sum(1)
+    assert np.array_equal(got, ref.astype(np.float64))
+
+
+@pytest.mark.parametrize("metric", [synth.L2, synth.IP])
+def test_dissimilarity_float_within_bound(metric):
+    X = synth.mixture(400, 96, synth.F32, 10, 0.3, seed=12, normalize=(metric == synth.IP))
+    a = np.arange(400)
+    b = (a * 13 + 5) % 400
+    got = oracle.dissimilarity(X, a, b, metric=metric)
+    x = X[a].astype(np.float64)
+    y = X[b].astype(np.float64)
+    d = X.shape[1]
+    if metric == synth.L2:
+        ref = ((x - y) ** 2).sum(1)
+        bound = (d + 3) * U * ref
+    else:
+        dot = (x * y).sum(1)
+        ref = 1.0 - dot
+        bound = (d + 1) * U * np.abs(x * y).sum(1) + U * np.abs(ref) + 1e-12
+    assert np.all(np.abs(got - ref) <= bound)
+    # the double-precision reference path agrees with numpy to rounding
+    f64 = oracle.dissimilarity(X, a, b, metric=metric, f64=True)
+    assert np.allclose(f64, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_dissimilarity_integer_valued_floats_exact():
+    # small integers in binary32: every product and partial sum is exact, so d_def is the exact sum
+    X = synth.uniform_points(200, 128, synth.I8, seed=13).astype(np.float32)
+    a = np.arange(200)
+    b = (a * 3 + 1) % 200
+    got = oracle.dissimilarity(X, a, b)
+    ref = ((X[a].astype(np.int64) - X[b].astype(np.int64)) ** 2).sum(1)
+    assert np.array_equal(got, ref.astype(np.float64))
+
+
+# --------------------------------------------------------------------------------------------
+# Sketches and the residualised hash (Sec. 3, Eq. 1)
+# --------------------------------------------------------------------------------------------
+def test_sketch_and_hash_bits():
+    X = synth.mixture(500, 128, synth.F32, 10, 0.3, seed=14)
+    H = synth.hyperplanes(12, 128, seed=3)
+    S, nrm = oracle.sketch(X, H)
+    ref = X.astype(np.float64) @ H.astype(np.float64).T
+    scale = np.abs(X.astype(np.float64)) @ np.abs(H.astype(np.float64)).T
+    assert np.all(np.abs(S - ref) <= 130 * U * scale + 1e-30)
+    assert np.allclose(nrm, (X.astype(np.float64) ** 2).sum(1), rtol=1e-12)
+    # bit i of h_p(c) is the sign of H_i . (c - p); where the exact margin exceeds the sketches'
+    # error the oracle's bits must agree with it
+    rng = np.random.default_rng(0)
+    p = rng.integers(0, 500, 2000)
+    c = rng.integers(0, 500, 2000)
+    margin = (X[c].astype(np.float64) - X[p].astype(np.float64)) @ H.astype(np.float64).T
+    err = 2 * 130 * U * (scale[c] + scale[p])
+    bits = (S[c] >= S[p])
+    sure = np.abs(margin) > err
+    assert sure.mean() > 0.99
+    assert np.array_equal(bits[sure], (margin >= 0)[sure])
+
+
+def test_sketch_bytes_exact():
+    X = synth.uniform_points(100, 128, synth.U8, seed=15)
+    H = np.round(synth.hyperplanes(8, 128, seed=4) * 4).astype(np.float32)  # small integers
+    S, nrm = oracle.sketch(X, H)
+    ref = X.astype(np.int64) @ H.astype(np.int64).T
+    assert np.array_equal(S.astype(np.int64), ref)
+    assert np.array_equal(nrm, (X.astype(np.int64) ** 2).sum(1).astype(np.float64))
+
+
+def test_slot_packing_orders_by_bf16_distance_then_id():
+    # 1.0 is 0x3F80 in bf16; 1.00390625 is halfway to 0x3F81 and rounds to even (0x3F80);
+    # 1.01171875 is halfway between 0x3F81 and 0x3F82 and rounds to even (0x3F82).
+    s = oracle.slot(1.0, 5, 3)
+    assert s >> 48 == (0x3F80 | 0x8000)
+    assert (s >> 16) & 0xFFFFFFFF == 5 and s & 0xFFFF == 3
+    assert oracle.slot(1.00390625, 0, 0) >> 48 == (0x3F80 | 0x8000)
+    assert oracle.slot(1.01171875, 0, 0) >> 48 == (0x3F82 | 0x8000)
+    assert oracle.slot(-2.0, 0, 0) >> 48 == (~0xC000) & 0xFFFF
+    vals = np.sort(np.random.default_rng(1).normal(0, 100, 500).astype(np.float32))
+    keys = [oracle.slot(float(v), 7, 0) for v in vals]
+    assert keys == sorted(keys)
+    assert oracle.slot(2.0, 3, 9) < oracle.slot(2.0, 4, 0)
+
+
+# --------------------------------------------------------------------------------------------
+# HashPrune (Alg. 3): hand-worked sequences, permutation invariance, closed form
+# --------------------------------------------------------------------------------------------
+def _load_hashprune_cases():
+    cases, cur = [], None
+    for line in open(os.path.join(GOLDEN, "hashprune_worked.txt")):
+        t = line.split()
+        if not t or t[0].startswith("#"):
+            continue
+        if t[0] == "case":
+            cur = dict(name=t[1], l_max=int(t[2]), m=int(t[3]), ins=[], expect=None)
+            cases.append(cur)
+        elif t[0] == "ins":
+            cur["ins"].append((int(t[1]), float(t[2]), int(t[3])))
+        elif t[0] == "expect":
+            cur["expect"] = [int(x) for x in t[1:]]
+    return cases
+
+
+def _case_stream(case):
+    ids = [c[0] for c in case["ins"]]
+    n = max(ids) + 1
+    m = case["m"]
+    S = np.zeros((n, m), dtype=np.float32)
+    for ident, _, h in case["ins"]:
+        if ident != 0:
+            S[ident] = [1.0 if (h >> i) & 1 else -1.0 for i in range(m)]
+    dst = np.zeros(len(ids), np.uint32)
+    src = np.array(ids, np.uint32)
+    dist = np.array([c[1] for c in case["ins"]], np.float32)
+    return dst, src, dist, S, n
+
+
+@pytest.mark.parametrize("case", _load_hashprune_cases(), ids=lambda c: c["name"])
+def test_hashprune_worked_sequences(case):
+    dst, src, dist, S, n = _case_stream(case)
+    for fn in (oracle.hashprune_stream, oracle.hashprune_closed):
+        res, cnt = fn(dst, src, dist, S, n, case["l_max"])
+        got = [int(s >> np.uint64(16)) & 0xFFFFFFFF for s in res[0, :cnt[0]]]
+        assert got == case["expect"], fn.__name__
+    # history independence (Sec. 3 theorem): every insertion order gives the same reservoir
+    for perm in itertools.permutations(range(len(src))):
+        p = np.array(perm)
+        res, cnt = oracle.hashprune_stream(dst[p], src[p], dist[p], S, n, case["l_max"])
+        got = [int(s >> np.uint64(16)) & 0xFFFFFFFF for s in res[0, :cnt[0]]]
+        assert got == case["expect"]
+
+
+def _random_stream(rng, n, count, m, spread=4.0):
+    dst = rng.integers(0, n, count).astype(np.uint32)
+    src = rng.integers(0, n, count).astype(np.uint32)
+    # a candidate's distance is a function of the (dst, src) pair, as in the build
+    key = (dst.astype(np.uint64) * np.uint64(1000003) + src.astype(np.uint64)) % np.uint64(977)
+    dist = (key.astype(np.float32) / np.float32(977.0) * np.float32(spread)).astype(np.float32)
+    S = rng.standard_normal((n, m)).astype(np.float32)
+    return dst, src, dist, S
+
+
+@pytest.mark.parametrize("m,l_max", [(3, 4), (6, 16), (12, 64)])
+def test_hashprune_stream_equals_closed_form_and_merges(m, l_max):
+    rng = np.random.default_rng(m * 100 + l_max)
+    n = 60
+    dst, src, dist, S = _random_stream(rng, n, 6000, m)
+    r1, c1 = oracle.hashprune_stream(dst, src, dist, S, n, l_max)
+    r2, c2 = oracle.hashprune_closed(dst, src, dist, S, n, l_max)
+    assert np.array_equal(c1, c2) and np.array_equal(r1, r2)
+    # reservoir bound: min(l_max, number of distinct buckets among non-self candidates)
+    for v in range(n):
+        sel = (dst == v) & (src != v)
+        hs = {int(sum(1 << i for i in range(m) if S[s, i] >= S[v, i])) for s in src[sel]}
+        assert c1[v] == min(l_max, len(hs))
+    # associativity: streaming a second batch into the first batch's reservoirs equals the
+    # closed form of the union, for random splits
+    for split in (1, 1500, 3000, 5999):
+        ra, ca = oracle.hashprune_stream(dst[:split], src[:split], dist[:split], S, n, l_max)
+        rb, cb = oracle.hashprune_stream(dst[split:], src[split:], dist[split:], S, n, l_max,
+                                         res=ra, cnt=ca)
+        assert np.array_equal(cb, c2) and np.array_equal(rb, r2)
+
+
+# --------------------------------------------------------------------------------------------
+# RobustPrune (Alg. 2): hand-worked example, standard == lazy, alpha -> infinity
+# --------------------------------------------------------------------------------------------
+def test_robustprune_worked_example():
+    pts, cases = {}, []
+    for line in open(os.path.join(GOLDEN, "robustprune_worked.txt")):
+        t = line.split()
+        if not t or t[0].startswith("#"):
+            continue
+        if t[0] == "point":
+            pts[int(t[1])] = (float(t[2]), float(t[3]))
+        else:
+            cases.append((float(t[1]), int(t[2]), [int(x) for x in t[3:]]))
+    X = np.array([pts[i] for i in range(len(pts))], np.float32)
+    n = len(pts)
+    l_max = 8
+    res = np.full((n, l_max), np.uint64(~np.uint64(0)), np.uint64)
+    cnt = np.zeros(n, np.uint32)
+    for t, c in enumerate(range(1, n)):
+        res[0, t] = oracle.slot(0.0, c, 0)
+    cnt[0] = n - 1
+    for alpha, R, want in cases:
+        for lazy in (False, True):
+            adj, deg = oracle.final_prune(X, res, cnt, R, alpha, lazy=lazy)
+            assert adj[0, :deg[0]].tolist() == want
+            assert np.all(adj[0, deg[0]:] == 0xFFFFFFFF)
+
+
+def _random_reservoirs(X, n, l_max, rng):
+    res = np.full((n, l_max), np.uint64(~np.uint64(0)), np.uint64)
+    cnt = np.zeros(n, np.uint32)
+    for v in range(n):
+        c = rng.integers(0, l_max + 1)
+        ids = rng.choice(np.delete(np.arange(n), v), size=c, replace=False)
+        for t, i in enumerate(ids):
+            res[v, t] = oracle.slot(0.0, int(i), 0)
+        cnt[v] = c
+    return res, cnt
+
+
+@pytest.mark.parametrize("dtype", [synth.F32, synth.U8])
+def test_robustprune_standard_equals_lazy(dtype):
+    rng = np.random.default_rng(5)
+    n, l_max = 300, 48
+    X = (synth.mixture(n, 32, synth.F32, 5, 0.5, seed=16) if dtype == synth.F32
+         else synth.uniform_points(n, 32, synth.U8, seed=16))
+    res, cnt = _random_reservoirs(X, n, l_max, rng)
+    for alpha, R in ((1.0, 16), (1.2, 32), (1.5, 48)):
+        a1, d1 = oracle.final_prune(X, res, cnt, R, alpha, lazy=False)
+        a2, d2 = oracle.final_prune(X, res, cnt, R, alpha, lazy=True)
+        assert np.array_equal(a1, a2) and np.array_equal(d1, d2)
+        assert np.all(d1 <= R)
+        for v in range(n):
+            got = set(a1[v, :d1[v]].tolist())
+            assert v not in got
+            assert got <= {int(s >> np.uint64(16)) & 0xFFFFFFFF for s in res[v, :cnt[v]]}
+
+
+def test_robustprune_large_alpha_keeps_R_nearest():
+    rng = np.random.default_rng(6)
+    n, l_max, R = 200, 32, 10
+    X = synth.uniform_points(n, 16, synth.U8, seed=17)
+    res, cnt = _random_reservoirs(X, n, l_max, rng)
+    adj, deg = oracle.final_prune(X, res, cnt, R, 1e18)
+    for v in range(n):
+        ids = np.array([int(s >> np.uint64(16)) & 0xFFFFFFFF for s in res[v, :cnt[v]]], np.int64)
+        dd = ((X[ids].astype(np.int64) - X[v].astype(np.int64)) ** 2).sum(1)
+        # duplicates at distance 0 from an admitted neighbour are the only thing alpha cannot keep
+        order = np.lexsort((ids, dd))
+        if np.unique(X[ids], axis=0).shape[0] == len(ids):
+            assert adj[v, :deg[v]].tolist() == ids[order][:R].tolist()
+
+
+# --------------------------------------------------------------------------------------------
+# Pick (Sec. 4.2): brute-force k-NN inside leaves
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_leaf_pick_brute_force(k):
+    X = synth.uniform_points(400, 24, synth.U8, lo=0, hi=6, seed=18)  # many exact ties
+    rng = np.random.default_rng(k)
+    leaves = [rng.choice(400, size=s, replace=False) for s in (1, 2, 3, 50, 137)]
+    leaves.append(np.concatenate([leaves[3][:10], leaves[3][:10]]))  # repeated ids count once
+    off = np.cumsum([0] + [len(l) for l in leaves]).astype(np.uint32)
+    mem = np.concatenate(leaves).astype(np.uint32)
+    dst, src, dist = oracle.leaf_pick(X, off, mem, k=k)
+    got = sorted(zip(dst.tolist(), src.tolist(), dist.tolist()))
+    want = []
+    for l in leaves:
+        u = np.unique(l)
+        D = ((X[u][:, None, :].astype(np.int64) - X[u][None, :, :].astype(np.int64)) ** 2).sum(2)
+        for a in range(len(u)):
+            cand = [(D[a, b], u[b]) for b in range(len(u)) if b != a]
+            for dv, j in sorted(cand)[:k]:
+                want.append((int(u[a]), int(j), float(dv)))
+                want.append((int(j), int(u[a]), float(dv)))
+    assert got == sorted(want)
+
+
+# --------------------------------------------------------------------------------------------
+# Partition (Alg. 5): single leaf, invariants, brute-force level 0, determinism, guard
+# --------------------------------------------------------------------------------------------
+def _leaf_sets(off, mem):
+    return sorted(tuple(sorted(mem[off[b]:off[b + 1]].tolist())) for b in range(len(off) - 1))
+
+
+def test_partition_single_leaf_and_exact_knn_graph():
+    X = synth.uniform_points(700, 32, synth.U8, seed=19)
+    bp = oracle.params(c_max=1024, l_max=32, R=32, fanout=(10, 3))
+    off, mem, _ = oracle.partition(X, bp, seed=1)
+    assert len(off) == 2 and sorted(mem.tolist()) == list(range(700))
+    # one leaf: the candidates are the exact bi-directed 2-NN graph
+    dst, src, dist = oracle.leaf_pick(X, off, mem, k=2)
+    D = ((X[:, None, :].astype(np.int64) - X[None, :, :].astype(np.int64)) ** 2).sum(2)
+    np.fill_diagonal(D, np.iinfo(np.int64).max)
+    nn = np.lexsort((np.broadcast_to(np.arange(700), D.shape), D), axis=1)[:, :2]
+    want = set()
+    for i in range(700):
+        for j in nn[i]:
+            want.add((i, int(j)))
+            want.add((int(j), i))
+    assert {(int(a), int(b)) for a, b in zip(dst, src)} == want
+
+
+def _level0_reference(X, bp, seed):
+    """Level 0 of Alg. 5 computed independently: leaders are the l smallest (Philox priority, id)
+    under subproblem 0, every point joins its f nearest leaders (ties to the smaller id)."""
+    n = X.shape[0]
+    l = int(max(2, min(np.ceil(np.float64(np.float32(bp.p_samp)) * n), bp.max_leaders)))
+    prio = np.array([oracle.philox4x32_10([i, 0, 0, 0x1EAD], [seed & 0xFFFFFFFF, seed >> 32])[0]
+                     for i in range(n)], np.uint64)
+    leaders = np.lexsort((np.arange(n), prio))[:l]
+    f = min(bp.fanout[0], l)
+    D = ((X[:, None, :].astype(np.int64) - X[leaders][None, :, :].astype(np.int64)) ** 2).sum(2)
+    order = np.lexsort((np.broadcast_to(leaders, D.shape), D), axis=1)[:, :f]
+    buckets = [sorted(np.nonzero((order == r).any(1))[0].tolist()) for r in range(l)]
+    return leaders, buckets
+
+
+def test_partition_level0_matches_brute_force():
+    X = synth.mixture(3000, 16, synth.U8, 20, 10.0, seed=20)
+    bp = oracle.params(c_max=2900, c_min=0, p_samp=0.01, fanout=(3,), l_max=32, R=32)
+    off, mem, levels = oracle.partition(X, bp, seed=77)
+    leaders, buckets = _level0_reference(X, bp, 77)
+    assert len(leaders) == 30
+    want = sorted(tuple(b) for b in buckets if len(b) > 0)
+    assert all(len(b) <= 2900 for b in want)
+    assert _leaf_sets(off, mem) == want
+    # every point sits in exactly min(fanout, l) leaves
+    assert np.array_equal(np.bincount(mem, minlength=3000), np.full(3000, 3))
+
+
+@pytest.mark.parametrize("dtype,metric", [(synth.F32, synth.L2), (synth.U8, synth.L2),
+                                          (synth.F32, synth.IP)])
+def test_partition_invariants_and_determinism(dtype, metric):
+    X = synth.mixture(12000, 32, dtype, 30, 0.3 if dtype == synth.F32 else 10.0, seed=21,
+                      normalize=(metric == synth.IP))
+    bp = oracle.params(c_max=512, fanout=(4, 2), p_samp=0.01, l_max=32, R=32)
+    off, mem, levels = oracle.partition(X, bp, seed=5, metric=metric)
+    sizes = np.diff(off.astype(np.int64))
+    assert sizes.max() <= 512 and sizes.min() >= 1
+    assert levels >= 2
+    assert np.all(np.bincount(mem, minlength=12000) >= 1)
+    for b in range(len(off) - 1):
+        seg = mem[off[b]:off[b + 1]]
+        assert len(np.unique(seg)) == len(seg)
+    off2, mem2, _ = oracle.partition(X, bp, seed=5, metric=metric)
+    assert np.array_equal(off, off2) and np.array_equal(mem, mem2)
+    off3, mem3, _ = oracle.partition(X, bp, seed=6, metric=metric)
+    assert _leaf_sets(off, mem) != _leaf_sets(off3, mem3)
+
+
+def test_partition_merge_packs_small_buckets():
+    X = synth.mixture(5000, 16, synth.U8, 200, 10.0, seed=22)
+    bp = oracle.params(c_max=400, c_min=100, p_samp=0.02, fanout=(1,), l_max=32, R=32)
+    off, mem, _ = oracle.partition(X, bp, seed=3)
+    sizes = np.diff(off.astype(np.int64))
+    assert sizes.max() <= 400
+    # fanout 1 and no recursion beyond carving: every point lands in exactly one leaf
+    assert np.array_equal(np.sort(mem), np.arange(5000))
+    # small buckets were merged: fewer leaves than leaders, and few leaves below C_min
+    assert len(sizes) < 100
+    assert (sizes < 100).sum() <= 1 + len(sizes) // 4
+
+
+def test_partition_duplicates_guard():
+    X = np.zeros((5000, 8), np.uint8)
+    X[::7] = 3
+    bp = oracle.params(c_max=256, fanout=(3, 2), l_max=16, R=16)
+    off, mem, _ = oracle.partition(X, bp, seed=9)
+    sizes = np.diff(off.astype(np.int64))
+    assert sizes.max() <= 256
+    assert np.all(np.bincount(mem, minlength=5000) >= 1)
+
+
+# --------------------------------------------------------------------------------------------
+# End to end (Alg. 4): graph structure and quality
+# --------------------------------------------------------------------------------------------
+def test_build_graph_quality_and_structure():
+    X, Q = synth.mixture(8000, 32, synth.F32, 40, 0.3, seed=23, n_queries=200)
+    H = synth.hyperplanes(12, 32, seed=5)
+    bp = oracle.params(c_max=512, l_max=64, R=32, fanout=(10, 3))
+    adj, deg, st = oracle.build(X, bp, H, seed=42)
+    assert st["candidates"] <= 4 * st["leaf_members"]
+    assert deg.max() <= 32 and deg.min() >= 1
+    for v in range(0, 8000, 97):
+        nb = adj[v, :deg[v]]
+        assert v not in nb.tolist() and len(set(nb.tolist())) == len(nb)
+        assert np.all(adj[v, deg[v]:] == 0xFFFFFFFF)
+    gt = oracle.knn(X, Q, 10)
+    ids, _ = oracle.beam_search(X, adj, deg, Q, 64)
+    assert oracle.recall(ids, gt) >= 0.95
+    # without the final prune a node keeps its reservoir's nearest R entries
+    bp.final_prune = 0
+    adj2, deg2, _ = oracle.build(X, bp, H, seed=42)
+    assert deg2.max() <= 32
+    ids2, _ = oracle.beam_search(X, adj2, deg2, Q, 64)
+    assert oracle.recall(ids2, gt) >= 0.9
+
+
+def test_knn_and_beam_search_exact_on_complete_graph():
+    X, Q = synth.mixture(300, 8, synth.F32, 5, 0.5, seed=24, n_queries=20)
+    gt = oracle.knn(X, Q, 10)
+    D = ((Q[:, None, :].astype(np.float64) - X[None, :, :].astype(np.float64)) ** 2).sum(2)
+    assert np.array_equal(gt, np.argsort(D, axis=1, kind="stable")[:, :10])
+    # on the complete graph Alg. 1 with L >= 10 finds the exact neighbours after one expansion
+    R = 299
+    adj = np.array([[j for j in range(300) if j != i] for i in range(300)], np.uint32)
+    deg = np.full(300, R, np.uint32)
+    ids, _ = oracle.beam_search(X, adj, deg, Q, 16)
+    assert oracle.recall(ids, gt) == 1.0
+
+
+def test_invalid_parameters_rejected():
+    X = synth.uniform_points(100, 8, synth.U8, seed=25)
+    for kw in (dict(c_max=1), dict(hash_bits=17), dict(R=65, l_max=64), dict(leaf_k=0)):
+        bp = oracle.params(**{**dict(c_max=64, l_max=64, R=64), **kw})
+        with pytest.raises(RuntimeError):
+            oracle.partition(X, bp, seed=1) if "hash_bits" not in kw else \
+                oracle.build(X, bp, np.zeros((17, 8), np.float32), seed=1)
+    Xf = synth.uniform_points(100, 8, synth.F32, seed=25)
+    Xf[3, 2] = np.nan
+    with pytest.raises(RuntimeError):
+        oracle.partition(Xf, oracle.params(c_max=64), seed=1)
