@@ -380,26 +380,27 @@ static void partition_rec(part_ctx *C, uint32_t *P, uint64_t np, uint32_t depth,
     uint32_t f = fanout_at(bp, depth);
     if (f > l) f = (uint32_t)l;
 
-    /* every point joins the buckets of its f nearest leaders, ties to the smaller leader id */
+    /* every point joins the buckets of its f nearest leaders; equidistant leaders are taken in
+     * the order they were drawn (leader rank) */
     uint32_t *assign = (uint32_t *)malloc(np * f * sizeof(uint32_t));
     uint64_t *cnt = (uint64_t *)calloc(l, sizeof(uint64_t));
     if (!assign || !cnt) { free(lead); free(assign); free(cnt); L->err = 1; return; }
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < (int64_t)np; i++) {
         double bd[64];
-        uint32_t br[64], bid[64];
+        uint32_t br[64];
         uint32_t have = 0;
         const void *x = row(C->X, P[i], C->d, C->dtype);
         for (uint64_t r = 0; r < l; r++) {
             double dv = dis_vec(x, row(C->X, lead[r], C->d, C->dtype), C->d, C->dtype, C->metric);
-            uint32_t lid = lead[r];
-            if (have == f && (dv > bd[f - 1] || (dv == bd[f - 1] && lid > bid[f - 1]))) continue;
+            /* ranks arrive in increasing order, so an equal distance never displaces */
+            if (have == f && dv >= bd[f - 1]) continue;
             uint32_t pos = have < f ? have++ : f - 1;
-            while (pos > 0 && (dv < bd[pos - 1] || (dv == bd[pos - 1] && lid < bid[pos - 1]))) {
-                bd[pos] = bd[pos - 1]; br[pos] = br[pos - 1]; bid[pos] = bid[pos - 1];
+            while (pos > 0 && dv < bd[pos - 1]) {
+                bd[pos] = bd[pos - 1]; br[pos] = br[pos - 1];
                 pos--;
             }
-            bd[pos] = dv; br[pos] = (uint32_t)r; bid[pos] = lid;
+            bd[pos] = dv; br[pos] = (uint32_t)r;
         }
         for (uint32_t j = 0; j < f; j++) assign[(uint64_t)i * f + j] = br[j];
     }

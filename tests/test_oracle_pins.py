@@ -325,7 +325,7 @@ def test_partition_single_leaf_and_exact_knn_graph():
 
 def _level0_reference(X, bp, seed):
     """Level 0 of Alg. 5 computed independently: leaders are the l smallest (Philox priority, id)
-    under subproblem 0, every point joins its f nearest leaders (ties to the smaller id)."""
+    under subproblem 0, every point joins its f nearest leaders (ties to the earlier-drawn one)."""
     n = X.shape[0]
     l = int(max(2, min(np.ceil(np.float64(np.float32(bp.p_samp)) * n), bp.max_leaders)))
     prio = np.array([oracle.philox4x32_10([i, 0, 0, 0x1EAD], [seed & 0xFFFFFFFF, seed >> 32])[0]
@@ -333,7 +333,7 @@ def _level0_reference(X, bp, seed):
     leaders = np.lexsort((np.arange(n), prio))[:l]
     f = min(bp.fanout[0], l)
     D = ((X[:, None, :].astype(np.int64) - X[leaders][None, :, :].astype(np.int64)) ** 2).sum(2)
-    order = np.lexsort((np.broadcast_to(leaders, D.shape), D), axis=1)[:, :f]
+    order = np.argsort(D, axis=1, kind="stable")[:, :f]
     buckets = [sorted(np.nonzero((order == r).any(1))[0].tolist()) for r in range(l)]
     return leaders, buckets
 
