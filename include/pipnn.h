@@ -1,0 +1,189 @@
+/*
+ * pipnn.h -- C ABI of the GB300 (sm_103a) PiPNN index-build library.
+ *
+ * PiPNN (Pick-in-Partitions Nearest Neighbors, arXiv 2602.21247) builds a graph index for
+ * approximate nearest-neighbour search without beam search (Alg. 4):
+ *   A0  sketches:   Sketch(v) = [v . H_i] for the m random hyperplanes of Sec. 3
+ *   A1  partition:  randomized ball carving with multi-level fanout and Merge (Alg. 5)
+ *   A2-A4 pick:     all-pairs dissimilarities inside every leaf and the bi-directed k-NN
+ *                   candidate edges (Sec. 4.2, App. A.3)
+ *   A5  HashPrune:  candidates streamed into per-node reservoirs of at most l_max slots (Alg. 3)
+ *   A6  prune:      RobustPrune of every reservoir down to degree R (Alg. 2, Sec. 4.3)
+ *
+ * Conventions for every entry point:
+ *  - Status: 0 on success, a negative PIPNN_E* code otherwise; pipnn_last_error() returns a
+ *    message for the calling thread's last failure.  A failed call writes no partial output
+ *    object (graph, leaves, edges) and frees everything it allocated.
+ *  - Pointers are device pointers unless the entry point says "host or device"; those accept
+ *    either and detect which with cudaPointerGetAttributes.  Inputs are read only and remain
+ *    owned by the caller.
+ *  - Work is issued on the stream set by pipnn_set_stream (default: the legacy default stream)
+ *    on the current CUDA device.  Entry points return after their results are complete (they
+ *    synchronise that stream).
+ *  - Points are n rows of d elements, row-major and contiguous, of type PIPNN_F32 (float),
+ *    PIPNN_U8 (uint8) or PIPNN_I8 (int8).  n < 2^32 - 1 (point ids are 32-bit).
+ *  - Dissimilarity (Sec. 2): PIPNN_L2 is the squared Euclidean distance, PIPNN_IP is
+ *    1 - <x, y> (for unit-norm data half the squared distance; float data only).  For float
+ *    data every decision (leader choice, pick, prune) uses the binary32 value accumulated with
+ *    one fused multiply-add per coordinate in index order; for byte data the exact integer.
+ *  - Library-owned outputs live in device memory allocated from the stream-ordered pool and are
+ *    released by the matching *_free call.
+ */
+#ifndef PIPNN_H
+#define PIPNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIPNN_OK 0
+#define PIPNN_EINVAL (-1)      /* invalid argument or parameter (message says which)         */
+#define PIPNN_ENOMEM (-2)      /* device or host allocation failed                            */
+#define PIPNN_ECUDA (-3)       /* a CUDA runtime call or kernel launch failed                 */
+#define PIPNN_ETIMEOUT (-4)    /* a bounded device-side wait gave up                          */
+#define PIPNN_EUNSUPPORTED (-5)/* valid but unsupported combination (e.g. IP on byte data)    */
+
+enum { PIPNN_F32 = 0, PIPNN_U8 = 1, PIPNN_I8 = 2 };
+enum { PIPNN_L2 = 0, PIPNN_IP = 1 };
+
+/* Engine of the leaf all-pairs step (A2).  Both give identical candidate edges.
+ *  PIPNN_LEAF_SIMT: CUDA-core arithmetic in the defining order (binary32 FMA chain / exact
+ *                   integer dot products).
+ *  PIPNN_LEAF_TC:   tcgen05 tensor-core Gram tiles with BF16 operands and FP32 accumulation in
+ *                   TMEM, dissimilarities formed in the epilogue (n_i + n_j - 2 G).  For byte
+ *                   data with d <= 256 every product and partial sum is an integer below 2^24,
+ *                   so the Gram is exact; float data is not supported by this engine. */
+enum { PIPNN_LEAF_SIMT = 0, PIPNN_LEAF_TC = 1 };
+
+/* Hyper-parameters BP of Alg. 4. */
+typedef struct pipnn_params {
+    uint32_t c_max;         /* Alg. 5: maximum leaf size C_max (>= 2)                           */
+    uint32_t c_min;         /* Alg. 5 Merge: buckets smaller than C_min are merged (<= C_max)   */
+    uint32_t max_leaders;   /* Sec. 4.1: cap on leaders per subproblem (2..1024)                */
+    float p_samp;           /* Sec. 4.1: leaders = max(2, min(ceil(p_samp*|P|), cap)), (0, 1]   */
+    uint32_t fanout[4];     /* Sec. 4.1 multi-level fanout: fanout at depth 0..3 (1..32)       */
+    uint32_t fanout_levels; /* number of valid fanout entries; deeper levels use fanout 1       */
+    uint32_t leaf_k;        /* App. A.3: k of the bi-directed k-NN pick (1..16)                 */
+    uint32_t hash_bits;     /* Sec. 3: m, number of hyperplanes / hash bits (1..16)             */
+    uint32_t l_max;         /* Alg. 3: reservoir capacity (1..256)                              */
+    uint32_t R;             /* Alg. 2: final degree bound (1..l_max)                            */
+    float alpha;            /* Alg. 2: pruning factor (>= 1), applied as alpha^2 on D           */
+    int32_t final_prune;    /* Alg. 4 BP.final_prune: 1 = RobustPrune every node, 0 = keep the
+                               first R reservoir entries in (distance, id) order               */
+    int32_t dtype;          /* PIPNN_F32 / PIPNN_U8 / PIPNN_I8                                  */
+    int32_t leaf_engine;    /* PIPNN_LEAF_SIMT / PIPNN_LEAF_TC                                  */
+    const float *hyperplanes; /* Sec. 3: the m x d random hyperplanes H (row i = H_i), float32,
+                                 host or device; required                                      */
+} pipnn_params;
+
+/* Output graph: ids[v*R + j] for j < deg[v] are v's out-neighbours in prune order; the rest of
+ * the row is 0xFFFFFFFF. */
+typedef struct pipnn_graph {
+    uint32_t *ids;
+    uint32_t *deg;
+    uint64_t n;
+    uint32_t R;
+    int32_t on_device;      /* 1: ids/deg are device memory; 0: pinned host memory              */
+} pipnn_graph;
+
+/* Leaves of the partition: leaf b holds members[offsets[b] .. offsets[b+1]). */
+typedef struct pipnn_leaves {
+    uint64_t *offsets;      /* num_leaves + 1 entries, device                                    */
+    uint32_t *members;      /* point ids, device                                                 */
+    uint64_t num_leaves;
+    uint64_t num_members;
+    uint32_t levels;        /* recursion levels of Alg. 5 that carved at least one subproblem   */
+} pipnn_leaves;
+
+/* Candidate edges: dst[e] receives src[e] at dissimilarity dist[e]. */
+typedef struct pipnn_edges {
+    uint32_t *dst;
+    uint32_t *src;
+    float *dist;            /* binary32 value of the dissimilarity (byte data: exact integer
+                               converted to binary32, round to nearest)                       */
+    uint64_t count;
+} pipnn_edges;
+
+/* Timings (CUDA events on the library stream) and counters of the last pipnn_build. */
+typedef struct pipnn_stats {
+    float ms_total, ms_sketch, ms_partition, ms_leaf, ms_hashprune, ms_prune;
+    float ms_leaf_kernel;        /* summed duration of the leaf all-pairs kernel launches       */
+    uint32_t leaf_kernel_launches;
+    uint32_t levels;
+    uint64_t leaves, leaf_members, candidates;
+    double leaf_pairs;           /* sum over leaves of |b| (|b| - 1), the unordered-pair work x2 */
+    double leaf_pairs_executed;  /* pairs the kernel evaluated (full tiles, both orders)        */
+} pipnn_stats;
+
+/* Sets the CUDA stream (a cudaStream_t, or NULL for the default stream) used by later calls. */
+int pipnn_set_stream(void *stream);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *pipnn_last_error(void);
+
+/* A0 -- sketches and squared norms (Sec. 3 "Implementation").
+ * points: n x d device; hyperplanes: m x d float32 device; sketch: n x m float32 device output,
+ * sketch[p*m + i] = sum_t x_t * H_i[t] as a binary32 FMA chain in index order; sqnorm: n
+ * entries device output (may be NULL): float32 FMA chain for float data, exact int32 for byte
+ * data (reinterpret the buffer).  Non-finite float input returns PIPNN_EINVAL. */
+int pipnn_sketch(const void *points, uint64_t n, uint32_t d, int32_t dtype, const float *hyperplanes,
+                 uint32_t m, float *sketch, void *sqnorm);
+
+/* A1 -- Alg. 5 randomized ball carving with multi-level fanout and Merge, seeded by `seed`
+ * (determinism lemma, App. A.5: the result is a function of the inputs and the seed).
+ * points: device.  On success *out holds library-owned device arrays; free with
+ * pipnn_leaves_free.  Leaves are listed in no particular order; members inside a leaf are in
+ * no particular order and distinct. */
+int pipnn_partition(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp,
+                    uint64_t seed, pipnn_leaves *out);
+void pipnn_leaves_free(pipnn_leaves *leaves);
+
+/* A2-A4 -- for every leaf (offsets/members as produced by pipnn_partition, device, distinct
+ * members), the k nearest other members of every member by (dissimilarity, id), emitted in both
+ * directions (Sec. 4.2, App. A.3): 2 * |b| * min(k, |b|-1) edges per leaf, in no particular
+ * order.  engine: PIPNN_LEAF_SIMT or PIPNN_LEAF_TC.  Free the result with pipnn_edges_free. */
+int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
+                    const uint64_t *offsets, const uint32_t *members, uint64_t num_leaves,
+                    uint32_t k, int32_t engine, pipnn_edges *out);
+void pipnn_edges_free(pipnn_edges *edges);
+
+/* A5 -- Alg. 3 HashPrune of a candidate stream into the reservoirs of n nodes.
+ * dst/src/dist: `count` candidates, device.  sketch: n x m float32 device (from pipnn_sketch).
+ * reservoir: n x l_max uint64 device, in/out; count_inout: n uint32 device, in/out (0 = empty).
+ * Slot layout: [ordered bf16(dist):16][src:32][h_dst(src):16]; unsigned order of slots is
+ * (distance, id).  h_p(c) bit i = [Sketch(c)_i >= Sketch(p)_i] (Eq. 1).  On return node v's
+ * slots are reservoir[v*l_max .. + count[v]) in ascending order, the rest 0xFF..FF.  By the
+ * history-independence theorem (Sec. 3) the result is the l_max smallest per-hash-bucket
+ * minima of the old reservoir together with the new candidates, whatever their order; calling
+ * twice on two halves of a stream equals one call on the whole.  Self candidates are dropped. */
+int pipnn_hashprune(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count,
+                    const float *sketch, uint32_t m, uint64_t n, uint32_t l_max, uint64_t *reservoir,
+                    uint32_t *count_inout);
+
+/* A6 -- Alg. 2 RobustPrune of every node's reservoir to at most R neighbours (Sec. 4.3).
+ * Candidates are ordered by (dissimilarity to the node, id); candidate z is removed by the
+ * admitted y when alpha^2 * D(y,z) < D(x,z), evaluated in binary32 with
+ * alpha^2 = (float)((double)alpha * alpha).  points, reservoir (n x l_max), count, adj (n x R)
+ * and deg (n) are device pointers. */
+int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
+                      const uint64_t *reservoir, const uint32_t *count, uint32_t l_max, uint32_t R,
+                      float alpha, uint32_t *adj, uint32_t *deg);
+
+/* Alg. 4 end to end: A0 .. A6 on the GPU.  points: host or device (host input is copied to the
+ * device inside the call).  graph_on_host = 1 returns the graph in pinned host memory, 0 in
+ * device memory.  Free with pipnn_free. */
+int pipnn_build(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp,
+                uint64_t seed, int32_t graph_on_host, pipnn_graph *out);
+void pipnn_free(pipnn_graph *graph);
+
+/* Statistics of the last successful pipnn_build on the calling thread. */
+int pipnn_get_stats(pipnn_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIPNN_H */

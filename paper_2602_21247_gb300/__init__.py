@@ -1,0 +1,273 @@
+"""GB300 (sm_103a) PiPNN index build: thin ctypes binding of libpipnn.so (include/pipnn.h).
+
+The binding only marshals arguments: torch tensors in device memory are passed as raw pointers,
+library-owned outputs are copied into torch tensors.  Every step of the path runs in the CUDA
+library; if it has not been built, importing works but every call raises.
+
+Entry points (same names as the C ABI):
+  pipnn_sketch       A0  sketches and squared norms (Sec. 3 "Implementation")
+  pipnn_partition    A1  Alg. 5 randomized ball carving with multi-level fanout and Merge
+  pipnn_leaf_pick    A2-A4 in-leaf all pairs + bi-directed k-NN candidates (Sec. 4.2)
+  pipnn_hashprune    A5  Alg. 3 HashPrune batch merge into reservoirs
+  pipnn_final_prune  A6  Alg. 2 RobustPrune to degree R (Sec. 4.3)
+  pipnn_build        Alg. 4 end to end (host or device input)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpipnn.so")
+
+PIPNN_F32, PIPNN_U8, PIPNN_I8 = 0, 1, 2
+PIPNN_L2, PIPNN_IP = 0, 1
+PIPNN_LEAF_SIMT, PIPNN_LEAF_TC = 0, 1
+PIPNN_OK = 0
+
+# symbols declared in include/pipnn.h
+EXPORTS = ("pipnn_set_stream", "pipnn_last_error", "pipnn_sketch", "pipnn_partition", "pipnn_leaves_free",
+           "pipnn_leaf_pick", "pipnn_edges_free", "pipnn_hashprune", "pipnn_final_prune", "pipnn_build",
+           "pipnn_free", "pipnn_get_stats")
+
+
+class PipnnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pipnn error {code}: {msg}")
+        self.code = code
+
+
+class pipnn_params(C.Structure):
+    _fields_ = [("c_max", C.c_uint32), ("c_min", C.c_uint32), ("max_leaders", C.c_uint32),
+                ("p_samp", C.c_float), ("fanout", C.c_uint32 * 4), ("fanout_levels", C.c_uint32),
+                ("leaf_k", C.c_uint32), ("hash_bits", C.c_uint32), ("l_max", C.c_uint32),
+                ("R", C.c_uint32), ("alpha", C.c_float), ("final_prune", C.c_int32),
+                ("dtype", C.c_int32), ("leaf_engine", C.c_int32), ("hyperplanes", C.c_void_p)]
+
+
+class pipnn_graph(C.Structure):
+    _fields_ = [("ids", C.c_void_p), ("deg", C.c_void_p), ("n", C.c_uint64), ("R", C.c_uint32),
+                ("on_device", C.c_int32)]
+
+
+class pipnn_leaves(C.Structure):
+    _fields_ = [("offsets", C.c_void_p), ("members", C.c_void_p), ("num_leaves", C.c_uint64),
+                ("num_members", C.c_uint64), ("levels", C.c_uint32)]
+
+
+class pipnn_edges(C.Structure):
+    _fields_ = [("dst", C.c_void_p), ("src", C.c_void_p), ("dist", C.c_void_p), ("count", C.c_uint64)]
+
+
+class pipnn_stats(C.Structure):
+    _fields_ = [("ms_total", C.c_float), ("ms_sketch", C.c_float), ("ms_partition", C.c_float),
+                ("ms_leaf", C.c_float), ("ms_hashprune", C.c_float), ("ms_prune", C.c_float),
+                ("ms_leaf_kernel", C.c_float), ("leaf_kernel_launches", C.c_uint32), ("levels", C.c_uint32),
+                ("leaves", C.c_uint64), ("leaf_members", C.c_uint64), ("candidates", C.c_uint64),
+                ("leaf_pairs", C.c_double), ("leaf_pairs_executed", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        L = C.CDLL(LIB_PATH)
+        vp, u64, u32, i32, f32 = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int32, C.c_float
+        L.pipnn_set_stream.argtypes = [vp]
+        L.pipnn_last_error.restype = C.c_char_p
+        L.pipnn_sketch.argtypes = [vp, u64, u32, i32, vp, u32, vp, vp]
+        L.pipnn_partition.argtypes = [vp, u64, u32, i32, C.POINTER(pipnn_params), u64, C.POINTER(pipnn_leaves)]
+        L.pipnn_leaves_free.argtypes = [C.POINTER(pipnn_leaves)]
+        L.pipnn_leaves_free.restype = None
+        L.pipnn_leaf_pick.argtypes = [vp, u64, u32, i32, i32, vp, vp, u64, u32, i32, C.POINTER(pipnn_edges)]
+        L.pipnn_edges_free.argtypes = [C.POINTER(pipnn_edges)]
+        L.pipnn_edges_free.restype = None
+        L.pipnn_hashprune.argtypes = [vp, vp, vp, u64, vp, u32, u64, u32, vp, vp]
+        L.pipnn_final_prune.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, u32, f32, vp, vp]
+        L.pipnn_build.argtypes = [vp, u64, u32, i32, C.POINTER(pipnn_params), u64, i32, C.POINTER(pipnn_graph)]
+        L.pipnn_free.argtypes = [C.POINTER(pipnn_graph)]
+        L.pipnn_free.restype = None
+        L.pipnn_get_stats.argtypes = [C.POINTER(pipnn_stats)]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != PIPNN_OK:
+        raise PipnnError(rc, lib().pipnn_last_error().decode(errors="replace"))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def dtype_code(t) -> int:
+    dt = t.dtype
+    if dt in (torch.float32, np.float32):
+        return PIPNN_F32
+    if dt in (torch.uint8, np.uint8):
+        return PIPNN_U8
+    if dt in (torch.int8, np.int8):
+        return PIPNN_I8
+    raise TypeError(f"unsupported point dtype {dt}")
+
+
+class _DevView:
+    """Library-owned device memory seen through __cuda_array_interface__ (copied immediately)."""
+
+    def __init__(self, ptr, count, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr,
+                                         "data": (int(ptr or 0), False), "version": 3, "strides": None}
+
+
+def _take(ptr, count, typestr, view=None):
+    if count == 0:
+        t = torch.empty(0, dtype={"<i4": torch.int32, "<i8": torch.int64, "<f4": torch.float32}[typestr],
+                        device="cuda")
+    else:
+        t = torch.as_tensor(_DevView(ptr, count, typestr), device="cuda").clone()
+    return t.view(view) if view is not None else t
+
+
+def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.005, fanout=(2,), leaf_k=2,
+           hash_bits=12, l_max=64, R=64, alpha=1.2, final_prune=True, leaf_engine=PIPNN_LEAF_SIMT,
+           hyperplanes=None) -> pipnn_params:
+    """BP of Alg. 4.  `hyperplanes` (hash_bits x d float32, numpy or torch) must stay alive for the call."""
+    p = pipnn_params()
+    p.c_max = c_max
+    p.c_min = c_max // 16 if c_min is None else c_min
+    p.max_leaders = max_leaders
+    p.p_samp = p_samp
+    for i in range(4):
+        p.fanout[i] = fanout[i] if i < len(fanout) else 1
+    p.fanout_levels = len(fanout)
+    p.leaf_k = leaf_k
+    p.hash_bits = hash_bits
+    p.l_max = l_max
+    p.R = R
+    p.alpha = alpha
+    p.final_prune = 1 if final_prune else 0
+    p.dtype = dtype
+    p.leaf_engine = leaf_engine
+    p.hyperplanes = _ptr(hyperplanes)
+    p._keep = hyperplanes
+    return p
+
+
+def pipnn_set_stream(stream=None):
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().pipnn_set_stream(C.c_void_p(s)))
+
+
+def pipnn_last_error() -> str:
+    return lib().pipnn_last_error().decode(errors="replace")
+
+
+def pipnn_sketch(points: torch.Tensor, hyperplanes: torch.Tensor):
+    """A0: returns (sketch n x m float32, squared norms n: float32 for float data, int32 for bytes)."""
+    n, d = points.shape
+    m = hyperplanes.shape[0]
+    S = torch.empty((n, m), dtype=torch.float32, device=points.device)
+    nrm = torch.empty(n, dtype=torch.float32 if points.dtype == torch.float32 else torch.int32,
+                      device=points.device)
+    pipnn_set_stream()
+    _check(lib().pipnn_sketch(_ptr(points), n, d, dtype_code(points), _ptr(hyperplanes), m, _ptr(S), _ptr(nrm)))
+    return S, nrm
+
+
+def pipnn_partition(points: torch.Tensor, bp: pipnn_params, seed: int, metric=PIPNN_L2):
+    """A1: returns (offsets uint64 [L+1], members uint32, levels)."""
+    n, d = points.shape
+    out = pipnn_leaves()
+    pipnn_set_stream()
+    _check(lib().pipnn_partition(_ptr(points), n, d, metric, C.byref(bp), seed, C.byref(out)))
+    try:
+        off = _take(out.offsets, out.num_leaves + 1, "<i8", torch.uint64)
+        mem = _take(out.members, out.num_members, "<i4", torch.uint32)
+        levels = out.levels
+    finally:
+        lib().pipnn_leaves_free(C.byref(out))
+    return off, mem, levels
+
+
+def pipnn_leaf_pick(points: torch.Tensor, offsets: torch.Tensor, members: torch.Tensor, k=2, metric=PIPNN_L2,
+                    engine=PIPNN_LEAF_SIMT):
+    """A2-A4: returns (dst uint32, src uint32, dist float32) candidate edges."""
+    n, d = points.shape
+    out = pipnn_edges()
+    pipnn_set_stream()
+    _check(lib().pipnn_leaf_pick(_ptr(points), n, d, dtype_code(points), metric, _ptr(offsets), _ptr(members),
+                                 offsets.numel() - 1, k, engine, C.byref(out)))
+    try:
+        dst = _take(out.dst, out.count, "<i4", torch.uint32)
+        src = _take(out.src, out.count, "<i4", torch.uint32)
+        dist = _take(out.dist, out.count, "<f4")
+    finally:
+        lib().pipnn_edges_free(C.byref(out))
+    return dst, src, dist
+
+
+def pipnn_hashprune(dst, src, dist, sketch, n, l_max, reservoir=None, count=None):
+    """A5: merges the candidates into (reservoir n x l_max uint64, count n uint32), in place if given."""
+    m = sketch.shape[1]
+    dev = sketch.device
+    if reservoir is None:
+        reservoir = torch.full((n, l_max), -1, dtype=torch.int64, device=dev).view(torch.uint64)
+    if count is None:
+        count = torch.zeros(n, dtype=torch.int32, device=dev).view(torch.uint32)
+    pipnn_set_stream()
+    _check(lib().pipnn_hashprune(_ptr(dst), _ptr(src), _ptr(dist), dst.numel(), _ptr(sketch), m, n, l_max,
+                                 _ptr(reservoir), _ptr(count)))
+    return reservoir, count
+
+
+def pipnn_final_prune(points, reservoir, count, R, alpha, metric=PIPNN_L2):
+    """A6: returns (adjacency n x R uint32 padded with 0xFFFFFFFF, degree n uint32)."""
+    n, d = points.shape
+    l_max = reservoir.shape[1]
+    adj = torch.empty((n, R), dtype=torch.int32, device=points.device).view(torch.uint32)
+    deg = torch.empty(n, dtype=torch.int32, device=points.device).view(torch.uint32)
+    pipnn_set_stream()
+    _check(lib().pipnn_final_prune(_ptr(points), n, d, dtype_code(points), metric, _ptr(reservoir), _ptr(count),
+                                   l_max, R, alpha, _ptr(adj), _ptr(deg)))
+    return adj, deg
+
+
+def pipnn_build(points, bp: pipnn_params, seed: int, metric=PIPNN_L2, graph_on_host=False):
+    """Alg. 4 end to end.  points: torch tensor (cuda or cpu) or numpy array.  Returns
+    (adjacency n x R uint32, degree n uint32) as torch tensors on the device, or numpy arrays on
+    the host when graph_on_host is set."""
+    n, d = points.shape
+    bp.dtype = dtype_code(points)
+    g = pipnn_graph()
+    pipnn_set_stream()
+    _check(lib().pipnn_build(_ptr(points), n, d, metric, C.byref(bp), seed, 1 if graph_on_host else 0, C.byref(g)))
+    try:
+        R = g.R
+        if g.on_device:
+            adj = _take(g.ids, n * R, "<i4", torch.uint32).view(n, R)
+            deg = _take(g.deg, n, "<i4", torch.uint32)
+        else:
+            adj = np.ctypeslib.as_array((C.c_uint32 * (n * R)).from_address(g.ids)).reshape(n, R).copy()
+            deg = np.ctypeslib.as_array((C.c_uint32 * n).from_address(g.deg)).copy()
+    finally:
+        lib().pipnn_free(C.byref(g))
+    return adj, deg
+
+
+def pipnn_get_stats() -> dict:
+    st = pipnn_stats()
+    _check(lib().pipnn_get_stats(C.byref(st)))
+    return {name: getattr(st, name) for name, _ in pipnn_stats._fields_}

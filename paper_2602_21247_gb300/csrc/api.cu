@@ -1,0 +1,375 @@
+// api.cu -- the extern "C" entry points declared in include/pipnn.h: argument validation,
+// host/device input handling, the Alg. 4 pipeline (A0 .. A6) and per-phase timing.
+#include "internal.cuh"
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+namespace pipnn {
+void set_stream(cudaStream_t s);
+void set_device_error_word(unsigned *p);
+int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float *H, uint32_t m, float *S,
+                  void *sqnorm);
+int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
+                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out);
+int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
+              const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, pipnn_edges *out,
+              float *ms_kernel, uint32_t *launches);
+int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
+                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt);
+int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
+                const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, uint32_t *adj,
+                uint32_t *deg);
+int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, uint32_t *adj,
+                    uint32_t *deg);
+
+namespace {
+thread_local pipnn_stats g_stats;
+
+// Per-call device error word, installed for the duration of an entry point.
+struct CallScope {
+    Workspace ws;
+    unsigned *err = nullptr;
+    int init() {
+        clear_error();
+        PIPNN_TRY(ws.zeros(&err, 1));
+        set_device_error_word(err);
+        return PIPNN_OK;
+    }
+    ~CallScope() { set_device_error_word(nullptr); }
+};
+
+size_t elem_size(int dtype) { return dtype == PIPNN_F32 ? 4 : 1; }
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric) {
+    if (!X) return set_error(PIPNN_EINVAL, "points is NULL");
+    if (n == 0) return set_error(PIPNN_EINVAL, "n must be positive");
+    if (n >= 0xFFFFFFFFull) return set_error(PIPNN_EINVAL, "n must be below 2^32 - 1");
+    if (d == 0) return set_error(PIPNN_EINVAL, "d must be positive");
+    if (dtype < PIPNN_F32 || dtype > PIPNN_I8) return set_error(PIPNN_EINVAL, "unknown dtype %d", dtype);
+    if (metric != PIPNN_L2 && metric != PIPNN_IP) return set_error(PIPNN_EINVAL, "unknown metric %d", metric);
+    if (metric == PIPNN_IP && dtype != PIPNN_F32)
+        return set_error(PIPNN_EUNSUPPORTED, "inner product is supported for float data only");
+    // the CUDA-core all-pairs kernel keeps a 128-row tile resident in shared memory
+    const size_t dw = dtype == PIPNN_F32 ? d : (d + 3) / 4;
+    if ((128 + 32) * dw * 4 > 227 * 1024)
+        return set_error(PIPNN_EUNSUPPORTED, "d = %u exceeds the resident-tile limit", d);
+    return PIPNN_OK;
+}
+
+int check_params(const pipnn_params *bp) {
+    if (!bp) return set_error(PIPNN_EINVAL, "params is NULL");
+    if (bp->c_max < 2) return set_error(PIPNN_EINVAL, "c_max must be at least 2");
+    if (bp->c_min > bp->c_max) return set_error(PIPNN_EINVAL, "c_min must not exceed c_max");
+    if (bp->max_leaders < 2 || bp->max_leaders > 1024) return set_error(PIPNN_EINVAL, "max_leaders outside 2..1024");
+    if (!(bp->p_samp > 0.0f) || !(bp->p_samp <= 1.0f)) return set_error(PIPNN_EINVAL, "p_samp outside (0, 1]");
+    if (bp->fanout_levels > 4) return set_error(PIPNN_EINVAL, "fanout_levels above 4");
+    for (uint32_t i = 0; i < bp->fanout_levels; i++)
+        if (bp->fanout[i] < 1 || bp->fanout[i] > 32) return set_error(PIPNN_EINVAL, "fanout[%u] outside 1..32", i);
+    if (bp->leaf_k < 1 || bp->leaf_k > 16) return set_error(PIPNN_EINVAL, "leaf_k outside 1..16");
+    if (bp->hash_bits < 1 || bp->hash_bits > 16) return set_error(PIPNN_EINVAL, "hash_bits outside 1..16");
+    if (bp->l_max < 1 || bp->l_max > 256) return set_error(PIPNN_EINVAL, "l_max outside 1..256");
+    if (bp->R < 1 || bp->R > bp->l_max) return set_error(PIPNN_EINVAL, "R outside 1..l_max");
+    if (!(bp->alpha >= 1.0f) || !std::isfinite(bp->alpha)) return set_error(PIPNN_EINVAL, "alpha must be finite and >= 1");
+    if (bp->leaf_engine != PIPNN_LEAF_SIMT && bp->leaf_engine != PIPNN_LEAF_TC)
+        return set_error(PIPNN_EINVAL, "unknown leaf_engine %d", bp->leaf_engine);
+    if (!bp->hyperplanes) return set_error(PIPNN_EINVAL, "hyperplanes is NULL");
+    return PIPNN_OK;
+}
+
+struct Timer {
+    cudaEvent_t ev[8] = {};
+    int init() {
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return set_error(PIPNN_ECUDA, "event creation failed");
+        return PIPNN_OK;
+    }
+    void mark(int i) { cudaEventRecord(ev[i], stream()); }
+    float ms(int a, int b) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, ev[a], ev[b]) != cudaSuccess) cudaGetLastError();
+        return t;
+    }
+    ~Timer() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+__global__ void leaf_pairs_kernel(const uint64_t *off, uint64_t L, double *acc) {
+    double local = 0.0;
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < L; b += (uint64_t)gridDim.x * blockDim.x) {
+        double s = (double)(off[b + 1] - off[b]);
+        local += s * (s - 1.0);
+    }
+    atomicAdd(acc, local);
+}
+
+int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pipnn_params *bp, uint64_t seed,
+               int graph_on_host, pipnn_graph *out) {
+    memset(out, 0, sizeof(*out));
+    PIPNN_TRY(check_params(bp));
+    const int dtype = bp->dtype;
+    PIPNN_TRY(check_points(points, n, d, dtype, metric));
+    if (bp->leaf_engine == PIPNN_LEAF_TC && dtype == PIPNN_F32)
+        return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes byte data only");
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    Workspace &ws = cs.ws;
+    Timer tm;
+    PIPNN_TRY(tm.init());
+    pipnn_stats st;
+    memset(&st, 0, sizeof(st));
+    tm.mark(0);
+
+    // inputs on the device
+    const void *X = points;
+    if (!is_device_ptr(points)) {
+        void *dx = nullptr;
+        PIPNN_TRY(ws.alloc((char **)&dx, n * d * elem_size(dtype)));
+        PIPNN_CUDA(cudaMemcpyAsync(dx, points, n * d * elem_size(dtype), cudaMemcpyHostToDevice, stream()));
+        X = dx;
+    }
+    const uint32_t m = bp->hash_bits;
+    const float *H = bp->hyperplanes;
+    if (!is_device_ptr(H)) {
+        float *dh = nullptr;
+        PIPNN_TRY(ws.alloc(&dh, (size_t)m * d));
+        PIPNN_CUDA(cudaMemcpyAsync(dh, H, (size_t)m * d * 4, cudaMemcpyHostToDevice, stream()));
+        H = dh;
+    }
+
+    // A0
+    float *S;
+    int32_t *sqn;
+    PIPNN_TRY(ws.alloc(&S, n * m));
+    PIPNN_TRY(ws.alloc(&sqn, n));
+    PIPNN_TRY(sketch_points(X, n, d, dtype, H, m, S, sqn));
+    tm.mark(1);
+    const int32_t *sqn_bytes = dtype == PIPNN_F32 ? nullptr : sqn;
+
+    // A1
+    pipnn_leaves leaves;
+    PIPNN_TRY(partition_points(X, n, d, dtype, metric, sqn_bytes, bp, seed, &leaves));
+    tm.mark(2);
+    st.levels = leaves.levels;
+    st.leaves = leaves.num_leaves;
+    st.leaf_members = leaves.num_members;
+    {
+        double *acc;
+        PIPNN_TRY(ws.zeros(&acc, 1));
+        if (leaves.num_leaves) {
+            leaf_pairs_kernel<<<grid_for(leaves.num_leaves, 256, 1024), 256, 0, stream()>>>(leaves.offsets,
+                                                                                           leaves.num_leaves, acc);
+        }
+        PIPNN_CUDA(cudaMemcpyAsync(&st.leaf_pairs, acc, 8, cudaMemcpyDeviceToHost, stream()));
+    }
+
+    // A2 .. A4
+    pipnn_edges edges;
+    int rc = leaf_pick(X, n, d, dtype, metric, sqn_bytes, leaves.offsets, leaves.members, leaves.num_leaves,
+                       bp->leaf_k, bp->leaf_engine, &edges, &st.ms_leaf_kernel, &st.leaf_kernel_launches);
+    dev_free_raw(leaves.offsets);
+    dev_free_raw(leaves.members);
+    if (rc != PIPNN_OK) return rc;
+    tm.mark(3);
+    st.candidates = edges.count;
+
+    // A5
+    uint64_t *res;
+    uint32_t *cnt;
+    rc = ws.alloc(&res, n * bp->l_max);
+    if (rc == PIPNN_OK) rc = ws.zeros(&cnt, n);
+    if (rc == PIPNN_OK) {
+        cudaError_t e = cudaMemsetAsync(res, 0xFF, n * bp->l_max * 8, stream());
+        if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "memset: %s", cudaGetErrorString(e));
+    }
+    if (rc == PIPNN_OK) rc = hashprune_merge(edges.dst, edges.src, edges.dist, edges.count, S, m, n, bp->l_max, res, cnt);
+    dev_free_raw(edges.dst);
+    dev_free_raw(edges.src);
+    dev_free_raw(edges.dist);
+    if (rc != PIPNN_OK) return rc;
+    tm.mark(4);
+
+    // A6
+    uint32_t *adj = nullptr, *deg = nullptr;
+    PIPNN_TRY(dev_alloc_raw((void **)&adj, n * bp->R * 4));
+    rc = dev_alloc_raw((void **)&deg, n * 4);
+    if (rc == PIPNN_OK) {
+        if (bp->final_prune)
+            rc = final_prune(X, n, d, dtype, metric, sqn_bytes, res, cnt, bp->l_max, bp->R, bp->alpha, adj, deg);
+        else
+            rc = reservoir_graph(n, res, cnt, bp->l_max, bp->R, adj, deg);
+    }
+    if (rc == PIPNN_OK) rc = check_device_error("final prune");
+    tm.mark(5);
+    if (rc == PIPNN_OK && graph_on_host) {
+        uint32_t *hadj = nullptr, *hdeg = nullptr;
+        cudaError_t e = cudaMallocHost(&hadj, n * bp->R * 4);
+        if (e == cudaSuccess) e = cudaMallocHost(&hdeg, n * 4);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hadj, adj, n * bp->R * 4, cudaMemcpyDeviceToHost, stream());
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hdeg, deg, n * 4, cudaMemcpyDeviceToHost, stream());
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream());
+        dev_free_raw(adj);
+        dev_free_raw(deg);
+        adj = deg = nullptr;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (hadj) cudaFreeHost(hadj);
+            if (hdeg) cudaFreeHost(hdeg);
+            return set_error(PIPNN_ECUDA, "graph copy to host: %s", cudaGetErrorString(e));
+        }
+        out->ids = hadj;
+        out->deg = hdeg;
+        out->on_device = 0;
+    } else if (rc == PIPNN_OK) {
+        out->ids = adj;
+        out->deg = deg;
+        out->on_device = 1;
+    }
+    if (rc != PIPNN_OK) {
+        dev_free_raw(adj);
+        dev_free_raw(deg);
+        return rc;
+    }
+    out->n = n;
+    out->R = bp->R;
+    tm.mark(6);
+    cudaStreamSynchronize(stream());
+    st.ms_sketch = tm.ms(0, 1);
+    st.ms_partition = tm.ms(1, 2);
+    st.ms_leaf = tm.ms(2, 3);
+    st.ms_hashprune = tm.ms(3, 4);
+    st.ms_prune = tm.ms(4, 5);
+    st.ms_total = tm.ms(0, 6);
+    g_stats = st;
+    return PIPNN_OK;
+}
+}  // namespace
+}  // namespace pipnn
+
+using namespace pipnn;
+
+extern "C" {
+
+int pipnn_set_stream(void *s) {
+    set_stream(static_cast<cudaStream_t>(s));
+    return PIPNN_OK;
+}
+
+const char *pipnn_last_error(void) { return error_message(); }
+
+int pipnn_sketch(const void *points, uint64_t n, uint32_t d, int32_t dtype, const float *hyperplanes, uint32_t m,
+                 float *sketch, void *sqnorm) {
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    PIPNN_TRY(check_points(points, n, d, dtype, PIPNN_L2));
+    if (!hyperplanes || !sketch) return set_error(PIPNN_EINVAL, "hyperplanes and sketch are required");
+    if (m < 1 || m > 16) return set_error(PIPNN_EINVAL, "m outside 1..16");
+    PIPNN_TRY(sketch_points(points, n, d, dtype, hyperplanes, m, sketch, sqnorm));
+    return check_device_error("sketch");
+}
+
+int pipnn_partition(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp, uint64_t seed,
+                    pipnn_leaves *out) {
+    if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    PIPNN_TRY(check_params(bp));
+    PIPNN_TRY(check_points(points, n, d, bp->dtype, metric));
+    return partition_points(points, n, d, bp->dtype, metric, nullptr, bp, seed, out);
+}
+
+void pipnn_leaves_free(pipnn_leaves *l) {
+    if (!l) return;
+    dev_free_raw(l->offsets);
+    dev_free_raw(l->members);
+    cudaStreamSynchronize(stream());
+    memset(l, 0, sizeof(*l));
+}
+
+int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric, const uint64_t *offsets,
+                    const uint32_t *members, uint64_t num_leaves, uint32_t k, int32_t engine, pipnn_edges *out) {
+    if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
+    memset(out, 0, sizeof(*out));
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    PIPNN_TRY(check_points(points, n, d, dtype, metric));
+    if (!offsets || (!members && num_leaves)) return set_error(PIPNN_EINVAL, "offsets/members are NULL");
+    if (k < 1 || k > 16) return set_error(PIPNN_EINVAL, "k outside 1..16");
+    if (engine != PIPNN_LEAF_SIMT && engine != PIPNN_LEAF_TC) return set_error(PIPNN_EINVAL, "unknown engine");
+    if (engine == PIPNN_LEAF_TC && dtype == PIPNN_F32)
+        return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes byte data only");
+    return leaf_pick(points, n, d, dtype, metric, nullptr, offsets, members, num_leaves, k, engine, out, nullptr,
+                     nullptr);
+}
+
+void pipnn_edges_free(pipnn_edges *e) {
+    if (!e) return;
+    dev_free_raw(e->dst);
+    dev_free_raw(e->src);
+    dev_free_raw(e->dist);
+    cudaStreamSynchronize(stream());
+    memset(e, 0, sizeof(*e));
+}
+
+int pipnn_hashprune(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *sketch,
+                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *reservoir, uint32_t *count_inout) {
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    if (count && (!dst || !src || !dist)) return set_error(PIPNN_EINVAL, "candidate arrays are NULL");
+    if (!sketch || !reservoir || !count_inout) return set_error(PIPNN_EINVAL, "sketch/reservoir/count are NULL");
+    if (n == 0 || n >= 0xFFFFFFFFull) return set_error(PIPNN_EINVAL, "n outside 1..2^32-2");
+    return hashprune_merge(dst, src, dist, count, sketch, m, n, l_max, reservoir, count_inout);
+}
+
+int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
+                      const uint64_t *reservoir, const uint32_t *count, uint32_t l_max, uint32_t R, float alpha,
+                      uint32_t *adj, uint32_t *deg) {
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    PIPNN_TRY(check_points(points, n, d, dtype, metric));
+    if (!reservoir || !count || !adj || !deg) return set_error(PIPNN_EINVAL, "NULL array");
+    if (l_max < 1 || l_max > 256 || R < 1 || R > l_max) return set_error(PIPNN_EINVAL, "need 1 <= R <= l_max <= 256");
+    if (!(alpha >= 1.0f) || !std::isfinite(alpha)) return set_error(PIPNN_EINVAL, "alpha must be finite and >= 1");
+    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, adj, deg));
+    return check_device_error("final prune");
+}
+
+int pipnn_build(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp, uint64_t seed,
+                int32_t graph_on_host, pipnn_graph *out) {
+    if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
+    return build_impl(points, n, d, metric, bp, seed, graph_on_host, out);
+}
+
+void pipnn_free(pipnn_graph *g) {
+    if (!g) return;
+    if (g->on_device) {
+        dev_free_raw(g->ids);
+        dev_free_raw(g->deg);
+        cudaStreamSynchronize(stream());
+    } else {
+        if (g->ids) cudaFreeHost(g->ids);
+        if (g->deg) cudaFreeHost(g->deg);
+    }
+    memset(g, 0, sizeof(*g));
+}
+
+int pipnn_get_stats(pipnn_stats *out) {
+    if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
+    *out = g_stats;
+    return PIPNN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// hashprune.cu -- A5: Alg. 3 HashPrune as a batch merge.
+//
+// Alg. 3 is history independent (Sec. 3 theorem): a node's reservoir ends up holding the l_max
+// smallest per-hash-bucket minima of all its candidates, in whatever order they arrive.  The
+// same fact makes the reservoir of a prefix plus the rest of the stream merge to the reservoir
+// of the whole stream, so the GPU inserts a whole batch at once:
+//   1. count candidates per destination, prefix-sum, scatter each candidate's slot
+//      [ordered bf16 dist:16][src:32][h_dst(src):16] next to its destination's others;
+//   2. one warp per node sorts (old reservoir + new slots) in shared memory and walks them in
+//      ascending order, keeping a slot iff its hash bucket has not been seen yet
+//      (__match_any_sync within a chunk of 32, a bitmap of 2^m bits across chunks), until
+//      l_max are kept.  Batches larger than the shared buffer are merged chunk by chunk.
+#include "internal.cuh"
+
+namespace pipnn {
+
+namespace {
+constexpr int HP_WARPS = 8;
+constexpr int HP_BUF = 512;   // slots per warp buffer
+
+__global__ void hp_count(const uint32_t *dst, const uint32_t *src, uint64_t count, uint64_t n, uint64_t *per_node,
+                         unsigned *err) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < count; e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v = dst[e], c = src[e];
+        if (v >= n || c >= n) {
+            atomicOr(err, DERR_RANGE);
+            continue;
+        }
+        if (v != c) atomicAdd((unsigned long long *)&per_node[v], 1ull);
+    }
+}
+
+__global__ void hp_scatter(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, uint64_t n,
+                           const float *S, uint32_t m, const uint64_t *start, unsigned *fill, uint64_t *slots) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < count; e += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v = dst[e], c = src[e];
+        if (v >= n || c >= n || v == c) continue;
+        // residualised hash h_v(c): bit i = [Sketch(c)_i >= Sketch(v)_i]  (Eq. 1)
+        uint32_t h = 0;
+        const float *sv = S + (uint64_t)v * m, *sc = S + (uint64_t)c * m;
+        for (uint32_t i = 0; i < m; i++) h |= (__ldg(sc + i) >= __ldg(sv + i) ? 1u : 0u) << i;
+        uint32_t pos = atomicAdd(&fill[v], 1u);
+        slots[start[v] + pos] = reservoir_slot(dist[e], c, h);
+    }
+}
+
+__device__ __forceinline__ void warp_bitonic_sort(uint64_t *buf, uint32_t P, int lane) {
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = lane; i < P; i += 32) {
+                uint32_t ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t a = buf[i], b = buf[ixj];
+                    bool asc = (i & k) == 0;
+                    if ((a > b) == asc) {
+                        buf[i] = b;
+                        buf[ixj] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(HP_WARPS * 32) hp_merge(uint64_t n, uint32_t m, uint32_t l_max,
+                                                         const uint64_t *start, const uint64_t *slots,
+                                                         uint64_t *res, uint32_t *cnt) {
+    extern __shared__ __align__(16) unsigned char hp_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bm_words = m >= 5 ? (1u << (m - 5)) : 1u;
+    uint64_t *buf = reinterpret_cast<uint64_t *>(hp_smem) + (size_t)warp * HP_BUF;
+    uint32_t *seen = reinterpret_cast<uint32_t *>(hp_smem + (size_t)HP_WARPS * HP_BUF * 8) + (size_t)warp * bm_words;
+    for (uint32_t w = lane; w < bm_words; w += 32) seen[w] = 0;
+    __syncwarp();
+
+    for (uint64_t v = (uint64_t)blockIdx.x * HP_WARPS + warp; v < n; v += (uint64_t)gridDim.x * HP_WARPS) {
+        uint32_t cur = cnt[v];
+        if (cur > l_max) cur = l_max;
+        uint64_t a = start[v];
+        const uint64_t b = start[v + 1];
+        if (a == b) {
+            // no new candidates: the reservoir is unchanged (normalise the padding)
+            for (uint32_t t = cur + lane; t < l_max; t += 32) res[v * l_max + t] = ~0ull;
+            continue;
+        }
+        for (uint32_t t = lane; t < cur; t += 32) buf[t] = res[v * l_max + t];
+        while (a < b) {
+            uint32_t take = (uint32_t)((b - a) < (uint64_t)(HP_BUF - cur) ? (b - a) : (uint64_t)(HP_BUF - cur));
+            for (uint32_t t = lane; t < take; t += 32) buf[cur + t] = slots[a + t];
+            a += take;
+            const uint32_t nb = cur + take;
+            uint32_t P = 32;
+            while (P < nb) P <<= 1;
+            for (uint32_t t = nb + lane; t < P; t += 32) buf[t] = ~0ull;
+            __syncwarp();
+            warp_bitonic_sort(buf, P, lane);
+            // walk ascending, keep the first slot of every unseen hash bucket
+            uint32_t out = 0;
+            for (uint32_t base = 0; base < nb && out < l_max; base += 32) {
+                const uint32_t i = base + lane;
+                const bool valid = i < nb;
+                const uint64_t key = valid ? buf[i] : ~0ull;
+                const uint32_t h = (uint32_t)(key & 0xFFFFu);
+                const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+                const unsigned same = __match_any_sync(0xffffffffu, valid ? h : 0xFFFFFFFFu);
+                const bool leader = valid && (__ffs(same & vmask) - 1) == lane;
+                const bool unseen = valid && !((seen[h >> 5] >> (h & 31)) & 1u);
+                const bool keep = leader && unseen;
+                __syncwarp();
+                if (valid) atomicOr(&seen[h >> 5], 1u << (h & 31));
+                const unsigned km = __ballot_sync(0xffffffffu, keep);
+                const uint32_t pos = out + __popc(km & ((1u << lane) - 1u));
+                if (keep && pos < l_max) buf[pos] = key;
+                out += __popc(km);
+                __syncwarp();
+            }
+            cur = out < l_max ? out : l_max;
+            for (uint32_t w = lane; w < bm_words; w += 32) seen[w] = 0;
+            __syncwarp();
+        }
+        for (uint32_t t = lane; t < l_max; t += 32) res[v * l_max + t] = t < cur ? buf[t] : ~0ull;
+        if (lane == 0) cnt[v] = cur;
+        __syncwarp();
+    }
+}
+}  // namespace
+
+size_t hashprune_smem_bytes(uint32_t m) {
+    uint32_t bm_words = m >= 5 ? (1u << (m - 5)) : 1u;
+    return (size_t)HP_WARPS * (HP_BUF * 8 + bm_words * 4);
+}
+
+int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
+                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt) {
+    if (m < 1 || m > 16) return set_error(PIPNN_EINVAL, "hash_bits %u outside 1..16", m);
+    if (l_max < 1 || l_max > 256) return set_error(PIPNN_EINVAL, "l_max %u outside 1..256", l_max);
+    Workspace ws;
+    unsigned *err = device_error_word();
+    uint64_t *start, *tot;
+    unsigned *fill;
+    uint64_t *slots;
+    uint64_t E = 0;
+    PIPNN_TRY(ws.zeros(&start, n + 1));
+    PIPNN_TRY(ws.zeros(&fill, n));
+    PIPNN_TRY(ws.alloc(&tot, 1));
+    if (count) {
+        hp_count<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, count, n, start, err);
+        PIPNN_LAUNCH_CHECK();
+    }
+    PIPNN_TRY(exclusive_scan_u64(start, start, n, tot, ws));
+    PIPNN_CUDA(cudaMemcpyAsync(start + n, tot, 8, cudaMemcpyDeviceToDevice, stream()));
+    PIPNN_TRY(read_u64(tot, &E));
+    PIPNN_TRY(ws.alloc(&slots, E));
+    if (count) {
+        hp_scatter<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m, start, fill, slots);
+        PIPNN_LAUNCH_CHECK();
+    }
+    size_t smem = hashprune_smem_bytes(m);
+    PIPNN_CUDA(cudaFuncSetAttribute(hp_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    hp_merge<<<grid_for(n, HP_WARPS, 152u * 8u), HP_WARPS * 32, smem, stream()>>>(n, m, l_max, start, slots, res, cnt);
+    PIPNN_LAUNCH_CHECK();
+    return check_device_error("hashprune");
+}
+
+}  // namespace pipnn

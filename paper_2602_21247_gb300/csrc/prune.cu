@@ -1,0 +1,200 @@
+// prune.cu -- A6: Alg. 2 RobustPrune of every node's reservoir down to degree R (Sec. 4.3).
+//
+// One warp per node.  The reservoir's ids are ordered by (dissimilarity to the node, id) with a
+// shared-memory bitonic sort; then the warp repeatedly admits the nearest live candidate y and
+// removes, in parallel over lanes, every live z with alpha^2 * D(y,z) < D(x,z) (binary32).
+// Dissimilarities use the defining order (binary32 FMA chain / exact integer), so the result
+// equals the CPU evaluation of Alg. 2 bit for bit.
+#include "allpairs.cuh"
+
+namespace pipnn {
+
+int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float *H, uint32_t m, float *S,
+                  void *sqnorm);
+
+namespace {
+constexpr int PR_WARPS = 8;
+constexpr int PR_MAX = 256;  // l_max bound
+
+template <int DT, int MET>
+struct Dis {
+    // decision value as (order key, binary32 value)
+    __device__ __forceinline__ static void eval(const void *X, uint32_t d, const int32_t *sqn, uint32_t a, uint32_t b,
+                                                uint32_t &key, float &val) {
+        if (DT == PIPNN_F32) {
+            const float *x = static_cast<const float *>(X) + (uint64_t)a * d;
+            const float *y = static_cast<const float *>(X) + (uint64_t)b * d;
+            float acc = 0.0f;
+            if (MET == PIPNN_L2) {
+                for (uint32_t t = 0; t < d; t++) {
+                    float df = __fsub_rn(__ldg(x + t), __ldg(y + t));
+                    acc = __fmaf_rn(df, df, acc);
+                }
+            } else {
+                for (uint32_t t = 0; t < d; t++) acc = __fmaf_rn(__ldg(x + t), __ldg(y + t), acc);
+                acc = __fsub_rn(1.0f, acc);
+            }
+            key = f32_order(acc);
+            val = acc;
+        } else {
+            const uint32_t dw = (d + 3) / 4;
+            int dot = 0;
+            for (uint32_t w = 0; w < dw; w++) dot = dot4<DT>(coord_word<DT>(X, a, d, w), coord_word<DT>(X, b, d, w), dot);
+            const int D = sqn[a] + sqn[b] - 2 * dot;
+            key = (uint32_t)D;
+            val = __int2float_rn(D);
+        }
+    }
+};
+
+template <int DT, int MET>
+__global__ void __launch_bounds__(PR_WARPS * 32) robust_prune(const void *X, uint64_t n, uint32_t d,
+                                                             const int32_t *sqn, const uint64_t *res,
+                                                             const uint32_t *cnt, uint32_t l_max, uint32_t R,
+                                                             float alpha2, uint32_t *adj, uint32_t *deg,
+                                                             unsigned *err) {
+    __shared__ uint64_t keys[PR_WARPS][PR_MAX];
+    __shared__ float dx[PR_WARPS][PR_MAX];
+    __shared__ uint32_t alive[PR_WARPS][PR_MAX / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *K = keys[warp];
+    float *DX = dx[warp];
+    uint32_t *A = alive[warp];
+
+    for (uint64_t v = (uint64_t)blockIdx.x * PR_WARPS + warp; v < n; v += (uint64_t)gridDim.x * PR_WARPS) {
+        uint32_t c = cnt[v];
+        if (c > l_max) c = l_max;
+        uint32_t P = 32;
+        while (P < c) P <<= 1;
+        // (dissimilarity to v, id) keys
+        for (uint32_t t = lane; t < P; t += 32) {
+            uint64_t kk = ~0ull;
+            if (t < c) {
+                uint32_t id = (uint32_t)(res[v * l_max + t] >> 16);
+                if (id < n) {
+                    uint32_t ok;
+                    float val;
+                    Dis<DT, MET>::eval(X, d, sqn, (uint32_t)v, id, ok, val);
+                    kk = ((uint64_t)ok << 32) | id;
+                } else {
+                    atomicOr(err, DERR_RANGE);
+                }
+            }
+            K[t] = kk;
+        }
+        __syncwarp();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = lane; i < P; i += 32) {
+                    uint32_t ixj = i ^ j;
+                    if (ixj > i) {
+                        uint64_t a = K[i], b = K[ixj];
+                        bool asc = (i & k) == 0;
+                        if ((a > b) == asc) {
+                            K[i] = b;
+                            K[ixj] = a;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        {
+            uint32_t bad = 0;
+            for (uint32_t t = lane; t < c; t += 32) bad += K[t] == ~0ull ? 1u : 0u;
+            for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+            c -= bad;
+        }
+        for (uint32_t t = lane; t < c; t += 32) {
+            uint32_t ord = (uint32_t)(K[t] >> 32);
+            DX[t] = DT == PIPNN_F32 ? f32_unorder(ord) : __int2float_rn((int)ord);
+        }
+        for (uint32_t w = lane; w < PR_MAX / 32; w += 32) {
+            uint32_t lo = w * 32;
+            A[w] = lo >= c ? 0u : (c - lo >= 32 ? 0xFFFFFFFFu : ((1u << (c - lo)) - 1u));
+        }
+        __syncwarp();
+
+        uint32_t e = 0, head = 0;
+        while (e < R) {
+            // next live candidate at or after head
+            uint32_t h = 0xFFFFFFFFu;
+            for (uint32_t w = head / 32; w < (c + 31) / 32; w++) {
+                uint32_t bits = A[w] & (w == head / 32 ? (0xFFFFFFFFu << (head & 31)) : 0xFFFFFFFFu);
+                if (bits) {
+                    h = w * 32 + (__ffs(bits) - 1);
+                    break;
+                }
+            }
+            __syncwarp();
+            if (h == 0xFFFFFFFFu) break;
+            const uint32_t y = (uint32_t)K[h];
+            if (lane == 0) {
+                adj[v * R + e] = y;
+                A[h / 32] &= ~(1u << (h & 31));
+            }
+            e++;
+            head = h + 1;
+            __syncwarp();
+            for (uint32_t z = head + lane; z < c; z += 32) {
+                if (!((A[z / 32] >> (z & 31)) & 1u)) continue;
+                uint32_t ok;
+                float dyz;
+                Dis<DT, MET>::eval(X, d, sqn, y, (uint32_t)K[z], ok, dyz);
+                if (__fmul_rn(alpha2, dyz) < DX[z]) atomicAnd(&A[z / 32], ~(1u << (z & 31)));
+            }
+            __syncwarp();
+        }
+        for (uint32_t t = e + lane; t < R; t += 32) adj[v * R + t] = 0xFFFFFFFFu;
+        if (lane == 0) deg[v] = e;
+        __syncwarp();
+    }
+}
+
+// Without the final prune: the first R reservoir entries in (distance, id) order.
+__global__ void reservoir_to_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R,
+                                   uint32_t *adj, uint32_t *deg) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n * R; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t v = i / R;
+        uint32_t t = (uint32_t)(i % R);
+        uint32_t c = cnt[v] < R ? cnt[v] : R;
+        adj[i] = t < c ? (uint32_t)(res[v * l_max + t] >> 16) : 0xFFFFFFFFu;
+        if (t == 0) deg[v] = c;
+    }
+}
+}  // namespace
+
+int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
+                const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, uint32_t *adj,
+                uint32_t *deg) {
+    if (l_max > PR_MAX) return set_error(PIPNN_EINVAL, "l_max %u exceeds %d", l_max, PR_MAX);
+    Workspace ws;
+    const int32_t *sqn = sqnorm_bytes;
+    if (dtype != PIPNN_F32 && !sqn) {
+        int32_t *tmp = nullptr;
+        PIPNN_TRY(ws.alloc(&tmp, n));
+        PIPNN_TRY(sketch_points(X, n, d, dtype, nullptr, 0, nullptr, tmp));
+        sqn = tmp;
+    }
+    const float alpha2 = (float)((double)alpha * (double)alpha);
+    const unsigned grid = grid_for(n, PR_WARPS, 152u * 16u);
+#define PIPNN_PR(DT, MET) \
+    robust_prune<DT, MET><<<grid, PR_WARPS * 32, 0, stream()>>>(X, n, d, sqn, res, cnt, l_max, R, alpha2, adj, deg, \
+                                                                device_error_word())
+    if (dtype == PIPNN_F32 && metric == PIPNN_L2) PIPNN_PR(PIPNN_F32, PIPNN_L2);
+    else if (dtype == PIPNN_F32) PIPNN_PR(PIPNN_F32, PIPNN_IP);
+    else if (dtype == PIPNN_U8) PIPNN_PR(PIPNN_U8, PIPNN_L2);
+    else PIPNN_PR(PIPNN_I8, PIPNN_L2);
+#undef PIPNN_PR
+    PIPNN_LAUNCH_CHECK();
+    return PIPNN_OK;
+}
+
+int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, uint32_t *adj,
+                    uint32_t *deg) {
+    reservoir_to_graph<<<grid_for(n * R, 256), 256, 0, stream()>>>(n, res, cnt, l_max, R, adj, deg);
+    PIPNN_LAUNCH_CHECK();
+    return PIPNN_OK;
+}
+
+}  // namespace pipnn

@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point include/pipnn.h
+declares; the binding fails loudly rather than falling back when the library is absent."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pipnn.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pipnn_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2602_21247_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("pipnn_build", "pipnn_free", "pipnn_sketch", "pipnn_partition", "pipnn_leaf_pick",
+              "pipnn_hashprune", "pipnn_final_prune", "pipnn_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    import paper_2602_21247_gb300 as pk
+    assert sorted(pk.EXPORTS) == _declared()
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_2602_21247_gb300 as pk
+    monkeypatch.setattr(pk, "_lib", None)
+    monkeypatch.setattr(pk, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        pk.lib()
+
+
+def test_params_struct_matches_header_layout():
+    import paper_2602_21247_gb300 as pk
+    # 3 x u32, f32, 4 x u32, 6 x u32/f32, 3 x i32, pointer (8-byte aligned)
+    assert ctypes.sizeof(pk.pipnn_params) == 4 * (3 + 1 + 4 + 1 + 4 + 1 + 1 + 2) + 4 + 8
+    assert pk.pipnn_params.hyperplanes.offset % 8 == 0
