@@ -1,0 +1,288 @@
+#!/usr/bin/env python
+"""Benchmark: PiPNN index build (Alg. 4) on GB300, points per second.
+
+One step = one full build (sketches, partition, leaf all-pairs + pick, HashPrune, final prune) of
+the bigann-like-u8 workload: 1,000,000 points x 128 uint8 (1,000-cluster mixture), squared L2,
+C_max 2048, l_max 96, R 64, multi-level fanout [10, 3], k = 2, m = 12 hash bits, alpha 1.2.
+The input is resident in HBM when a step starts; L2 is flushed (256 MB write) before every step,
+outside the timed events.  Each rank builds its own independently seeded instance of the workload
+(independent indexes: no collective on the data path), so the job's throughput is the number of
+points all ranks built divided by the slowest rank's time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--engine tc|simt] [--impl reference]
+
+--impl reference times the CPU oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOAD = "bigann-like-u8"
+METRIC = "build points/sec at recall@10>=oracle-0.3pp; GEMM tensor-pipe % and prune HBM GB/s"
+CPU_SAMPLE = 50_000
+REF_SAMPLE = 20_000
+
+
+def workload_params(w):
+    return dict(c_max=w["c_max"], l_max=w["l_max"], R=w["R"], fanout=tuple(w["fanout"]))
+
+
+def config_dict(w, engine, n):
+    return {"workload": WORKLOAD, "n": n, "d": w["d"], "dtype": "u8", "metric": "L2", "c_max": w["c_max"],
+            "c_min": w["c_max"] // 16, "l_max": w["l_max"], "R": w["R"], "fanout": list(w["fanout"]), "leaf_k": 2,
+            "hash_bits": 12, "alpha": 1.2, "p_samp": 0.005, "max_leaders": 1000, "leaf_engine": engine,
+            "l2": "flushed before every step (256 MB write)", "input": "resident in HBM",
+            "data": "synthetic, seeded per rank"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def profiled_traffic(kernel_file, profile_file):
+    """DRAM bytes per launch recorded by an ncu capture, if that capture is of the current source."""
+    src = os.path.join(ROOT, "paper_2602_21247_gb300", "csrc", kernel_file)
+    prof = os.path.join(ROOT, "profiles", profile_file)
+    if not (os.path.exists(src) and os.path.exists(prof)):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    text = open(prof).read()
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(X, H, w):
+    import oracle  # the CPU oracle: timed here as a reported baseline only
+
+    n = min(CPU_SAMPLE, X.shape[0])
+    bp = oracle.params(**workload_params(w))
+    t = time.perf_counter()
+    oracle.build(X[:n], bp, H, synth.BUILD_SEED)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "points/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"first {n:,} points of the {WORKLOAD} workload, full Alg. 4 build ({dt:.1f} s)"}
+
+
+def run_reference(args, w):
+    """Reference arm: the CPU oracle as it stands, on bounded samples of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    n = REF_SAMPLE
+    X = synth.mixture(n, w["d"], w["dtype"], w["centers"], w["sigma"], w["data_seed"])
+    H = synth.hyperplanes(12, w["d"])
+    bp = oracle.params(**workload_params(w))
+    for _ in range(args.warmup):
+        oracle.build(X, bp, H, synth.BUILD_SEED)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.build(X, bp, H, synth.BUILD_SEED)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = n / (ms / 1e3)
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {**config_dict(w, "cpu-oracle", n), "sample": f"first {n:,} points per step"},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {n:,} points of the {WORKLOAD} workload per step"},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--engine", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--n", type=int, default=None, help="override the workload size (tests)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="timed steps only (for profiler launch lists)")
+    args = ap.parse_args()
+    w = dict(synth.WORKLOADS[WORKLOAD])
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2602_21247_gb300 as pk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n = args.n or w["n"]
+    X = synth.mixture(n, w["d"], w["dtype"], w["centers"], w["sigma"], w["data_seed"] + 7919 * rank)
+    H = synth.hyperplanes(12, w["d"])
+    Xd = torch.from_numpy(X).cuda()
+    Hd = torch.from_numpy(H).cuda()
+    engine = pk.PIPNN_LEAF_TC if args.engine == "tc" else pk.PIPNN_LEAF_SIMT
+    bp = pk.params(dtype=pk.PIPNN_U8, hyperplanes=Hd, leaf_engine=engine, **workload_params(w))
+    R = w["R"]
+    adj = torch.empty((n, R), dtype=torch.int32, device="cuda")
+    deg = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")  # 256 MB > 129 MB L2
+
+    for _ in range(args.warmup):
+        pk.pipnn_build_into(Xd, bp, synth.BUILD_SEED, adj, deg)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    sampler = ClockSampler(torch.cuda.current_device())
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        pk.pipnn_build_into(Xd, bp, synth.BUILD_SEED, adj, deg)
+        evs[i][1].record(stream)
+        stats.append(pk.pipnn_get_stats())
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = world * n / (ms / 1e3)
+
+    # dominant kernel: the leaf all-pairs Gram + pick
+    leaf_ms = sum(s["ms_leaf_kernel"] for s in stats) / max(1, sum(s["leaf_kernel_launches"] for s in stats))
+    leaf_flops = stats[-1]["leaf_pairs"] * w["d"]  # sum |b|(|b|-1) d: every unordered pair once, 2 flops/MAC
+    peaks, peak_kind = measured_peaks()
+    peak = peaks["bf16_tflops_sustained"]
+    achieved = leaf_flops / (leaf_ms / 1e3) / 1e12
+    traffic = profiled_traffic("leaf_tc.cu", "leaf_gram_tc_bigann-like-u8.md") if args.engine == "tc" else None
+    roofline = {"kernel": "leaf all-pairs Gram + k-NN pick (" + args.engine + ")", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} bf16 sustained", "traffic": traffic,
+                "algorithmic_flops_per_launch": leaf_flops, "ms_per_launch": leaf_ms}
+    phases = {k: statistics.mean(s[k] for s in stats)
+              for k in ("ms_sketch", "ms_partition", "ms_leaf", "ms_hashprune", "ms_prune")}
+
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": ms, "phases_ms": phases}), flush=True)
+        return 0
+
+    # end to end through the public call: pinned host input, host output, copies inside the region
+    Xh = torch.from_numpy(X).pin_memory()
+    adj_h = torch.empty((n, R), dtype=torch.int32).pin_memory()
+    deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    Hh = torch.from_numpy(H)
+    bp_h = pk.params(dtype=pk.PIPNN_U8, hyperplanes=Hh, leaf_engine=engine, **workload_params(w))
+    pk.pipnn_build_into(Xh, bp_h, synth.BUILD_SEED, adj_h, deg_h)
+    e2e_steps = max(3, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pk.pipnn_build_into(Xh, bp_h, synth.BUILD_SEED, adj_h, deg_h)
+        int(deg_h[0])  # the result is read on the host
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e = {"value": world * n / float(te.item()), "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes + H.nbytes),
+           "d2h_bytes_per_step": int(n * R * 4 + n * 4)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": config_dict(w, args.engine, n), "roofline": roofline, "e2e": e2e,
+                "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks,
+                "phases_ms": phases, "leaves": stats[-1]["leaves"], "candidates": stats[-1]["candidates"]}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(X, H, w)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -116,6 +116,7 @@ typedef struct pipnn_stats {
     uint64_t leaves, leaf_members, candidates;
     double leaf_pairs;           /* sum over leaves of |b| (|b| - 1), the unordered-pair work x2 */
     double leaf_pairs_executed;  /* pairs the kernel evaluated (full tiles, both orders)        */
+    uint64_t kernel_launches;    /* kernels this library launched during the build              */
 } pipnn_stats;
 
 /* Sets the CUDA stream (a cudaStream_t, or NULL for the default stream) used by later calls. */
@@ -179,7 +180,13 @@ int pipnn_build(const void *points, uint64_t n, uint32_t d, int32_t metric, cons
                 uint64_t seed, int32_t graph_on_host, pipnn_graph *out);
 void pipnn_free(pipnn_graph *graph);
 
-/* Statistics of the last successful pipnn_build on the calling thread. */
+/* Alg. 4 end to end into caller-owned outputs: adj (n x R uint32) and deg (n uint32), host or
+ * device pointers, written completely on success (rows padded with 0xFFFFFFFF).  points: host or
+ * device.  Allocates only its device workspace. */
+int pipnn_build_into(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp,
+                     uint64_t seed, uint32_t *adj, uint32_t *deg);
+
+/* Statistics of the last successful pipnn_build / pipnn_build_into on the calling thread. */
 int pipnn_get_stats(pipnn_stats *out);
 
 #ifdef __cplusplus

@@ -31,7 +31,7 @@ PIPNN_OK = 0
 # symbols declared in include/pipnn.h
 EXPORTS = ("pipnn_set_stream", "pipnn_last_error", "pipnn_sketch", "pipnn_partition", "pipnn_leaves_free",
            "pipnn_leaf_pick", "pipnn_edges_free", "pipnn_hashprune", "pipnn_final_prune", "pipnn_build",
-           "pipnn_free", "pipnn_get_stats")
+           "pipnn_free", "pipnn_build_into", "pipnn_get_stats")
 
 
 class PipnnError(RuntimeError):
@@ -67,7 +67,8 @@ class pipnn_stats(C.Structure):
                 ("ms_leaf", C.c_float), ("ms_hashprune", C.c_float), ("ms_prune", C.c_float),
                 ("ms_leaf_kernel", C.c_float), ("leaf_kernel_launches", C.c_uint32), ("levels", C.c_uint32),
                 ("leaves", C.c_uint64), ("leaf_members", C.c_uint64), ("candidates", C.c_uint64),
-                ("leaf_pairs", C.c_double), ("leaf_pairs_executed", C.c_double)]
+                ("leaf_pairs", C.c_double), ("leaf_pairs_executed", C.c_double),
+                ("kernel_launches", C.c_uint64)]
 
 
 _lib = None
@@ -95,6 +96,7 @@ def lib():
         L.pipnn_build.argtypes = [vp, u64, u32, i32, C.POINTER(pipnn_params), u64, i32, C.POINTER(pipnn_graph)]
         L.pipnn_free.argtypes = [C.POINTER(pipnn_graph)]
         L.pipnn_free.restype = None
+        L.pipnn_build_into.argtypes = [vp, u64, u32, i32, C.POINTER(pipnn_params), u64, vp, vp]
         L.pipnn_get_stats.argtypes = [C.POINTER(pipnn_stats)]
         _lib = L
     return _lib
@@ -264,6 +266,16 @@ def pipnn_build(points, bp: pipnn_params, seed: int, metric=PIPNN_L2, graph_on_h
             deg = np.ctypeslib.as_array((C.c_uint32 * n).from_address(g.deg)).copy()
     finally:
         lib().pipnn_free(C.byref(g))
+    return adj, deg
+
+
+def pipnn_build_into(points, bp: pipnn_params, seed: int, adj, deg, metric=PIPNN_L2):
+    """Alg. 4 end to end into caller-owned adj (n x R) / deg (n) uint32 buffers, host or device
+    (torch tensors or numpy arrays)."""
+    n, d = points.shape
+    bp.dtype = dtype_code(points)
+    pipnn_set_stream()
+    _check(lib().pipnn_build_into(_ptr(points), n, d, metric, C.byref(bp), seed, _ptr(adj), _ptr(deg)))
     return adj, deg
 
 

@@ -115,9 +115,27 @@ __global__ void leaf_pairs_kernel(const uint64_t *off, uint64_t L, double *acc) 
     atomicAdd(acc, local);
 }
 
+// Keeps freed stream-ordered allocations in the device's default pool (the build allocates and
+// frees the same large buffers every call).
+void keep_pool_memory() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+}
+
+// graph_on_host: 0 device graph, 1 pinned host graph, 2 caller buffers (user_adj/user_deg)
 int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pipnn_params *bp, uint64_t seed,
-               int graph_on_host, pipnn_graph *out) {
+               int graph_on_host, pipnn_graph *out, uint32_t *user_adj = nullptr, uint32_t *user_deg = nullptr) {
     memset(out, 0, sizeof(*out));
+    keep_pool_memory();
     PIPNN_TRY(check_params(bp));
     const int dtype = bp->dtype;
     PIPNN_TRY(check_points(points, n, d, dtype, metric));
@@ -130,6 +148,7 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     PIPNN_TRY(tm.init());
     pipnn_stats st;
     memset(&st, 0, sizeof(st));
+    const uint64_t launches0 = launch_count();
     tm.mark(0);
 
     // inputs on the device
@@ -213,7 +232,18 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     }
     if (rc == PIPNN_OK) rc = check_device_error("final prune");
     tm.mark(5);
-    if (rc == PIPNN_OK && graph_on_host) {
+    if (rc == PIPNN_OK && graph_on_host == 2) {
+        cudaError_t e = cudaMemcpyAsync(user_adj, adj, n * bp->R * 4, cudaMemcpyDefault, stream());
+        if (e == cudaSuccess) e = cudaMemcpyAsync(user_deg, deg, n * 4, cudaMemcpyDefault, stream());
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream());
+        dev_free_raw(adj);
+        dev_free_raw(deg);
+        adj = deg = nullptr;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(PIPNN_ECUDA, "graph copy: %s", cudaGetErrorString(e));
+        }
+    } else if (rc == PIPNN_OK && graph_on_host) {
         uint32_t *hadj = nullptr, *hdeg = nullptr;
         cudaError_t e = cudaMallocHost(&hadj, n * bp->R * 4);
         if (e == cudaSuccess) e = cudaMallocHost(&hdeg, n * 4);
@@ -252,6 +282,7 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     st.ms_hashprune = tm.ms(3, 4);
     st.ms_prune = tm.ms(4, 5);
     st.ms_total = tm.ms(0, 6);
+    st.kernel_launches = launch_count() - launches0;
     g_stats = st;
     return PIPNN_OK;
 }
@@ -350,7 +381,14 @@ int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype,
 int pipnn_build(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp, uint64_t seed,
                 int32_t graph_on_host, pipnn_graph *out) {
     if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
-    return build_impl(points, n, d, metric, bp, seed, graph_on_host, out);
+    return build_impl(points, n, d, metric, bp, seed, graph_on_host ? 1 : 0, out);
+}
+
+int pipnn_build_into(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp,
+                     uint64_t seed, uint32_t *adj, uint32_t *deg) {
+    if (!adj || !deg) return set_error(PIPNN_EINVAL, "adj/deg are NULL");
+    pipnn_graph g;
+    return build_impl(points, n, d, metric, bp, seed, 2, &g, adj, deg);
 }
 
 void pipnn_free(pipnn_graph *g) {

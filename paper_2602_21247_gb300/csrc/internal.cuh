@@ -39,7 +39,14 @@ void clear_error();
         if (rc_ != PIPNN_OK) return rc_;                                                      \
     } while (0)
 
-#define PIPNN_LAUNCH_CHECK() PIPNN_CUDA(cudaGetLastError())
+// counts this thread's kernel launches (every launch site is followed by this check)
+void count_launch();
+uint64_t launch_count();
+#define PIPNN_LAUNCH_CHECK()                                                                  \
+    do {                                                                                      \
+        ::pipnn::count_launch();                                                              \
+        PIPNN_CUDA(cudaGetLastError());                                                       \
+    } while (0)
 
 cudaStream_t stream();
 

@@ -8,6 +8,10 @@ namespace pipnn {
 static thread_local char g_msg[1024];
 static thread_local cudaStream_t g_stream = nullptr;
 static thread_local unsigned *g_err_word = nullptr;
+static thread_local uint64_t g_launches = 0;
+
+void count_launch() { g_launches++; }
+uint64_t launch_count() { return g_launches; }
 
 int set_error(int code, const char *fmt, ...) {
     va_list ap;
