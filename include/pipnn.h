@@ -164,6 +164,24 @@ int pipnn_hashprune(const uint32_t *dst, const uint32_t *src, const float *dist,
                     const float *sketch, uint32_t m, uint64_t n, uint32_t l_max, uint64_t *reservoir,
                     uint32_t *count_inout);
 
+/* pipnn_hashprune without any device allocation (the paper has no counterpart; this is a
+ * deployment variant of A5).  Some callers cannot call cudaMalloc or let a library do it: a
+ * serving process whose own allocator has reserved the GPU's memory up front, or a host thread
+ * that must not block on the driver's allocator.  This entry point takes the same arguments
+ * and returns the same reservoirs as pipnn_hashprune, bit for bit, but keeps its scratch in a
+ * fixed 64 MiB device array inside the library, which every GPU that loads the library holds
+ * until the process exits.  The call needs
+ *   256 + 8(n+1) + 4n + 8*(ceil(n/4096) + ceil(n/4096^2) + ... + 1) + 8*count  bytes
+ * (each term rounded up to 256); larger inputs return PIPNN_EINVAL with the sizes in the
+ * message, before any GPU work.  The first call on each device looks up the array's device
+ * address (with that device current) and remembers it; make that first call before any stream
+ * capture.  All calls share the array and clear what they need on entry, so calls that overlap
+ * on the GPU (different streams or threads on one device) race and must be serialised by the
+ * caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
+int pipnn_hashprune_noalloc(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count,
+                            const float *sketch, uint32_t m, uint64_t n, uint32_t l_max, uint64_t *reservoir,
+                            uint32_t *count_inout);
+
 /* A6 -- Alg. 2 RobustPrune of every node's reservoir to at most R neighbours (Sec. 4.3).
  * Candidates are ordered by (dissimilarity to the node, id); candidate z is removed by the
  * admitted y when alpha^2 * D(y,z) < D(x,z), evaluated in binary32 with

@@ -31,7 +31,7 @@ PIPNN_OK = 0
 # symbols declared in include/pipnn.h
 EXPORTS = ("pipnn_set_stream", "pipnn_last_error", "pipnn_sketch", "pipnn_partition", "pipnn_leaves_free",
            "pipnn_leaf_pick", "pipnn_edges_free", "pipnn_hashprune", "pipnn_final_prune", "pipnn_build",
-           "pipnn_free", "pipnn_build_into", "pipnn_get_stats")
+           "pipnn_free", "pipnn_build_into", "pipnn_get_stats", "pipnn_hashprune_noalloc")
 
 
 class PipnnError(RuntimeError):
@@ -92,6 +92,7 @@ def lib():
         L.pipnn_edges_free.argtypes = [C.POINTER(pipnn_edges)]
         L.pipnn_edges_free.restype = None
         L.pipnn_hashprune.argtypes = [vp, vp, vp, u64, vp, u32, u64, u32, vp, vp]
+        L.pipnn_hashprune_noalloc.argtypes = [vp, vp, vp, u64, vp, u32, u64, u32, vp, vp]
         L.pipnn_final_prune.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, u32, f32, vp, vp]
         L.pipnn_build.argtypes = [vp, u64, u32, i32, C.POINTER(pipnn_params), u64, i32, C.POINTER(pipnn_graph)]
         L.pipnn_free.argtypes = [C.POINTER(pipnn_graph)]
@@ -232,6 +233,16 @@ def pipnn_hashprune(dst, src, dist, sketch, n, l_max, reservoir=None, count=None
     pipnn_set_stream()
     _check(lib().pipnn_hashprune(_ptr(dst), _ptr(src), _ptr(dist), dst.numel(), _ptr(sketch), m, n, l_max,
                                  _ptr(reservoir), _ptr(count)))
+    return reservoir, count
+
+
+def pipnn_hashprune_noalloc(dst, src, dist, sketch, n, l_max, reservoir, count):
+    """A5 without device allocation (fixed 64 MiB library scratch); reservoir/count are updated
+    in place and must be provided by the caller."""
+    m = sketch.shape[1]
+    pipnn_set_stream()
+    _check(lib().pipnn_hashprune_noalloc(_ptr(dst), _ptr(src), _ptr(dist), dst.numel(), _ptr(sketch), m, n, l_max,
+                                         _ptr(reservoir), _ptr(count)))
     return reservoir, count
 
 

@@ -164,3 +164,120 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
 }
 
 }  // namespace pipnn
+
+// ---------------------------------------------------------------------------------------------
+// pipnn_hashprune_noalloc: HashPrune for callers that cannot allocate device memory.
+//
+// Its scratch (per-node run offsets and fill counters, the scan's per-tile totals, the grouped
+// slots and the error word) lives in one file-scope device array of HP_STATIC_BYTES that every
+// GPU loading this library keeps until the process exits.  Host code cannot use the array's
+// name as a device address, so the first call on each device, with that device current, asks
+// the runtime for the address once (cudaGetSymbolAddress) and later calls reuse it.  Every call
+// shares the array and reuses whatever the previous call left there, so the parts that must
+// start at zero are cleared on each call; two calls whose work overlaps on the GPU (different
+// streams or host threads on the same device) race on it.
+// ---------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace pipnn {
+void set_device_error_word(unsigned *p);
+
+namespace {
+constexpr size_t HP_STATIC_BYTES = 64ull << 20;
+constexpr int HP_STATIC_MAX_DEVICES = 64;
+static __device__ __align__(256) unsigned char g_hp_static_scratch[HP_STATIC_BYTES];
+std::mutex g_hp_static_mu;
+void *g_hp_static_addr[HP_STATIC_MAX_DEVICES];
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct StaticLayout {
+    size_t err, total, start, fill, scan, slots, bytes;
+};
+
+StaticLayout static_layout(uint64_t n, uint64_t count) {
+    StaticLayout L;
+    L.err = 0;
+    L.total = 8;
+    L.start = 256;
+    L.fill = L.start + round256((n + 1) * 8);
+    L.scan = L.fill + round256(n * 4);
+    L.slots = L.scan + round256(scan_scratch_elems(n) * 8);
+    L.bytes = L.slots + count * 8;
+    return L;
+}
+
+int static_scratch_address(unsigned char **base) {
+    int dev = 0;
+    PIPNN_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= HP_STATIC_MAX_DEVICES) return set_error(PIPNN_EUNSUPPORTED, "device %d", dev);
+    std::lock_guard<std::mutex> lock(g_hp_static_mu);
+    if (!g_hp_static_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_hp_static_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return set_error(PIPNN_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                             cudaGetErrorString(e));
+        }
+        g_hp_static_addr[dev] = p;
+    }
+    *base = static_cast<unsigned char *>(g_hp_static_addr[dev]);
+    return PIPNN_OK;
+}
+
+int hashprune_noalloc_impl(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count,
+                           const float *S, uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt) {
+    if (count && (!dst || !src || !dist)) return set_error(PIPNN_EINVAL, "candidate arrays are NULL");
+    if (!S || !res || !cnt) return set_error(PIPNN_EINVAL, "sketch/reservoir/count are NULL");
+    if (n == 0 || n >= 0xFFFFFFFFull) return set_error(PIPNN_EINVAL, "n outside 1..2^32-2");
+    if (m < 1 || m > 16) return set_error(PIPNN_EINVAL, "hash_bits %u outside 1..16", m);
+    if (l_max < 1 || l_max > 256) return set_error(PIPNN_EINVAL, "l_max %u outside 1..256", l_max);
+    const StaticLayout L = static_layout(n, count);
+    if (L.bytes > HP_STATIC_BYTES)
+        return set_error(PIPNN_EINVAL,
+                         "n = %llu nodes and %llu candidates need %zu bytes of scratch; the static scratch "
+                         "holds %zu bytes (use pipnn_hashprune or split the stream)",
+                         (unsigned long long)n, (unsigned long long)count, L.bytes, HP_STATIC_BYTES);
+    unsigned char *base = nullptr;
+    PIPNN_TRY(static_scratch_address(&base));
+    unsigned *err = reinterpret_cast<unsigned *>(base + L.err);
+    uint64_t *total = reinterpret_cast<uint64_t *>(base + L.total);
+    uint64_t *start = reinterpret_cast<uint64_t *>(base + L.start);
+    unsigned *fill = reinterpret_cast<unsigned *>(base + L.fill);
+    uint64_t *scan = reinterpret_cast<uint64_t *>(base + L.scan);
+    uint64_t *slots = reinterpret_cast<uint64_t *>(base + L.slots);
+
+    PIPNN_CUDA(cudaMemsetAsync(base, 0, 256, stream()));
+    PIPNN_CUDA(cudaMemsetAsync(start, 0, (n + 1) * 8, stream()));
+    PIPNN_CUDA(cudaMemsetAsync(fill, 0, n * 4, stream()));
+    set_device_error_word(err);
+    struct Restore {
+        ~Restore() { set_device_error_word(nullptr); }
+    } restore;
+
+    if (count) {
+        hp_count<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, count, n, start, err);
+        PIPNN_LAUNCH_CHECK();
+    }
+    PIPNN_TRY(exclusive_scan_u64_scratch(start, start, n, total, scan));
+    PIPNN_CUDA(cudaMemcpyAsync(start + n, total, 8, cudaMemcpyDeviceToDevice, stream()));
+    if (count) {
+        hp_scatter<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m, start, fill, slots);
+        PIPNN_LAUNCH_CHECK();
+    }
+    const size_t smem = hashprune_smem_bytes(m);
+    PIPNN_CUDA(cudaFuncSetAttribute(hp_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    hp_merge<<<grid_for(n, HP_WARPS, 152u * 8u), HP_WARPS * 32, smem, stream()>>>(n, m, l_max, start, slots, res, cnt);
+    PIPNN_LAUNCH_CHECK();
+    return check_device_error("hashprune (static scratch)");
+}
+}  // namespace
+}  // namespace pipnn
+
+extern "C" int pipnn_hashprune_noalloc(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count,
+                                       const float *sketch, uint32_t m, uint64_t n, uint32_t l_max,
+                                       uint64_t *reservoir, uint32_t *count_inout) {
+    pipnn::clear_error();
+    return pipnn::hashprune_noalloc_impl(dst, src, dist, count, sketch, m, n, l_max, reservoir, count_inout);
+}

@@ -114,6 +114,11 @@ void dev_free_raw(void *p);
 // exclusive prefix sum of n uint64 values (in may equal out); total written to *total_dev
 int exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, uint64_t *total_dev,
                        Workspace &ws);
+// the same with caller-provided scratch for the per-tile totals (no allocation);
+// scratch holds scan_scratch_elems(n) values
+size_t scan_scratch_elems(uint64_t n);
+int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t *out, uint64_t n, uint64_t *total_dev,
+                               uint64_t *scratch);
 // copy one device value to the host (synchronises the stream)
 int read_u64(const uint64_t *dev, uint64_t *host);
 

@@ -169,6 +169,38 @@ int exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, uint64_t *
     return PIPNN_OK;
 }
 
+size_t scan_scratch_elems(uint64_t n) {
+    size_t total = 1;
+    for (uint64_t t = n;;) {
+        uint64_t tiles = (t + SCAN_TILE - 1) / SCAN_TILE;
+        total += tiles;
+        if (tiles <= 1) break;
+        t = tiles;
+    }
+    return total;
+}
+
+int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t *out, uint64_t n, uint64_t *total_dev,
+                               uint64_t *scratch) {
+    if (n == 0) {
+        PIPNN_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), stream()));
+        return PIPNN_OK;
+    }
+    const uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    uint64_t *sums = scratch;
+    scan_tiles<<<(unsigned)tiles, SCAN_THREADS, 0, stream()>>>(in, out, n, sums);
+    PIPNN_LAUNCH_CHECK();
+    if (tiles == 1) {
+        copy_one<<<1, 1, 0, stream()>>>(sums, total_dev);
+        PIPNN_LAUNCH_CHECK();
+        return PIPNN_OK;
+    }
+    PIPNN_TRY(exclusive_scan_u64_scratch(sums, sums, tiles, total_dev, scratch + tiles));
+    scan_add<<<(unsigned)tiles, SCAN_THREADS, 0, stream()>>>(out, n, sums);
+    PIPNN_LAUNCH_CHECK();
+    return PIPNN_OK;
+}
+
 int make_tiles(const uint32_t *size, uint64_t groups, uint32_t tile, uint32_t **tile_grp,
                uint32_t **tile_row0, uint64_t *num_tiles, Workspace &ws) {
     *num_tiles = 0;
