@@ -151,6 +151,219 @@ __global__ void __launch_bounds__(PR_WARPS * 32) robust_prune(const void *X, uin
     }
 }
 
+// Shared-memory variant: the node's candidate rows (and its own) are staged once per node with
+// coalesced row loads (row stride dw+1 words, so lanes reading different rows hit different
+// banks); keys (D(x,c), id) are sorted with the slot as payload and every D(y,z) of the prune
+// loop reads shared memory only.  Same arithmetic and order as robust_prune.
+struct PruneSmem {
+    uint32_t dw, lmax, P;
+    size_t rows, keys, perm, dx, nz, alive, per_warp;
+};
+
+__host__ __device__ inline PruneSmem prune_smem_layout(int dtype, uint32_t d, uint32_t l_max) {
+    PruneSmem L;
+    L.dw = dtype == PIPNN_F32 ? d : (d + 3) / 4;
+    L.lmax = l_max;
+    L.P = 32;
+    while (L.P < l_max) L.P <<= 1;
+    size_t o = 0;
+    L.rows = o;
+    o += (size_t)(l_max + 1) * (L.dw + 1) * 4;
+    o = (o + 7) & ~(size_t)7;
+    L.keys = o;
+    o += (size_t)L.P * 8;
+    L.perm = o;
+    o += (size_t)L.P * 2;
+    o = (o + 3) & ~(size_t)3;
+    L.dx = o;
+    o += (size_t)l_max * 4;
+    L.nz = o;
+    o += (size_t)(l_max + 1) * 4;
+    L.alive = o;
+    o += (size_t)((l_max + 31) / 32) * 4;
+    L.per_warp = (o + 15) & ~(size_t)15;
+    return L;
+}
+
+template <int DT, int MET>
+__device__ __forceinline__ void dis_smem(const uint32_t *ra, const uint32_t *rb, uint32_t dw, int na, int nb,
+                                         uint32_t &key, float &val) {
+    if (DT == PIPNN_F32) {
+        float acc = 0.0f;
+        if (MET == PIPNN_L2) {
+            for (uint32_t t = 0; t < dw; t++) {
+                const float df = __fsub_rn(__uint_as_float(ra[t]), __uint_as_float(rb[t]));
+                acc = __fmaf_rn(df, df, acc);
+            }
+        } else {
+            for (uint32_t t = 0; t < dw; t++) acc = __fmaf_rn(__uint_as_float(ra[t]), __uint_as_float(rb[t]), acc);
+            acc = __fsub_rn(1.0f, acc);
+        }
+        key = f32_order(acc);
+        val = acc;
+    } else {
+        int dot = 0;
+        for (uint32_t w = 0; w < dw; w++) dot = dot4<DT>(ra[w], rb[w], dot);
+        const int D = na + nb - 2 * dot;
+        key = (uint32_t)D;
+        val = __int2float_rn(D);
+    }
+}
+
+template <int DT, int MET>
+__global__ void robust_prune_smem(const void *X, uint64_t n, uint32_t d, const int32_t *sqn, const uint64_t *res,
+                                  const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha2, uint32_t *adj,
+                                  uint32_t *deg, unsigned *err) {
+    extern __shared__ __align__(16) unsigned char pr_smem[];
+    const PruneSmem L = prune_smem_layout(DT, d, l_max);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    unsigned char *base = pr_smem + (size_t)warp * L.per_warp;
+    uint32_t *rows = reinterpret_cast<uint32_t *>(base + L.rows);   // (l_max + 1) x (dw + 1); row l_max = node
+    uint64_t *K = reinterpret_cast<uint64_t *>(base + L.keys);
+    uint16_t *perm = reinterpret_cast<uint16_t *>(base + L.perm);
+    float *DX = reinterpret_cast<float *>(base + L.dx);
+    int *NZ = reinterpret_cast<int *>(base + L.nz);
+    uint32_t *A = reinterpret_cast<uint32_t *>(base + L.alive);
+    const uint32_t stride = L.dw + 1;
+
+    for (uint64_t v = (uint64_t)blockIdx.x * nwarps + warp; v < n; v += (uint64_t)gridDim.x * nwarps) {
+        uint32_t c = cnt[v];
+        if (c > l_max) c = l_max;
+        // stage the node and its candidates; invalid ids are dropped (and reported)
+        uint32_t nvalid = 0;
+        for (uint32_t t0 = 0; t0 < c; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            uint32_t id = 0xFFFFFFFFu;
+            if (t < c) {
+                id = (uint32_t)(res[v * l_max + t] >> 16);
+                if (id >= n) {
+                    atomicOr(err, DERR_RANGE);
+                    id = 0xFFFFFFFFu;
+                }
+            }
+            const unsigned okm = __ballot_sync(0xffffffffu, id != 0xFFFFFFFFu);
+            const uint32_t slot = nvalid + __popc(okm & ((1u << lane) - 1u));
+            if (id != 0xFFFFFFFFu) {
+                K[slot] = id;  // ids first; keys are formed below
+                NZ[slot] = DT == PIPNN_F32 ? 0 : sqn[id];
+            }
+            nvalid += __popc(okm);
+        }
+        c = nvalid;
+        __syncwarp();
+        // candidate rows into rows 0..c-1, the node's own row into row l_max; four independent
+        // loads per lane are in flight before their stores
+        {
+            const uint32_t total = (c + 1) * L.dw;
+            for (uint32_t b0 = 0; b0 < total; b0 += 128) {
+                uint32_t vals[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t idx = b0 + u * 32 + lane;
+                    vals[u] = 0;
+                    if (idx < total) {
+                        const uint32_t t = idx / L.dw, w = idx - t * L.dw;
+                        const uint32_t id = t < c ? (uint32_t)K[t] : (uint32_t)v;
+                        if (DT == PIPNN_F32) vals[u] = __float_as_uint(__ldg(static_cast<const float *>(X) + (uint64_t)id * d + w));
+                        else vals[u] = coord_word<DT>(X, id, d, w);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t idx = b0 + u * 32 + lane;
+                    if (idx < total) {
+                        const uint32_t t = idx / L.dw, w = idx - t * L.dw;
+                        rows[(size_t)(t < c ? t : l_max) * stride + w] = vals[u];
+                    }
+                }
+            }
+        }
+        if (lane == 0) NZ[l_max] = DT == PIPNN_F32 ? 0 : sqn[v];
+        __syncwarp();
+        const uint32_t *xr = rows + (size_t)l_max * stride;
+        uint32_t P = 32;
+        while (P < c) P <<= 1;
+        for (uint32_t t = lane; t < P; t += 32) {
+            uint64_t kk = ~0ull;
+            if (t < c) {
+                uint32_t ok;
+                float val;
+                dis_smem<DT, MET>(xr, rows + (size_t)t * stride, L.dw, NZ[l_max], NZ[t], ok, val);
+                kk = ((uint64_t)ok << 32) | (uint32_t)K[t];
+            }
+            K[t] = kk;
+            perm[t] = (uint16_t)t;
+        }
+        __syncwarp();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = lane; i < P; i += 32) {
+                    const uint32_t ixj = i ^ j;
+                    if (ixj > i) {
+                        const uint64_t a = K[i], b = K[ixj];
+                        const bool asc = (i & k) == 0;
+                        if ((a > b) == asc) {
+                            K[i] = b;
+                            K[ixj] = a;
+                            const uint16_t pa = perm[i];
+                            perm[i] = perm[ixj];
+                            perm[ixj] = pa;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (uint32_t t = lane; t < c; t += 32) {
+            const uint32_t ord = (uint32_t)(K[t] >> 32);
+            DX[t] = DT == PIPNN_F32 ? f32_unorder(ord) : __int2float_rn((int)ord);
+        }
+        for (uint32_t w = lane; w < (l_max + 31) / 32; w += 32) {
+            const uint32_t lo = w * 32;
+            A[w] = lo >= c ? 0u : (c - lo >= 32 ? 0xFFFFFFFFu : ((1u << (c - lo)) - 1u));
+        }
+        __syncwarp();
+
+        uint32_t e = 0, head = 0;
+        while (e < R) {
+            uint32_t h = 0xFFFFFFFFu;
+            for (uint32_t w = head / 32; w < (c + 31) / 32; w++) {
+                const uint32_t bits = A[w] & (w == head / 32 ? (0xFFFFFFFFu << (head & 31)) : 0xFFFFFFFFu);
+                if (bits) {
+                    h = w * 32 + (__ffs(bits) - 1);
+                    break;
+                }
+            }
+            __syncwarp();
+            if (h == 0xFFFFFFFFu) break;
+            const uint32_t y = (uint32_t)K[h];
+            const uint32_t ys = perm[h];
+            if (lane == 0) {
+                adj[v * R + e] = y;
+                A[h / 32] &= ~(1u << (h & 31));
+            }
+            e++;
+            head = h + 1;
+            __syncwarp();
+            const uint32_t *yr = rows + (size_t)ys * stride;
+            const int ny = NZ[ys];
+            for (uint32_t z = head + lane; z < c; z += 32) {
+                if (!((A[z / 32] >> (z & 31)) & 1u)) continue;
+                const uint32_t zs = perm[z];
+                uint32_t ok;
+                float dyz;
+                dis_smem<DT, MET>(yr, rows + (size_t)zs * stride, L.dw, ny, NZ[zs], ok, dyz);
+                if (__fmul_rn(alpha2, dyz) < DX[z]) atomicAnd(&A[z / 32], ~(1u << (z & 31)));
+            }
+            __syncwarp();
+        }
+        for (uint32_t t = e + lane; t < R; t += 32) adj[v * R + t] = 0xFFFFFFFFu;
+        if (lane == 0) deg[v] = e;
+        __syncwarp();
+    }
+}
+
 // Without the final prune: the first R reservoir entries in (distance, id) order.
 __global__ void reservoir_to_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R,
                                    uint32_t *adj, uint32_t *deg) {
@@ -177,6 +390,29 @@ int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, co
         sqn = tmp;
     }
     const float alpha2 = (float)((double)alpha * (double)alpha);
+    const PruneSmem L = prune_smem_layout(dtype, d, l_max);
+    const size_t budget = 200 * 1024;
+    if (L.per_warp <= budget) {
+        uint32_t wpb = (uint32_t)(budget / L.per_warp);
+        if (wpb > 8) wpb = 8;
+        const size_t smem = wpb * L.per_warp;
+        const unsigned grid = grid_for(n, wpb, 152u * 64u);
+        unsigned *err = device_error_word();
+#define PIPNN_PRS(DT, MET)                                                                                   \
+    do {                                                                                                     \
+        PIPNN_CUDA(cudaFuncSetAttribute(robust_prune_smem<DT, MET>,                                           \
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));            \
+        robust_prune_smem<DT, MET><<<grid, wpb * 32, smem, stream()>>>(X, n, d, sqn, res, cnt, l_max, R, alpha2, \
+                                                                      adj, deg, err);                        \
+    } while (0)
+        if (dtype == PIPNN_F32 && metric == PIPNN_L2) PIPNN_PRS(PIPNN_F32, PIPNN_L2);
+        else if (dtype == PIPNN_F32) PIPNN_PRS(PIPNN_F32, PIPNN_IP);
+        else if (dtype == PIPNN_U8) PIPNN_PRS(PIPNN_U8, PIPNN_L2);
+        else PIPNN_PRS(PIPNN_I8, PIPNN_L2);
+#undef PIPNN_PRS
+        PIPNN_LAUNCH_CHECK();
+        return PIPNN_OK;
+    }
     const unsigned grid = grid_for(n, PR_WARPS, 152u * 16u);
 #define PIPNN_PR(DT, MET) \
     robust_prune<DT, MET><<<grid, PR_WARPS * 32, 0, stream()>>>(X, n, d, sqn, res, cnt, l_max, R, alpha2, adj, deg, \
