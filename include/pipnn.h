@@ -52,10 +52,11 @@ enum { PIPNN_L2 = 0, PIPNN_IP = 1 };
 /* Engine of the leaf all-pairs step (A2).  Both give identical candidate edges.
  *  PIPNN_LEAF_SIMT: CUDA-core arithmetic in the defining order (binary32 FMA chain / exact
  *                   integer dot products).
- *  PIPNN_LEAF_TC:   tcgen05 tensor-core Gram tiles with BF16 operands and FP32 accumulation in
- *                   TMEM, dissimilarities formed in the epilogue (n_i + n_j - 2 G).  For byte
- *                   data with d <= 256 every product and partial sum is an integer below 2^24,
- *                   so the Gram is exact; float data is not supported by this engine. */
+ *  PIPNN_LEAF_TC:   tcgen05 tensor-core tiles with BF16 operands and FP32 accumulation in TMEM
+ *                   that produce n_j - 2<x_i, x_j> directly (the norm enters as three extra
+ *                   K columns).  For byte data with d <= 128 every product and partial sum is an
+ *                   integer below 2^24, so the result is exact; float data and d > 128 return
+ *                   PIPNN_EUNSUPPORTED. */
 enum { PIPNN_LEAF_SIMT = 0, PIPNN_LEAF_TC = 1 };
 
 /* Hyper-parameters BP of Alg. 4. */

@@ -1,38 +1,42 @@
 // leaf_tc.cu -- A2..A4 on the 5th-generation tensor cores (tcgen05 + TMEM), byte data.
 //
-// For every leaf b and every 128-row tile of it, one CTA computes the Gram block
-// G = X_rows X_colsᵀ against all |b| members, 256 columns at a time, and keeps, per row, the
-// k nearest other members by (D, id) with D = n_i + n_j - 2 G_ij (Sec. 4.2: the all-pairs
-// distance matrix of a leaf; App. A.3: bi-directed k-NN pick).  The distance matrix never
-// leaves TMEM / registers.
+// For every leaf b and every 128-row tile of it, the kernel forms, for all |b| members j,
+//     v_ij = n_j - 2 <x_i, x_j>         (D_ij = n_i + v_ij, squared L2; n = squared norm)
+// directly in the tensor-core accumulator, and keeps per row the k nearest other members by
+// (D, id) (Sec. 4.2: the all-pairs distance matrix of a leaf; App. A.3: bi-directed k-NN pick).
+// The distance matrix never leaves TMEM / registers.
 //
-// Exactness: u8 / i8 coordinates are exact in BF16; every product is an integer of magnitude
-// <= 65,536 and for d <= 256 every partial sum of d products, n_j - 2G and D stay below 2^24,
-// so FP32 accumulation in the tensor core is exact in any order and the picks equal those of
-// the defining integer arithmetic.
+// The MMA operands come from one leaf-ordered BF16 copy of the members' rows: A_i = [x_i, 1,1,1,1]
+// and B_j = [x_j, -b1, -b2, -b3, -h] with n_j / 2 = b1 + b2 + b3 + h split into byte-wide pieces and
+// h = (n_j mod 2) / 2, so the accumulator is  x_i . x_j - n_j / 2 = -v_ij / 2.  Exactness: u8 / i8
+// values and the pieces are exact in BF16, every product is an integer, and for d <= 128 every
+// partial sum is a multiple of 1/2 below 2^23 in magnitude, so FP32 accumulation in any order is
+// exact and the picks equal those of the defining integer arithmetic.
 //
-// CTA layout (13 warps):
-//   warps 0-3  producers: gather the tile's rows from the BF16 copy of the points (16-byte
-//              loads), store them in the 128-byte-swizzled K-major layout the MMA descriptors
-//              describe, fence the async proxy, arrive on the stage's "full" barrier
-//   warp 4     allocates 512 TMEM columns; one thread issues tcgen05.mma (M=128, N<=256, K=16
-//              steps) into accumulator buffer t%2 and commits to "empty[stage]" / "tmem_full"
-//   warps 5-12 epilogue: tcgen05.ld 32 columns at a time, v = n_j - 2G (exact), per 32-column
-//              chunk a min filter against the row's current k-th best, exact (v, id) insertion;
-//              two warps share each TMEM lane quarter and split the columns, then merge
-// Every mbarrier wait is bounded by %globaltimer (2 s); on expiry the CTA records
-// DERR_TIMEOUT, stops all roles, and still frees its TMEM.
+// Persistent CTA (one per SM, 13 warps) over units (leaf, 128-row tile):
+//   warp 0     producer: TMA tiled loads (128 rows x 64 columns, 128-byte swizzle) of the A and B
+//              tiles from the leaf-ordered copy; B tiles also get the norm pieces (a 32-byte slice
+//              per stage) and a column-id list
+//   warp 1     owns TMEM; one thread issues tcgen05.mma M=128, N<=128, K=16 steps into one of four
+//              accumulator buffers and commits to the stage / accumulator barriers
+//   warps 2-9  epilogue: tcgen05.ld 32 columns at a time, two smallest per row (k = 2) or exact
+//              (v, id) insertion (k > 2); two warps share each TMEM lane quarter
+// Every mbarrier wait is bounded by %globaltimer (2 s); on expiry the CTA records DERR_TIMEOUT,
+// every role stops at the same points, and the TMEM is still released.
 #include "internal.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 namespace pipnn {
 
 namespace {
 
-constexpr int TC_PRODUCER_WARPS = 4;
-constexpr int TC_MMA_WARP = 4;
-constexpr int TC_EPI_WARP0 = 5;
+constexpr int TC_PRODUCER_WARP = 0;
+constexpr int TC_MMA_WARP = 1;
+constexpr int TC_EPI_WARP0 = 2;
 constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_THREADS = (TC_PRODUCER_WARPS + 1 + TC_EPI_WARPS) * 32;  // 416
+constexpr int TC_THREADS = (2 + TC_EPI_WARPS) * 32;  // 320
 constexpr int TC_ROWS = 128;
 constexpr uint32_t TC_TMEM_COLS = 512;
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
@@ -160,38 +164,61 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // ------------------------------------------------------------------ kernel
+struct TcUnit {
+    uint64_t off;   // first member of the leaf
+    uint32_t s;     // leaf size
+    uint32_t row0;  // first row of the tile
+};
+
 struct TcArgs {
-    const __nv_bfloat16 *Xb;     // n x Kp BF16 copy of the points (zero padded)
-    const int32_t *sqnorm;       // exact squared norms
-    const uint32_t *tile_grp, *tile_row0;
-    const uint64_t *leaf_off;
-    const uint32_t *members;
-    const uint64_t *cand_off;
+    const TcUnit *units;
+    const uint32_t *members;     // leaf members, ascending ids inside every leaf
+    const int32_t *member_norm;  // squared norm of every leaf member, in member order
+    const uint64_t *cand_off;    // per unit: first output slot of the unit's leaf
+    const uint32_t *unit_leaf;   // per unit: leaf index (for cand_off)
     uint32_t k;
     uint32_t *out_dst, *out_src;
     float *out_dist;
     unsigned *err;
 };
 
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// TMA tiled load of a 128-row x 64-column BF16 box at (x, y) into 16 KB of shared memory,
+// 128-byte swizzled -- the layout the MMA descriptors read.  Rows past the tensor read as zero.
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y,
+                                              uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
 template <int KB, int KMAX>
 struct TcCfg {
-    static constexpr int KP = 64 * KB;                       // padded K (elements)
-    static constexpr int NMAX = KB <= 2 ? 256 : 128;         // columns per B tile
-    static constexpr int A_REGION = TC_ROWS * 128;           // bytes per 64-wide K block of A
-    static constexpr int B_REGION = NMAX * 128;              // bytes per 64-wide K block of B
-    static constexpr int A_BYTES = A_REGION * KB;
-    static constexpr int B_BYTES = B_REGION * KB;
-    static constexpr int OFF_A = 0;
-    static constexpr int OFF_B0 = OFF_A + A_BYTES;
-    static constexpr int OFF_B1 = OFF_B0 + B_BYTES;
-    static constexpr int OFF_NB = OFF_B1 + B_BYTES;          // 2 x NMAX floats
-    static constexpr int OFF_GB = OFF_NB + 2 * NMAX * 4;     // 2 x NMAX ids
-    static constexpr int OFF_MV = OFF_GB + 2 * NMAX * 4;     // 128 rows x KMAX (v, id) merge buffer
+    static constexpr int NMAX = 128;                                     // columns per B tile
+    static constexpr int S = 3;                                          // B stages
+    static constexpr int T = 4;                                          // accumulator buffers
+    static constexpr int REGION = 128 * 128;                             // bytes per 64-wide K block, 128 rows
+    static constexpr int OFF_A0 = 0;                                     // A data, 2 buffers
+    static constexpr int OFF_AN = OFF_A0 + 2 * KB * REGION;              // A norm block (constant)
+    static constexpr int OFF_B0 = OFF_AN + REGION;                       // B data, S stages
+    static constexpr int OFF_BN = OFF_B0 + S * KB * REGION;              // B norm blocks (32-byte slice per stage)
+    static constexpr int OFF_CI = OFF_BN + REGION;                       // T x NMAX column ids
+    static constexpr int OFF_MV = OFF_CI + T * NMAX * 4;                 // 128 rows x KMAX (v, id)
     static constexpr int OFF_BAR = OFF_MV + TC_ROWS * KMAX * 8;
-    static constexpr int BAR_FULL_A = 0, BAR_FULL = 1, BAR_EMPTY = 3, BAR_TFULL = 5, BAR_TEMPTY = 7;
-    static constexpr int OFF_MISC = OFF_BAR + 9 * 8;         // tmem base, abort flag
+    static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = 2, BAR_FULL = 4, BAR_EMPTY = BAR_FULL + S,
+                         BAR_TFULL = BAR_EMPTY + S, BAR_TEMPTY = BAR_TFULL + T, BAR_CFULL = BAR_TEMPTY + T,
+                         NBAR = BAR_CFULL + T;
+    static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;                  // tmem base, abort flag
     static constexpr int BYTES = OFF_MISC + 16;
-    static constexpr int SMEM = BYTES + 1024;                // + alignment slack
+    static constexpr int SMEM = BYTES + 1024;                            // + alignment slack
+    static_assert(SMEM <= 232448, "shared memory budget");
+    static_assert(T * NMAX <= (int)TC_TMEM_COLS, "TMEM budget");
+    static_assert(S <= 4, "norm slices per 128-byte row");
 };
 
 template <int KMAX>
@@ -211,34 +238,37 @@ __device__ __forceinline__ void topk_insert(float (&kv)[KMAX], uint32_t (&ki)[KM
     }
 }
 
+// Persistent: CTA b processes units b, b + grid, ...; every role walks the same unit sequence.
+// B job j (one 128-column tile) uses B stage j % S (phase (j / S) % 2) and accumulator buffer /
+// column-id slot j % T (phase (j / T) % 2); unit i uses A buffer i % 2 (phase (i / 2) % 2).
 template <int KB, int KMAX>
-__global__ void __launch_bounds__(TC_THREADS, 1) leaf_gram_tc(const TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    leaf_gram_tc(const __grid_constant__ CUtensorMap map, const TcArgs a, uint32_t nunits) {
     using C = TcCfg<KB, KMAX>;
     extern __shared__ unsigned char tc_smem_raw[];
     unsigned char *smem =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(smem);
-    float *nbuf = reinterpret_cast<float *>(smem + C::OFF_NB);
-    uint32_t *gbuf = reinterpret_cast<uint32_t *>(smem + C::OFF_GB);
+    uint32_t *colid = reinterpret_cast<uint32_t *>(smem + C::OFF_CI);
     volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + C::OFF_MISC);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + C::OFF_MISC + 4);
     auto bar = [&](int i) { return sbase + C::OFF_BAR + 8 * i; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t g = a.tile_grp[blockIdx.x];
-    const uint32_t row0 = a.tile_row0[blockIdx.x];
-    const uint64_t off = a.leaf_off[g];
-    const uint32_t s = (uint32_t)(a.leaf_off[g + 1] - off);
-    const uint32_t nct = (s + C::NMAX - 1) / C::NMAX;  // column tiles
-    const uint32_t *mem = a.members + off;
 
     if (threadIdx.x == 0) {
-        mbar_init(bar(C::BAR_FULL_A), TC_PRODUCER_WARPS * 32);
         for (int i = 0; i < 2; i++) {
-            mbar_init(bar(C::BAR_FULL + i), TC_PRODUCER_WARPS * 32);
+            mbar_init(bar(C::BAR_FULL_A + i), 1);
+            mbar_init(bar(C::BAR_EMPTY_A + i), 1);
+        }
+        for (int i = 0; i < C::S; i++) {
+            mbar_init(bar(C::BAR_FULL + i), 32);
             mbar_init(bar(C::BAR_EMPTY + i), 1);
+        }
+        for (int i = 0; i < C::T; i++) {
             mbar_init(bar(C::BAR_TFULL + i), 1);
             mbar_init(bar(C::BAR_TEMPTY + i), TC_EPI_WARPS * 32);
+            mbar_init(bar(C::BAR_CFULL + i), 32);
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -256,178 +286,356 @@ __global__ void __launch_bounds__(TC_THREADS, 1) leaf_gram_tc(const TcArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < TC_PRODUCER_WARPS) {
-        // ---------------- producers
-        const int pt = threadIdx.x;  // 0..127
-        constexpr int CHUNKS = KB * 8;  // 16-byte chunks per row
-        auto load_rows = [&](uint32_t dst_base, int region, uint32_t first, uint32_t nrows_alloc) {
-            // rows r < nrows_alloc of the tile starting at member `first`; rows past the leaf
-            // repeat its first member (their columns / rows are masked later).  All of a
-            // thread's 16-byte copies are in flight at once (cp.async, L2 only); the thread
-            // waits for its own copies, then makes them visible to the tensor core's proxy.
-            for (uint32_t idx = pt; idx < nrows_alloc * CHUNKS; idx += TC_PRODUCER_WARPS * 32) {
-                const uint32_t r = idx / CHUNKS, c = idx % CHUNKS;
-                const uint32_t m = first + r < s ? mem[first + r] : mem[0];
-                const __nv_bfloat16 *src = a.Xb + (uint64_t)m * C::KP + c * 8;
-                const uint32_t kb = c >> 3, ch = c & 7;
-                const uint32_t addr = dst_base + kb * region + r * 128 + ((ch ^ (r & 7)) << 4);
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(addr), "l"(src) : "memory");
-            }
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            fence_proxy_async();
+    if (warp == TC_PRODUCER_WARP) {
+        // ------------------------------------------------------------ producer (one warp)
+        // A's norm block: [1, 1, 1, 1, 0, ...] in logical chunk 0 of every row, zeros in chunk 1
+        for (uint32_t r = lane; r < (uint32_t)TC_ROWS; r += 32) {
+            const uint32_t one = 0x3F80u;  // bf16 1.0
+            const uint32_t base = sbase + C::OFF_AN + r * 128;
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((0u ^ (r & 7)) << 4)),
+                         "r"(one | (one << 16)), "r"(one | (one << 16)), "r"(0u), "r"(0u)
+                         : "memory");
+            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((1u ^ (r & 7)) << 4)), "r"(0u),
+                         "r"(0u), "r"(0u), "r"(0u)
+                         : "memory");
+        }
+        fence_proxy_async();
+        // job stream: per unit one A job, then one B job per 128-column tile.  The member ids
+        // and norms of the next B job are loaded while the current one is issued.
+        struct Job {
+            uint32_t kind;  // 0 A, 1 B, 2 end
+            uint32_t i, u, t, s, first;
+            uint64_t off;
         };
-        load_rows(sbase + C::OFF_A, C::A_REGION, row0, TC_ROWS);
-        mbar_arrive(bar(C::BAR_FULL_A));
-        for (uint32_t t = 0; t < nct; t++) {
-            const uint32_t st = t & 1;
-            if (!mbar_wait(bar(C::BAR_EMPTY + st), ((t >> 1) & 1) ^ 1, abort, a.err)) break;
-            const uint32_t c0 = t * C::NMAX;
-            const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
-            const uint32_t nalloc = (ncols + 15) & ~15u;
-            load_rows(sbase + (st ? C::OFF_B1 : C::OFF_B0), C::B_REGION, c0, nalloc);
-            mbar_arrive(bar(C::BAR_FULL + st));
+        auto unit_job = [&](uint32_t i, uint32_t u) {
+            Job q;
+            if (u >= nunits) {
+                q.kind = 2;
+                return q;
+            }
+            const TcUnit un = a.units[u];
+            q.kind = 0;
+            q.i = i;
+            q.u = u;
+            q.t = 0;
+            q.s = un.s;
+            q.first = un.row0;
+            q.off = un.off;
+            return q;
+        };
+        auto next_job = [&](const Job &c) {
+            Job q = c;
+            if (c.kind == 0) {
+                q.kind = 1;
+                q.t = 0;
+                q.first = 0;
+                return q;
+            }
+            const uint32_t nct = (c.s + C::NMAX - 1) / C::NMAX;
+            if (c.t + 1 < nct) {
+                q.t = c.t + 1;
+                q.first = q.t * C::NMAX;
+                return q;
+            }
+            return unit_job(c.i + 1, c.u + gridDim.x);
+        };
+        auto load_ids = [&](const Job &q, uint32_t (&id)[4], int32_t (&nr)[4]) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const uint32_t r = q.first + 4 * lane + e;
+                const bool in = q.kind != 2 && r < q.s;
+                id[e] = (q.kind == 1 && in) ? a.members[q.off + r] : 0u;
+                nr[e] = (q.kind == 1 && in) ? a.member_norm[q.off + r] : 0;
+            }
+        };
+        Job cur = unit_job(0, blockIdx.x);
+        uint32_t id[4];
+        int32_t nr[4];
+        load_ids(cur, id, nr);
+        uint32_t j = 0;
+        while (cur.kind != 2) {
+            const Job nxt = next_job(cur);
+            uint32_t nid[4];
+            int32_t nnr[4];
+            load_ids(nxt, nid, nnr);
+            bool ok;
+            if (cur.kind == 0) {
+                const uint32_t ua = cur.i & 1;
+                ok = mbar_wait(bar(C::BAR_EMPTY_A + ua), ((cur.i >> 1) & 1) ^ 1, abort, a.err);
+                if (ok && lane == 0) {
+                    const uint32_t fb = bar(C::BAR_FULL_A + ua);
+                    mbar_arrive_tx(fb, KB * C::REGION);
+                    const uint32_t dst = sbase + C::OFF_A0 + ua * KB * C::REGION;
+#pragma unroll
+                    for (int kb = 0; kb < KB; kb++)
+                        tma_load_tile(dst + kb * C::REGION, &map, kb * 64, (int32_t)(cur.off + cur.first), fb);
+                }
+            } else {
+                const uint32_t st = j % C::S, tb = j % C::T;
+                ok = mbar_wait(bar(C::BAR_EMPTY + st), ((j / C::S) & 1) ^ 1, abort, a.err) &&
+                     mbar_wait(bar(C::BAR_TEMPTY + tb), ((j / C::T) & 1) ^ 1, abort, a.err);
+                if (ok) {
+                    uint32_t *ci = colid + tb * C::NMAX;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const uint32_t r = 4 * lane + e;
+                        const bool in = cur.first + r < cur.s;
+                        ci[r] = in ? id[e] : 0xFFFFFFFFu;
+                        // -(n_j / 2) as four BF16-exact pieces: the bytes of floor(n_j / 2) and
+                        // (n_j mod 2) / 2, in this stage's 32-byte slice (logical chunks 2 st, 2 st + 1)
+                        const uint32_t nj = in ? (uint32_t)nr[e] : 0u, hj = nj >> 1;
+                        const uint32_t b1 = __bfloat16_as_ushort(__float2bfloat16_rn(-(float)(hj & 0xFF0000u)));
+                        const uint32_t b2 = __bfloat16_as_ushort(__float2bfloat16_rn(-(float)(hj & 0x00FF00u)));
+                        const uint32_t b3 = __bfloat16_as_ushort(__float2bfloat16_rn(-(float)(hj & 0x0000FFu)));
+                        const uint32_t b4 = __bfloat16_as_ushort(__float2bfloat16_rn((nj & 1u) ? -0.5f : 0.0f));
+                        const uint32_t nb = sbase + C::OFF_BN + r * 128;
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st) ^ (r & 7)) << 4)),
+                                     "r"(b1 | (b2 << 16)), "r"(b3 | (b4 << 16)), "r"(0u), "r"(0u)
+                                     : "memory");
+                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st + 1) ^ (r & 7)) << 4)),
+                                     "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+                                     : "memory");
+                    }
+                    fence_proxy_async();
+                    mbar_arrive(bar(C::BAR_CFULL + tb));
+                    const uint32_t fb = bar(C::BAR_FULL + st);
+                    if (lane == 0) {
+                        mbar_arrive_tx(fb, KB * C::REGION);
+                        const uint32_t dst = sbase + C::OFF_B0 + st * KB * C::REGION;
+#pragma unroll
+                        for (int kb = 0; kb < KB; kb++)
+                            tma_load_tile(dst + kb * C::REGION, &map, kb * 64, (int32_t)(cur.off + cur.first), fb);
+                    } else {
+                        mbar_arrive(fb);
+                    }
+                }
+                j++;
+            }
+            if (!__all_sync(0xffffffffu, ok)) break;
+            cur = nxt;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                id[e] = nid[e];
+                nr[e] = nnr[e];
+            }
         }
     } else if (warp == TC_MMA_WARP) {
-        // ---------------- MMA issuer
+        // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            bool ok = mbar_wait(bar(C::BAR_FULL_A), 0, abort, a.err);
-            uint32_t issued = 0;
-            for (uint32_t t = 0; ok && t < nct; t++) {
-                const uint32_t st = t & 1;
-                if (!mbar_wait(bar(C::BAR_FULL + st), (t >> 1) & 1, abort, a.err)) break;
-                if (!mbar_wait(bar(C::BAR_TEMPTY + st), ((t >> 1) & 1) ^ 1, abort, a.err)) break;
-                tc_fence_after();
-                const uint32_t c0 = t * C::NMAX;
-                const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
-                const uint32_t N = (ncols + 15) & ~15u;
-                const uint32_t idesc = idesc_bf16(128, N);
-                const uint32_t aB = sbase + C::OFF_A, bB = sbase + (st ? C::OFF_B1 : C::OFF_B0);
+            uint32_t j = 0, issued_j = 0;
+            bool any = false, stop = false;
+            for (uint32_t i = 0, u = blockIdx.x; u < nunits && !stop; i++, u += gridDim.x) {
+                const uint32_t s = a.units[u].s;
+                const uint32_t ua = i & 1;
+                if (!mbar_wait(bar(C::BAR_FULL_A + ua), (i >> 1) & 1, abort, a.err)) break;
+                const uint32_t aB = sbase + C::OFF_A0 + ua * KB * C::REGION;
+                const uint32_t nct = (s + C::NMAX - 1) / C::NMAX;
+                for (uint32_t t = 0; t < nct; t++, j++) {
+                    const uint32_t st = j % C::S, tb = j % C::T;
+                    if (!mbar_wait(bar(C::BAR_FULL + st), (j / C::S) & 1, abort, a.err) ||
+                        !mbar_wait(bar(C::BAR_TEMPTY + tb), ((j / C::T) & 1) ^ 1, abort, a.err)) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t c0 = t * C::NMAX;
+                    const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
+                    const uint32_t idesc = idesc_bf16(128, (ncols + 15) & ~15u);
+                    const uint32_t bB = sbase + C::OFF_B0 + st * KB * C::REGION;
+                    const uint32_t d = tmem + tb * C::NMAX;
 #pragma unroll
-                for (int kk = 0; kk < KB * 4; kk++) {
-                    const uint64_t ad = smem_desc_sw128(aB + (kk >> 2) * C::A_REGION + (kk & 3) * 32);
-                    const uint64_t bd = smem_desc_sw128(bB + (kk >> 2) * C::B_REGION + (kk & 3) * 32);
-                    mma_bf16(tmem + st * C::NMAX, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    for (int kk = 0; kk < KB * 4; kk++) {
+                        const uint64_t ad = smem_desc_sw128(aB + (kk >> 2) * C::REGION + (kk & 3) * 32);
+                        const uint64_t bd = smem_desc_sw128(bB + (kk >> 2) * C::REGION + (kk & 3) * 32);
+                        mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    }
+                    // + n_j: ones x norm pieces (this stage's 32-byte slice)
+                    mma_bf16(d, smem_desc_sw128(sbase + C::OFF_AN), smem_desc_sw128(sbase + C::OFF_BN + st * 32),
+                             idesc, 1u);
+                    mma_commit(bar(C::BAR_EMPTY + st));
+                    mma_commit(bar(C::BAR_TFULL + tb));
+                    any = true;
+                    issued_j = j;
                 }
-                mma_commit(bar(C::BAR_EMPTY + st));
-                mma_commit(bar(C::BAR_TFULL + st));
-                issued = t + 1;
+                if (!stop) mma_commit(bar(C::BAR_EMPTY_A + ua));
             }
-            // on an early stop, let the last issued MMAs finish before TMEM is released
-            if (issued && issued < nct) mbar_wait(bar(C::BAR_TFULL + ((issued - 1) & 1)), ((issued - 1) >> 1) & 1, abort, a.err);
+            // after an early stop, let the issued MMAs drain before TMEM is released
+            if (stop && any)
+                mbar_wait(bar(C::BAR_TFULL + issued_j % C::T), (issued_j / C::T) & 1, abort, a.err);
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue
+        // ------------------------------------------------------------ epilogue
         const int ew = warp - TC_EPI_WARP0;          // 0..7
         const int half = ew >> 2;                    // which column chunks
         const int quarter = warp & 3;                // TMEM lane quarter this warp may access
         const uint32_t r = quarter * 32 + lane;      // row inside the tile
-        const uint32_t et = (uint32_t)(threadIdx.x - TC_EPI_WARP0 * 32);  // 0..255
-        const bool row_ok = row0 + r < s;
-        const uint32_t my_id = row_ok ? mem[row0 + r] : 0xFFFFFFFFu;
-        float kv[KMAX];
-        uint32_t ki[KMAX];
-#pragma unroll
-        for (int p = 0; p < KMAX; p++) {
-            kv[p] = __int_as_float(0x7f800000);
-            ki[p] = 0xFFFFFFFFu;
-        }
+        float2 *mv = reinterpret_cast<float2 *>(smem + C::OFF_MV);
+        uint32_t j = 0;
         bool failed = false;
-        for (uint32_t t = 0; t < nct; t++) {
-            const uint32_t st = t & 1;
-            const uint32_t c0 = t * C::NMAX;
-            if (et < (uint32_t)C::NMAX) {
-                const uint32_t col = c0 + et;
-                uint32_t gid = 0xFFFFFFFFu;
-                float nb = __int_as_float(0x7f800000);
-                if (col < s) {
-                    gid = mem[col];
-                    nb = (float)a.sqnorm[gid];
-                }
-                nbuf[st * C::NMAX + et] = nb;
-                gbuf[st * C::NMAX + et] = gid;
-            }
-            if (named_barrier_or(1, TC_EPI_WARPS * 32, failed || *abort)) {
-                failed = true;
-                break;
-            }
-            // warp-uniform wait: tcgen05.ld below is a warp-collective instruction
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_TFULL + st), (t >> 1) & 1, abort, a.err));
-            if (!ok) {
-                failed = true;
-                continue;
-            }
-            tc_fence_after();
-            const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
-            const float *nbt = nbuf + st * C::NMAX;
-            const uint32_t *gbt = gbuf + st * C::NMAX;
-            for (uint32_t q = half; q * 32 < ncols; q += 2) {
-                uint32_t gv[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + st * C::NMAX + q * 32, gv);
-                if (!row_ok) continue;
-                float v[32];
-                const float4 *n4 = reinterpret_cast<const float4 *>(nbt + q * 32);
+        for (uint32_t i = 0, u = blockIdx.x; u < nunits; i++, u += gridDim.x) {
+            const TcUnit un = a.units[u];
+            const uint64_t off = un.off;
+            const uint32_t s = un.s, row0 = un.row0;
+            const bool row_ok = row0 + r < s;
+            const uint32_t my_id = row_ok ? a.members[off + row0 + r] : 0xFFFFFFFFu;
+            float kv[KMAX];
+            uint32_t ki[KMAX];
 #pragma unroll
-                for (int j4 = 0; j4 < 8; j4++) {
-                    const float4 nn = n4[j4];
-                    v[4 * j4 + 0] = __fmaf_rn(-2.0f, __uint_as_float(gv[4 * j4 + 0]), nn.x);
-                    v[4 * j4 + 1] = __fmaf_rn(-2.0f, __uint_as_float(gv[4 * j4 + 1]), nn.y);
-                    v[4 * j4 + 2] = __fmaf_rn(-2.0f, __uint_as_float(gv[4 * j4 + 2]), nn.z);
-                    v[4 * j4 + 3] = __fmaf_rn(-2.0f, __uint_as_float(gv[4 * j4 + 3]), nn.w);
+            for (int p = 0; p < KMAX; p++) {
+                kv[p] = __int_as_float(0x7f800000);
+                ki[p] = 0xFFFFFFFFu;
+            }
+            const uint32_t nct = (s + C::NMAX - 1) / C::NMAX;
+            const uint32_t self_col = row0 + r;      // this row's own column inside the leaf
+            // k = 2: running two smallest (v, column) of this half, columns in increasing order
+            float R1 = __int_as_float(0x7f800000), R2 = R1;
+            uint32_t C1 = 0xFFFFFFFFu, C2 = 0xFFFFFFFFu;
+            for (uint32_t t = 0; t < nct; t++, j++) {
+                const uint32_t tb = j % C::T, ph = (j / C::T) & 1;
+                if (failed) continue;
+                // warp-uniform waits: tcgen05.ld below is a warp-collective instruction
+                const bool ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_TFULL + tb), ph, abort, a.err) &&
+                                                            mbar_wait(bar(C::BAR_CFULL + tb), ph, abort, a.err));
+                if (!ok) {
+                    failed = true;
+                    continue;
                 }
-                float m0 = fminf(fminf(v[0], v[1]), fminf(v[2], v[3]));
-                float m1 = fminf(fminf(v[4], v[5]), fminf(v[6], v[7]));
-                float m2 = fminf(fminf(v[8], v[9]), fminf(v[10], v[11]));
-                float m3 = fminf(fminf(v[12], v[13]), fminf(v[14], v[15]));
-                m0 = fminf(m0, fminf(fminf(v[16], v[17]), fminf(v[18], v[19])));
-                m1 = fminf(m1, fminf(fminf(v[20], v[21]), fminf(v[22], v[23])));
-                m2 = fminf(m2, fminf(fminf(v[24], v[25]), fminf(v[26], v[27])));
-                m3 = fminf(m3, fminf(fminf(v[28], v[29]), fminf(v[30], v[31])));
-                const float mn = fminf(fminf(m0, m1), fminf(m2, m3));
-                if (mn <= kv[KMAX - 1]) {
+                tc_fence_after();
+                const uint32_t c0 = t * C::NMAX;
+                const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
+                const uint32_t *info = colid + tb * C::NMAX;
+                for (uint32_t q = half; q * 32 < ncols; q += 2) {
+                    uint32_t gv[32];
+                    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX + q * 32, gv);
+                    if (!row_ok) continue;
+                    // the accumulator holds -v/2; rank by v/2 (same order, exact)
+                    float v[32];
 #pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        if (v[j] <= kv[KMAX - 1]) {
-                            const uint32_t id = gbt[q * 32 + j];
-                            if (id != my_id && id != 0xFFFFFFFFu) topk_insert<KMAX>(kv, ki, v[j], id);
+                    for (int jj = 0; jj < 32; jj++) v[jj] = -__uint_as_float(gv[jj]);
+                    const uint32_t base = c0 + q * 32;
+                    if constexpr (KMAX == 2) {
+                        // the row's own column and columns past the leaf never qualify
+                        if (self_col - base < 32u || base + 32 > s) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; jj++)
+                                if (base + jj == self_col || base + jj >= s) v[jj] = __int_as_float(0x7f800000);
+                        }
+                        // two smallest of the chunk: four independent in-order scans of 8, merged in
+                        // order; strict comparisons keep the earlier (smaller-id) column on ties
+                        float a1[4], a2[4];
+                        uint32_t i1[4], i2[4];
+#pragma unroll
+                        for (int ch = 0; ch < 4; ch++) {
+                            a1[ch] = __int_as_float(0x7f800000);
+                            a2[ch] = a1[ch];
+                            i1[ch] = 0;
+                            i2[ch] = 0;
+#pragma unroll
+                            for (int e = 0; e < 8; e++) {
+                                const float x = v[ch * 8 + e];
+                                const uint32_t xi = ch * 8 + e;
+                                const bool lt1 = x < a1[ch], lt2 = x < a2[ch];
+                                a2[ch] = lt1 ? a1[ch] : (lt2 ? x : a2[ch]);
+                                i2[ch] = lt1 ? i1[ch] : (lt2 ? xi : i2[ch]);
+                                a1[ch] = lt1 ? x : a1[ch];
+                                i1[ch] = lt1 ? xi : i1[ch];
+                            }
+                        }
+#pragma unroll
+                        for (int ch = 1; ch < 4; ch++) {
+                            // merge chain ch (later columns) into chain 0
+                            if (a1[ch] < a1[0]) {
+                                const bool b = a2[ch] < a1[0];
+                                a2[0] = b ? a2[ch] : a1[0];
+                                i2[0] = b ? i2[ch] : i1[0];
+                                a1[0] = a1[ch];
+                                i1[0] = i1[ch];
+                            } else if (a1[ch] < a2[0]) {
+                                a2[0] = a1[ch];
+                                i2[0] = i1[ch];
+                            }
+                        }
+                        // merge the chunk into the running pair (running columns come first)
+                        if (a1[0] < R2) {
+                            if (a1[0] < R1) {
+                                const bool b = a2[0] < R1;
+                                R2 = b ? a2[0] : R1;
+                                C2 = b ? base + i2[0] : C1;
+                                R1 = a1[0];
+                                C1 = base + i1[0];
+                            } else {
+                                R2 = a1[0];
+                                C2 = base + i1[0];
+                            }
+                        }
+                        continue;
+                    }
+                    float m0 = fminf(fminf(v[0], v[1]), fminf(v[2], v[3]));
+                    float m1 = fminf(fminf(v[4], v[5]), fminf(v[6], v[7]));
+                    float m2 = fminf(fminf(v[8], v[9]), fminf(v[10], v[11]));
+                    float m3 = fminf(fminf(v[12], v[13]), fminf(v[14], v[15]));
+                    m0 = fminf(m0, fminf(fminf(v[16], v[17]), fminf(v[18], v[19])));
+                    m1 = fminf(m1, fminf(fminf(v[20], v[21]), fminf(v[22], v[23])));
+                    m2 = fminf(m2, fminf(fminf(v[24], v[25]), fminf(v[26], v[27])));
+                    m3 = fminf(m3, fminf(fminf(v[28], v[29]), fminf(v[30], v[31])));
+                    const float mn = fminf(fminf(m0, m1), fminf(m2, m3));
+                    if (mn <= kv[KMAX - 1]) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj++) {
+                            if (v[jj] <= kv[KMAX - 1]) {
+                                const uint32_t id = info[q * 32 + jj];
+                                if (id != my_id && id != 0xFFFFFFFFu) topk_insert<KMAX>(kv, ki, v[jj], id);
+                            }
                         }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(bar(C::BAR_TEMPTY + tb));
             }
-            tc_fence_before();
-            mbar_arrive(bar(C::BAR_TEMPTY + st));
-        }
-        // merge the two halves of each row
-        float2 *mv = reinterpret_cast<float2 *>(smem + C::OFF_MV);
-        if (half == 1) {
-#pragma unroll
-            for (int p = 0; p < KMAX; p++) mv[r * KMAX + p] = make_float2(kv[p], __uint_as_float(ki[p]));
-        }
-        failed = named_barrier_or(1, TC_EPI_WARPS * 32, failed || *abort);
-        if (half == 0 && row_ok && !failed) {
-#pragma unroll
-            for (int p = 0; p < KMAX; p++) {
-                const float2 e = mv[r * KMAX + p];
-                const uint32_t id = __float_as_uint(e.y);
-                if (id != 0xFFFFFFFFu) topk_insert<KMAX>(kv, ki, e.x, id);
+            if constexpr (KMAX == 2) {
+                // columns -> member ids (the leaf's members are in ascending id order)
+                kv[0] = R1;
+                ki[0] = C1 < s ? a.members[off + C1] : 0xFFFFFFFFu;
+                kv[1] = R2;
+                ki[1] = C2 < s ? a.members[off + C2] : 0xFFFFFFFFu;
+                if (ki[0] == 0xFFFFFFFFu) kv[0] = __int_as_float(0x7f800000);
+                if (ki[1] == 0xFFFFFFFFu) kv[1] = __int_as_float(0x7f800000);
             }
-            const uint32_t kk = s - 1 < a.k ? s - 1 : a.k;
-            const float ni = (float)a.sqnorm[my_id];
-            uint64_t w = a.cand_off[g] + (uint64_t)(row0 + r) * 2 * kk;
+            // merge the two halves of each row, then emit
+            if (half == 1) {
 #pragma unroll
-            for (int p = 0; p < KMAX; p++) {
-                if ((uint32_t)p < kk) {
-                    const uint32_t src = ki[p] == 0xFFFFFFFFu ? my_id : ki[p];
-                    const float D = __fadd_rn(ni, kv[p]);
-                    a.out_dst[w] = my_id;
-                    a.out_src[w] = src;
-                    a.out_dist[w] = D;
-                    a.out_dst[w + 1] = src;
-                    a.out_src[w + 1] = my_id;
-                    a.out_dist[w + 1] = D;
-                    w += 2;
+                for (int p = 0; p < KMAX; p++) mv[r * KMAX + p] = make_float2(kv[p], __uint_as_float(ki[p]));
+            }
+            failed = named_barrier_or(1, TC_EPI_WARPS * 32, failed || *abort);
+            if (half == 0 && row_ok && !failed) {
+#pragma unroll
+                for (int p = 0; p < KMAX; p++) {
+                    const float2 e = mv[r * KMAX + p];
+                    const uint32_t id = __float_as_uint(e.y);
+                    if (id != 0xFFFFFFFFu) topk_insert<KMAX>(kv, ki, e.x, id);
+                }
+                const uint32_t kk = s - 1 < a.k ? s - 1 : a.k;
+                const float ni = (float)a.member_norm[off + row0 + r];
+                uint64_t w = a.cand_off[a.unit_leaf[u]] + (uint64_t)(row0 + r) * 2 * kk;
+#pragma unroll
+                for (int p = 0; p < KMAX; p++) {
+                    if ((uint32_t)p < kk) {
+                        const uint32_t src = ki[p] == 0xFFFFFFFFu ? my_id : ki[p];
+                        const float D = __fadd_rn(ni, __fmul_rn(2.0f, kv[p]));
+                        a.out_dst[w] = my_id;
+                        a.out_src[w] = src;
+                        a.out_dist[w] = D;
+                        a.out_dst[w + 1] = src;
+                        a.out_src[w + 1] = my_id;
+                        a.out_dist[w + 1] = D;
+                        w += 2;
+                    }
                 }
             }
+            // mv is rewritten by the next unit only after every reader is done
+            failed = named_barrier_or(1, TC_EPI_WARPS * 32, failed || *abort);
+            if (failed) break;
         }
     }
 
@@ -440,42 +648,142 @@ __global__ void __launch_bounds__(TC_THREADS, 1) leaf_gram_tc(const TcArgs a) {
     }
 }
 
-__global__ void to_bf16_padded(const void *X, uint64_t n, uint32_t d, uint32_t kp, int dtype, __nv_bfloat16 *out) {
-    const uint64_t total = n * kp;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t p = i / kp;
-        const uint32_t t = (uint32_t)(i % kp);
-        float v = 0.0f;
-        if (t < d) {
-            v = dtype == PIPNN_U8 ? (float)static_cast<const uint8_t *>(X)[p * d + t]
-                                  : (float)static_cast<const int8_t *>(X)[p * d + t];
+__global__ void build_units(const uint32_t *tile_grp, const uint32_t *tile_row0, uint64_t nunits,
+                            const uint64_t *leaf_off, TcUnit *units) {
+    for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < nunits; u += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t g = tile_grp[u];
+        TcUnit x;
+        x.off = leaf_off[g];
+        x.s = (uint32_t)(leaf_off[g + 1] - x.off);
+        x.row0 = tile_row0[u];
+        units[u] = x;
+    }
+}
+
+// Sorts every leaf's members ascending, one block per leaf in shared memory (leaves of up to
+// TC_MAX_LEAF members; the host rejects larger ones).
+constexpr uint32_t TC_MAX_LEAF = 4096;
+
+__global__ void __launch_bounds__(1024) sort_leaf_members(const uint64_t *off, uint64_t L, uint32_t *mem) {
+    __shared__ uint32_t sh[TC_MAX_LEAF];
+    for (uint64_t b = blockIdx.x; b < L; b += gridDim.x) {
+        const uint64_t o = off[b];
+        const uint32_t n = (uint32_t)(off[b + 1] - o);
+        if (n < 2 || n > TC_MAX_LEAF) continue;
+        uint32_t P = 1;
+        while (P < n) P <<= 1;
+        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < n ? mem[o + i] : 0xFFFFFFFFu;
+        __syncthreads();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+                    const uint32_t ixj = i ^ jj;
+                    if (ixj > i) {
+                        const uint32_t x = sh[i], y = sh[ixj];
+                        const bool asc = (i & k) == 0;
+                        if ((x > y) == asc) {
+                            sh[i] = y;
+                            sh[ixj] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
         }
-        out[i] = __float2bfloat16_rn(v);
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) mem[o + i] = sh[i];
+        __syncthreads();
+    }
+}
+
+__global__ void max_leaf_size(const uint32_t *size, uint64_t L, unsigned *out) {
+    unsigned m = 0;
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < L; b += (uint64_t)gridDim.x * blockDim.x)
+        m = size[b] > m ? size[b] : m;
+    atomicMax(out, m);
+}
+
+__global__ void member_norms(const uint32_t *members, uint64_t M, const int32_t *sqnorm, int32_t *out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < M; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = sqnorm[members[i]];
+}
+
+// Leaf-ordered BF16 copy of the members' rows, zero padded to kp columns (exact for byte data):
+// row i holds the point members[i].
+__global__ void stage_rows(const void *X, uint32_t d, uint32_t kp, int dtype, const uint32_t *members, uint64_t M,
+                           __nv_bfloat16 *out) {
+    const uint32_t per_row = kp / 8;  // 16-byte output chunks per row
+    const uint64_t total = M * per_row;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t row = i / per_row;
+        const uint32_t c = (uint32_t)(i % per_row);
+        const uint64_t src = (uint64_t)members[row] * d;
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            float lo = 0.0f, hi = 0.0f;
+            const uint32_t t = c * 8 + 2 * h;
+            if (t < d) lo = dtype == PIPNN_U8 ? (float)static_cast<const uint8_t *>(X)[src + t]
+                                              : (float)static_cast<const int8_t *>(X)[src + t];
+            if (t + 1 < d) hi = dtype == PIPNN_U8 ? (float)static_cast<const uint8_t *>(X)[src + t + 1]
+                                                  : (float)static_cast<const int8_t *>(X)[src + t + 1];
+            w[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+        }
+        reinterpret_cast<uint4 *>(out)[i] = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
 template <int KB, int KMAX>
-int launch_tc(const TcArgs &args, uint64_t ntiles) {
+int launch_tc(const CUtensorMap &map, const TcArgs &args, uint64_t ntiles) {
     using C = TcCfg<KB, KMAX>;
     auto kern = leaf_gram_tc<KB, KMAX>;
     PIPNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-    for (uint64_t t0 = 0; t0 < ntiles; t0 += 0x7FFFFFFFull) {
-        const uint64_t cnt = ntiles - t0 < 0x7FFFFFFFull ? ntiles - t0 : 0x7FFFFFFFull;
+    int dev = 0, sms = 0;
+    PIPNN_CUDA(cudaGetDevice(&dev));
+    PIPNN_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (uint64_t t0 = 0; t0 < ntiles; t0 += 0xFFFFFFFFull) {
+        const uint64_t cnt = ntiles - t0 < 0xFFFFFFFFull ? ntiles - t0 : 0xFFFFFFFFull;
         TcArgs a = args;
-        a.tile_grp += t0;
-        a.tile_row0 += t0;
-        kern<<<(unsigned)cnt, TC_THREADS, C::SMEM, stream()>>>(a);
+        a.units += t0;
+        a.unit_leaf += t0;
+        const unsigned grid = (unsigned)(cnt < (uint64_t)sms ? cnt : (uint64_t)sms);
+        kern<<<grid, TC_THREADS, C::SMEM, stream()>>>(map, a, (uint32_t)cnt);
         PIPNN_LAUNCH_CHECK();
     }
     return PIPNN_OK;
 }
 
 template <int KB>
-int launch_tc_k(const TcArgs &args, uint64_t ntiles, uint32_t k) {
-    if (k <= 2) return launch_tc<KB, 2>(args, ntiles);
-    if (k <= 4) return launch_tc<KB, 4>(args, ntiles);
-    if (k <= 8) return launch_tc<KB, 8>(args, ntiles);
-    return launch_tc<KB, 16>(args, ntiles);
+int launch_tc_k(const CUtensorMap &map, const TcArgs &args, uint64_t ntiles, uint32_t k) {
+    if (k <= 2) return launch_tc<KB, 2>(map, args, ntiles);
+    if (k <= 4) return launch_tc<KB, 4>(map, args, ntiles);
+    if (k <= 8) return launch_tc<KB, 8>(map, args, ntiles);
+    return launch_tc<KB, 16>(map, args, ntiles);
+}
+
+// Tensor map over an n x kp BF16 matrix: boxes of 128 rows x 64 columns, 128-byte swizzle.
+int encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *base, uint64_t n, uint32_t kp) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            !fn) {
+            cudaGetLastError();
+            return set_error(PIPNN_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t gdim[2] = {kp, n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)kp * 2};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult rc = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), gdim,
+                               gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rc != CUDA_SUCCESS) return set_error(PIPNN_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)rc);
+    return PIPNN_OK;
 }
 }  // namespace
 
@@ -484,24 +792,60 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
                  uint32_t *out_dst, uint32_t *out_src, float *out_dist, Workspace &ws, cudaEvent_t ev0,
                  cudaEvent_t ev1, uint32_t *launches) {
     if (dtype == PIPNN_F32) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes byte data only");
-    if (d > 256) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine is exact for d <= 256");
+    if (d > 128) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine is exact for d <= 128");
     if (k > 16) return set_error(PIPNN_EINVAL, "k above 16");
     const uint32_t kb = (d + 63) / 64;
     const uint32_t kp = kb * 64;
-    __nv_bfloat16 *Xb = nullptr;
-    PIPNN_TRY(ws.alloc(&Xb, n * kp));
-    to_bf16_padded<<<grid_for(n * kp, 256), 256, 0, stream()>>>(X, n, d, kp, dtype, Xb);
-    PIPNN_LAUNCH_CHECK();
+    uint64_t M = 0;
+    PIPNN_TRY(read_u64(off + L, &M));
+    if (L) {
+        unsigned *mx = nullptr, hmx = 0;
+        PIPNN_TRY(ws.zeros(&mx, 1));
+        max_leaf_size<<<grid_for(L, 256, 1024), 256, 0, stream()>>>(leaf_size, L, mx);
+        PIPNN_LAUNCH_CHECK();
+        PIPNN_CUDA(cudaMemcpyAsync(&hmx, mx, 4, cudaMemcpyDeviceToHost, stream()));
+        PIPNN_CUDA(cudaStreamSynchronize(stream()));
+        if (hmx > TC_MAX_LEAF)
+            return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes leaves of at most %u members",
+                             TC_MAX_LEAF);
+    }
+    // a copy of the members with every leaf in ascending id order: column order is then id order,
+    // which is the tie order of (D, id)
+    uint32_t *smem_members = nullptr;
+    PIPNN_TRY(ws.alloc(&smem_members, M));
+    int32_t *mnorm = nullptr;
+    PIPNN_TRY(ws.alloc(&mnorm, M));
+    if (M) {
+        PIPNN_CUDA(cudaMemcpyAsync(smem_members, mem, M * 4, cudaMemcpyDeviceToDevice, stream()));
+        sort_leaf_members<<<grid_for(L, 1, 152u * 16u), 1024, 0, stream()>>>(off, L, smem_members);
+        PIPNN_LAUNCH_CHECK();
+        mem = smem_members;
+        member_norms<<<grid_for(M, 256), 256, 0, stream()>>>(mem, M, sqnorm, mnorm);
+        PIPNN_LAUNCH_CHECK();
+    }
+    if (M >= 0x7FFFFF00ull) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes < 2^31 leaf members");
+    __nv_bfloat16 *staged = nullptr;
+    PIPNN_TRY(ws.alloc(&staged, (M ? M : 1) * kp));
+    if (M) {
+        stage_rows<<<grid_for(M * (kp / 8), 256), 256, 0, stream()>>>(X, d, kp, dtype, mem, M, staged);
+        PIPNN_LAUNCH_CHECK();
+    }
     uint32_t *tile_grp = nullptr, *tile_row0 = nullptr;
     uint64_t ntiles = 0;
     PIPNN_TRY(make_tiles(leaf_size, L, TC_ROWS, &tile_grp, &tile_row0, &ntiles, ws));
+    TcUnit *units = nullptr;
+    PIPNN_TRY(ws.alloc(&units, ntiles));
+    if (ntiles) {
+        build_units<<<grid_for(ntiles, 256), 256, 0, stream()>>>(tile_grp, tile_row0, ntiles, off, units);
+        PIPNN_LAUNCH_CHECK();
+    }
+    CUtensorMap map;
+    PIPNN_TRY(encode_rows_map(&map, staged, M ? M : 1, kp));
     TcArgs a{};
-    a.Xb = Xb;
-    a.sqnorm = sqnorm;
-    a.tile_grp = tile_grp;
-    a.tile_row0 = tile_row0;
-    a.leaf_off = off;
+    a.units = units;
+    a.unit_leaf = tile_grp;
     a.members = mem;
+    a.member_norm = mnorm;
     a.cand_off = cand_off;
     a.k = k;
     a.out_dst = out_dst;
@@ -512,12 +856,8 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
     if (ntiles == 0) return PIPNN_OK;
     cudaEventRecord(ev0, stream());
     int rc;
-    switch (kb) {
-    case 1: rc = launch_tc_k<1>(a, ntiles, k); break;
-    case 2: rc = launch_tc_k<2>(a, ntiles, k); break;
-    case 3: rc = launch_tc_k<3>(a, ntiles, k); break;
-    default: rc = launch_tc_k<4>(a, ntiles, k); break;
-    }
+    if (kb == 1) rc = launch_tc_k<1>(map, a, ntiles, k);
+    else rc = launch_tc_k<2>(map, a, ntiles, k);
     cudaEventRecord(ev1, stream());
     *launches = 1;
     return rc;

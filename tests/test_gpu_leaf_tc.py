@@ -1,9 +1,10 @@
 """The tcgen05 tensor-core leaf engine (byte data) against the oracle: identical candidate edges.
 
-BF16 holds every u8 / i8 value exactly and, for d <= 256, every product, partial sum and
-dissimilarity formed from them is an integer below 2^24, so the tensor-core Gram is exact and the
-picks must equal the oracle's integer picks bit for bit -- including extreme values (all 255,
-int8 -128) and leaves whose size is not a multiple of the 128-row / 256-column tiles."""
+BF16 holds every u8 / i8 value, -2x and the byte-wide pieces of a squared norm exactly and, for
+d <= 128, every partial sum of the accumulated n_j - 2<x_i, x_j> is an integer below 2^24, so the
+tensor-core result is exact and the picks must equal the oracle's integer picks bit for bit --
+including extreme values (all 255, int8 -128) and leaves whose size is not a multiple of the
+128-row / 128-column tiles."""
 import numpy as np
 import pytest
 
@@ -79,11 +80,21 @@ def test_tc_pick_extreme_values_exact(kind):
     check(X, off, mem, 2)
 
 
-@pytest.mark.parametrize("d", [8, 64, 100, 192, 256])
-def test_tc_pick_dimensions(d):
-    X = synth.mixture(6000, d, synth.I8 if d % 2 else synth.U8, 30, 10.0, seed=56 + d)
+@pytest.mark.parametrize("d,dtype", [(8, synth.U8), (64, synth.I8), (100, synth.I8), (100, synth.U8),
+                                     (127, synth.U8), (128, synth.I8)])
+def test_tc_pick_dimensions(d, dtype):
+    X = synth.mixture(6000, d, dtype, 30, 10.0, seed=56 + d)
     off, mem = random_leaves(6000, [2048, 777, 300, 64, 1], seed=d)
     check(X, off, mem, 2)
+
+
+def test_tc_engine_rejects_d_beyond_exactness_bound():
+    X = dev(synth.uniform_points(300, 129, synth.U8, seed=59))
+    off = dev(np.array([0, 300], np.uint64))
+    mem = dev(np.arange(300, dtype=np.uint32))
+    with pytest.raises(pk.PipnnError) as e:
+        pk.pipnn_leaf_pick(X, off, mem, k=2, engine=pk.PIPNN_LEAF_TC)
+    assert e.value.code == -5
 
 
 @pytest.mark.parametrize("dtype", [synth.U8, synth.I8])
