@@ -19,6 +19,7 @@ enum { MODE_ASSIGN = 0, MODE_PICK = 1 };
 
 constexpr int AP_ROWS = 128;   // rows per block (one per thread)
 constexpr int AP_COLS = 32;    // columns per shared-memory tile
+constexpr int AP_PREFETCH = 8; // 16-byte column chunks each thread keeps in flight (rows <= 512 B)
 
 struct AllPairsArgs {
     const void *X;
@@ -89,7 +90,7 @@ __device__ __forceinline__ int dot4(uint32_t a, uint32_t b, int acc) {
 // Shared memory words needed per block.
 inline size_t allpairs_smem_bytes(int dtype, uint32_t d) {
     size_t dw = dtype == PIPNN_F32 ? d : (d + 3) / 4;
-    return (size_t)(AP_ROWS + AP_COLS) * dw * 4;
+    return (size_t)(AP_ROWS + AP_COLS) * dw * 4 + 2 * AP_COLS * 4;
 }
 
 template <int DT, int MET, int KMAX, int MODE>
@@ -99,6 +100,8 @@ __global__ void __launch_bounds__(AP_ROWS) allpairs_topk(AllPairsArgs a) {
     const uint32_t dw = DT == PIPNN_F32 ? d : (d + 3) / 4;
     uint32_t *Rs = smem;                       // [dw][AP_ROWS]
     uint32_t *Cs = smem + (size_t)dw * AP_ROWS;  // [dw][AP_COLS]
+    uint32_t *Cid = Cs + (size_t)dw * AP_COLS;   // column ids of the tile
+    int *Cn = reinterpret_cast<int *>(Cid + AP_COLS);  // their exact squared norms (byte data)
 
     const uint32_t g = a.tile_grp[blockIdx.x];
     const uint32_t row0 = a.tile_row0[blockIdx.x];
@@ -138,10 +141,63 @@ __global__ void __launch_bounds__(AP_ROWS) allpairs_topk(AllPairsArgs a) {
 #pragma unroll
     for (int p = 0; p < KMAX; p++) kv[p] = ~0ull;
 
+    // Column tiles: rows that are whole 16-byte chunks are fetched as uint4, and the next tile's
+    // chunks are in flight while the current tile is consumed.
+    const uint32_t row_bytes = DT == PIPNN_F32 ? d * 4 : d;
+    const uint32_t nch = row_bytes / 16;                       // chunks per column row
+    const bool vec = row_bytes % 16 == 0 && nch * AP_COLS <= AP_PREFETCH * AP_ROWS;
+    uint4 pre[AP_PREFETCH];
+    uint32_t pre_id = 0xFFFFFFFFu;
+    int pre_n = 0;
+    auto fetch_info = [&](uint32_t c0) {
+        if (tid < AP_COLS) {
+            pre_id = c0 + tid < ncols ? col_ids[c0 + tid] : 0xFFFFFFFFu;
+            pre_n = (DT != PIPNN_F32 && pre_id != 0xFFFFFFFFu) ? a.sqnorm[pre_id] : 0;
+        }
+    };
+    auto fetch = [&](uint32_t c0) {
+#pragma unroll
+        for (int u = 0; u < AP_PREFETCH; u++) {
+            const uint32_t idx = u * AP_ROWS + tid;
+            pre[u] = make_uint4(0, 0, 0, 0);
+            if (idx < nch * AP_COLS) {
+                const uint32_t c = idx / nch, ch = idx - c * nch;
+                if (c0 + c < ncols) {
+                    const uint32_t cid = col_ids[c0 + c];
+                    pre[u] = __ldg(reinterpret_cast<const uint4 *>(static_cast<const char *>(a.X) +
+                                                                   (uint64_t)cid * row_bytes) + ch);
+                }
+            }
+        }
+    };
+    if (vec && ncols) fetch(0);
+    if (ncols) fetch_info(0);
     for (uint32_t c0 = 0; c0 < ncols; c0 += AP_COLS) {
         __syncthreads();  // previous column tile fully consumed (and row tile written)
-        // column tile: thread (tid % 32) owns column c0 + tid%32, strides over words by 4
-        {
+        if (tid < AP_COLS) {
+            Cid[tid] = pre_id;
+            Cn[tid] = pre_n;
+        }
+        if (c0 + AP_COLS < ncols && !vec) fetch_info(c0 + AP_COLS);
+        if (vec) {
+#pragma unroll
+            for (int u = 0; u < AP_PREFETCH; u++) {
+                const uint32_t idx = u * AP_ROWS + tid;
+                if (idx < nch * AP_COLS) {
+                    const uint32_t c = idx / nch, w0 = (idx - c * nch) * 4;
+                    Cs[(size_t)(w0 + 0) * AP_COLS + c] = pre[u].x;
+                    Cs[(size_t)(w0 + 1) * AP_COLS + c] = pre[u].y;
+                    Cs[(size_t)(w0 + 2) * AP_COLS + c] = pre[u].z;
+                    Cs[(size_t)(w0 + 3) * AP_COLS + c] = pre[u].w;
+                }
+            }
+            __syncthreads();
+            if (c0 + AP_COLS < ncols) {
+                fetch(c0 + AP_COLS);
+                fetch_info(c0 + AP_COLS);
+            }
+        } else {
+            // thread (tid % 32) owns column c0 + tid%32, strides over words by 4
             const uint32_t c = tid % AP_COLS;
             const uint32_t cc = c0 + c;
             const bool ok = cc < ncols;
@@ -154,8 +210,8 @@ __global__ void __launch_bounds__(AP_ROWS) allpairs_topk(AllPairsArgs a) {
                 }
                 Cs[(size_t)w * AP_COLS + c] = v;
             }
+            __syncthreads();
         }
-        __syncthreads();
         if (!row_ok) continue;
 
         if (DT == PIPNN_F32) {
@@ -188,7 +244,7 @@ __global__ void __launch_bounds__(AP_ROWS) allpairs_topk(AllPairsArgs a) {
                 const uint32_t cc = c0 + c;
                 if (cc < ncols) {
                     float D = MET == PIPNN_L2 ? acc[c] : __fsub_rn(1.0f, acc[c]);
-                    uint32_t pay = MODE == MODE_ASSIGN ? cc : col_ids[cc];
+                    uint32_t pay = MODE == MODE_ASSIGN ? cc : Cid[c];
                     if (MODE == MODE_PICK && pay == my_id) continue;
                     topk_insert<KMAX>(kv, ((uint64_t)f32_order(D) << 32) | pay);
                 }
@@ -213,9 +269,9 @@ __global__ void __launch_bounds__(AP_ROWS) allpairs_topk(AllPairsArgs a) {
             for (int c = 0; c < AP_COLS; c++) {
                 const uint32_t cc = c0 + c;
                 if (cc < ncols) {
-                    const uint32_t cid = col_ids[cc];
+                    const uint32_t cid = Cid[c];
                     if (MODE == MODE_PICK && cid == my_id) continue;
-                    int D = my_norm + a.sqnorm[cid] - 2 * acc[c];
+                    int D = my_norm + Cn[c] - 2 * acc[c];
                     uint32_t pay = MODE == MODE_ASSIGN ? cc : cid;
                     topk_insert<KMAX>(kv, ((uint64_t)(uint32_t)D << 32) | pay);
                 }

@@ -151,12 +151,15 @@ __global__ void __launch_bounds__(PR_WARPS * 32) robust_prune(const void *X, uin
     }
 }
 
-// Shared-memory variant: the node's candidate rows (and its own) are staged once per node with
-// coalesced row loads (row stride dw+1 words, so lanes reading different rows hit different
-// banks); keys (D(x,c), id) are sorted with the slot as payload and every D(y,z) of the prune
-// loop reads shared memory only.  Same arithmetic and order as robust_prune.
+// Shared-memory variant: the node's candidate rows (and its own) are staged once per node --
+// with 16-byte cp.async copies all in flight when a row is a whole number of 16-byte chunks,
+// else with word loads -- into rows whose 16-byte chunks are XOR-swizzled by row index (lanes
+// reading different rows then hit different banks); keys (D(x,c), id) are sorted with the slot as
+// payload and every D(y,z) of the prune loop reads shared memory only.  Same arithmetic and
+// order as robust_prune.
 struct PruneSmem {
-    uint32_t dw, lmax, P;
+    uint32_t dw, lmax, P, stride, smask;
+    bool async16;
     size_t rows, keys, perm, dx, nz, alive, per_warp;
 };
 
@@ -166,9 +169,15 @@ __host__ __device__ inline PruneSmem prune_smem_layout(int dtype, uint32_t d, ui
     L.lmax = l_max;
     L.P = 32;
     while (L.P < l_max) L.P <<= 1;
+    const uint32_t row_bytes = dtype == PIPNN_F32 ? d * 4 : d;
+    L.async16 = row_bytes % 16 == 0;
+    L.stride = (L.dw + 3) & ~3u;                 // words per staged row (whole 16-byte chunks)
+    const uint32_t nch = L.stride / 4;
+    // the XOR must keep every chunk inside its row: full groups of 8 chunks, or a power of two
+    L.smask = nch % 8 == 0 ? 7u : ((nch & (nch - 1)) == 0 ? nch - 1 : 0u);
     size_t o = 0;
     L.rows = o;
-    o += (size_t)(l_max + 1) * (L.dw + 1) * 4;
+    o += (size_t)(l_max + 1) * L.stride * 4;
     o = (o + 7) & ~(size_t)7;
     L.keys = o;
     o += (size_t)L.P * 8;
@@ -185,29 +194,59 @@ __host__ __device__ inline PruneSmem prune_smem_layout(int dtype, uint32_t d, ui
     return L;
 }
 
+// word w of a staged row sits at w ^ (xor_a << 2) (chunk index XOR-swizzled by row)
 template <int DT, int MET>
-__device__ __forceinline__ void dis_smem(const uint32_t *ra, const uint32_t *rb, uint32_t dw, int na, int nb,
-                                         uint32_t &key, float &val) {
+__device__ __forceinline__ void dis_smem(const uint32_t *ra, uint32_t xa, const uint32_t *rb, uint32_t xb,
+                                         uint32_t dw, int na, int nb, uint32_t &key, float &val) {
+    xa <<= 2;
+    xb <<= 2;
     if (DT == PIPNN_F32) {
         float acc = 0.0f;
         if (MET == PIPNN_L2) {
             for (uint32_t t = 0; t < dw; t++) {
-                const float df = __fsub_rn(__uint_as_float(ra[t]), __uint_as_float(rb[t]));
+                const float df = __fsub_rn(__uint_as_float(ra[t ^ xa]), __uint_as_float(rb[t ^ xb]));
                 acc = __fmaf_rn(df, df, acc);
             }
         } else {
-            for (uint32_t t = 0; t < dw; t++) acc = __fmaf_rn(__uint_as_float(ra[t]), __uint_as_float(rb[t]), acc);
+            for (uint32_t t = 0; t < dw; t++)
+                acc = __fmaf_rn(__uint_as_float(ra[t ^ xa]), __uint_as_float(rb[t ^ xb]), acc);
             acc = __fsub_rn(1.0f, acc);
         }
         key = f32_order(acc);
         val = acc;
     } else {
         int dot = 0;
-        for (uint32_t w = 0; w < dw; w++) dot = dot4<DT>(ra[w], rb[w], dot);
+        for (uint32_t w = 0; w < dw; w++) dot = dot4<DT>(ra[w ^ xa], rb[w ^ xb], dot);
         const int D = na + nb - 2 * dot;
         key = (uint32_t)D;
         val = __int2float_rn(D);
     }
+}
+
+// Byte data with staged rows of at most 8 chunks (d <= 128): one operand's row in registers,
+// the other read with 16-byte shared loads, four independent integer partial sums (exact in any
+// order).
+template <int DT>
+__device__ __forceinline__ void row_to_regs(const uint32_t *row, uint32_t x, uint32_t nch, uint4 (&r)[8]) {
+#pragma unroll
+    for (int c = 0; c < 8; c++)
+        r[c] = (uint32_t)c < nch ? *reinterpret_cast<const uint4 *>(row + (((uint32_t)c ^ x) << 2)) : make_uint4(0, 0, 0, 0);
+}
+
+template <int DT>
+__device__ __forceinline__ int dot_regs(const uint4 (&y)[8], const uint32_t *zrow, uint32_t zx, uint32_t nch) {
+    int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        if ((uint32_t)c < nch) {
+            const uint4 z = *reinterpret_cast<const uint4 *>(zrow + (((uint32_t)c ^ zx) << 2));
+            a0 = dot4<DT>(y[c].x, z.x, a0);
+            a1 = dot4<DT>(y[c].y, z.y, a1);
+            a2 = dot4<DT>(y[c].z, z.z, a2);
+            a3 = dot4<DT>(y[c].w, z.w, a3);
+        }
+    }
+    return (a0 + a1) + (a2 + a3);
 }
 
 template <int DT, int MET>
@@ -225,7 +264,7 @@ __global__ void robust_prune_smem(const void *X, uint64_t n, uint32_t d, const i
     float *DX = reinterpret_cast<float *>(base + L.dx);
     int *NZ = reinterpret_cast<int *>(base + L.nz);
     uint32_t *A = reinterpret_cast<uint32_t *>(base + L.alive);
-    const uint32_t stride = L.dw + 1;
+    const uint32_t stride = L.stride, sm = L.smask;
 
     for (uint64_t v = (uint64_t)blockIdx.x * nwarps + warp; v < n; v += (uint64_t)gridDim.x * nwarps) {
         uint32_t c = cnt[v];
@@ -252,9 +291,22 @@ __global__ void robust_prune_smem(const void *X, uint64_t n, uint32_t d, const i
         }
         c = nvalid;
         __syncwarp();
-        // candidate rows into rows 0..c-1, the node's own row into row l_max; four independent
-        // loads per lane are in flight before their stores
-        {
+        // candidate rows into rows 0..c-1, the node's own row into row l_max
+        if (L.async16) {
+            const uint32_t nch = stride / 4, row_bytes = DT == PIPNN_F32 ? d * 4 : d;
+            const uint32_t total = (c + 1) * nch;
+            for (uint32_t idx = lane; idx < total; idx += 32) {
+                const uint32_t t = idx / nch, ch = idx - t * nch;
+                const uint32_t id = t < c ? (uint32_t)K[t] : (uint32_t)v;
+                const uint32_t row = t < c ? t : l_max;
+                const char *src = static_cast<const char *>(X) + (uint64_t)id * row_bytes + ch * 16;
+                const uint32_t dst = static_cast<uint32_t>(
+                    __cvta_generic_to_shared(rows + (size_t)row * stride + ((ch ^ (row & sm)) << 2)));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        } else {
+            // four independent loads per lane are in flight before their stores
             const uint32_t total = (c + 1) * L.dw;
             for (uint32_t b0 = 0; b0 < total; b0 += 128) {
                 uint32_t vals[4];
@@ -274,7 +326,8 @@ __global__ void robust_prune_smem(const void *X, uint64_t n, uint32_t d, const i
                     const uint32_t idx = b0 + u * 32 + lane;
                     if (idx < total) {
                         const uint32_t t = idx / L.dw, w = idx - t * L.dw;
-                        rows[(size_t)(t < c ? t : l_max) * stride + w] = vals[u];
+                        const uint32_t row = t < c ? t : l_max;
+                        rows[(size_t)row * stride + (w ^ ((row & sm) << 2))] = vals[u];
                     }
                 }
             }
@@ -284,12 +337,21 @@ __global__ void robust_prune_smem(const void *X, uint64_t n, uint32_t d, const i
         const uint32_t *xr = rows + (size_t)l_max * stride;
         uint32_t P = 32;
         while (P < c) P <<= 1;
+        const bool regs = DT != PIPNN_F32 && stride <= 32;
+        uint4 xw[8];
+        if (regs) row_to_regs<DT>(xr, l_max & sm, stride / 4, xw);
         for (uint32_t t = lane; t < P; t += 32) {
             uint64_t kk = ~0ull;
             if (t < c) {
                 uint32_t ok;
                 float val;
-                dis_smem<DT, MET>(xr, rows + (size_t)t * stride, L.dw, NZ[l_max], NZ[t], ok, val);
+                if (regs) {
+                    const int D = NZ[l_max] + NZ[t] - 2 * dot_regs<DT>(xw, rows + (size_t)t * stride, t & sm, stride / 4);
+                    ok = (uint32_t)D;
+                } else {
+                    dis_smem<DT, MET>(xr, l_max & sm, rows + (size_t)t * stride, t & sm, L.dw, NZ[l_max], NZ[t], ok,
+                                      val);
+                }
                 kk = ((uint64_t)ok << 32) | (uint32_t)K[t];
             }
             K[t] = kk;
@@ -348,12 +410,18 @@ __global__ void robust_prune_smem(const void *X, uint64_t n, uint32_t d, const i
             __syncwarp();
             const uint32_t *yr = rows + (size_t)ys * stride;
             const int ny = NZ[ys];
+            uint4 yw[8];
+            if (regs) row_to_regs<DT>(yr, ys & sm, stride / 4, yw);
             for (uint32_t z = head + lane; z < c; z += 32) {
                 if (!((A[z / 32] >> (z & 31)) & 1u)) continue;
                 const uint32_t zs = perm[z];
                 uint32_t ok;
                 float dyz;
-                dis_smem<DT, MET>(yr, rows + (size_t)zs * stride, L.dw, ny, NZ[zs], ok, dyz);
+                if (regs) {
+                    dyz = __int2float_rn(ny + NZ[zs] - 2 * dot_regs<DT>(yw, rows + (size_t)zs * stride, zs & sm, stride / 4));
+                } else {
+                    dis_smem<DT, MET>(yr, ys & sm, rows + (size_t)zs * stride, zs & sm, L.dw, ny, NZ[zs], ok, dyz);
+                }
                 if (__fmul_rn(alpha2, dyz) < DX[z]) atomicAnd(&A[z / 32], ~(1u << (z & 31)));
             }
             __syncwarp();
