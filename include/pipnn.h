@@ -49,14 +49,17 @@ extern "C" {
 enum { PIPNN_F32 = 0, PIPNN_U8 = 1, PIPNN_I8 = 2 };
 enum { PIPNN_L2 = 0, PIPNN_IP = 1 };
 
-/* Engine of the leaf all-pairs step (A2).  Both give identical candidate edges.
+/* Engine of the distance contractions: the leaf all-pairs step (A2) and the leader assignment
+ * of Alg. 5 (A1).  Both engines give identical results.
  *  PIPNN_LEAF_SIMT: CUDA-core arithmetic in the defining order (binary32 FMA chain / exact
  *                   integer dot products).
  *  PIPNN_LEAF_TC:   tcgen05 tensor-core tiles with BF16 operands and FP32 accumulation in TMEM
- *                   that produce n_j - 2<x_i, x_j> directly (the norm enters as three extra
- *                   K columns).  For byte data with d <= 128 every product and partial sum is an
- *                   integer below 2^24, so the result is exact; float data and d > 128 return
- *                   PIPNN_EUNSUPPORTED. */
+ *                   that produce n_j - 2<x_i, x_j> directly (the norm enters as extra K
+ *                   columns).  For byte data with d <= 128 every product and partial sum is an
+ *                   integer below 2^24, so the result is exact.  The leaf step returns
+ *                   PIPNN_EUNSUPPORTED for float data and d > 128; the assignment runs on the
+ *                   tensor cores where it applies (byte data, d <= 128, fanout of the level
+ *                   <= 16) and on the CUDA cores otherwise. */
 enum { PIPNN_LEAF_SIMT = 0, PIPNN_LEAF_TC = 1 };
 
 /* Hyper-parameters BP of Alg. 4. */
@@ -138,7 +141,7 @@ int pipnn_sketch(const void *points, uint64_t n, uint32_t d, int32_t dtype, cons
  * (determinism lemma, App. A.5: the result is a function of the inputs and the seed).
  * points: device.  On success *out holds library-owned device arrays; free with
  * pipnn_leaves_free.  Leaves are listed in no particular order; members inside a leaf are in
- * no particular order and distinct. */
+ * no particular order and distinct.  The leader assignment runs on bp->leaf_engine. */
 int pipnn_partition(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp,
                     uint64_t seed, pipnn_leaves *out);
 void pipnn_leaves_free(pipnn_leaves *leaves);

@@ -13,7 +13,7 @@
 // partial sum is a multiple of 1/2 below 2^23 in magnitude, so FP32 accumulation in any order is
 // exact and the picks equal those of the defining integer arithmetic.
 //
-// Persistent CTA (one per SM, 13 warps) over units (leaf, 128-row tile):
+// Persistent CTA (one per SM, 10 warps) over units (leaf, 128-row tile):
 //   warp 0     producer: TMA tiled loads (128 rows x 64 columns, 128-byte swizzle) of the A and B
 //              tiles from the leaf-ordered copy; B tiles also get the norm pieces (a 32-byte slice
 //              per stage) and a column-id list
@@ -23,145 +23,13 @@
 //              (v, id) insertion (k > 2); two warps share each TMEM lane quarter
 // Every mbarrier wait is bounded by %globaltimer (2 s); on expiry the CTA records DERR_TIMEOUT,
 // every role stops at the same points, and the TMEM is still released.
-#include "internal.cuh"
-
-#include <cuda.h>
-#include <cudaTypedefs.h>
+#include "tc_common.cuh"
 
 namespace pipnn {
 
 namespace {
 
-constexpr int TC_PRODUCER_WARP = 0;
-constexpr int TC_MMA_WARP = 1;
-constexpr int TC_EPI_WARP0 = 2;
-constexpr int TC_EPI_WARPS = 8;
-constexpr int TC_THREADS = (2 + TC_EPI_WARPS) * 32;  // 320
-constexpr int TC_ROWS = 128;
-constexpr uint32_t TC_TMEM_COLS = 512;
-constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
-
-// ------------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: false if the CTA aborted or the wait ran past TC_WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, unsigned *err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    for (uint32_t i = 1;; i++) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((i & 63) == 0) {
-            if (*abort) return false;
-            if (globaltimer() - t0 > TC_WAIT_NS) {
-                *abort = 1;
-                atomicOr(err, DERR_TIMEOUT);
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Named barrier that also ORs a predicate over the participating threads, so a stop decision
-// is identical for all of them (no thread can leave a loop its peers are still in).
-__device__ __forceinline__ bool named_barrier_or(uint32_t id, uint32_t count, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, %2, %3, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(id), "r"(count)
-        : "memory");
-    return r != 0;
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);        // start address
-    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
-    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset: next 8-row group
-    d |= (uint64_t)1 << 46;                          // descriptor version
-    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both operands K-major.
-__device__ __forceinline__ uint32_t idesc_bf16(uint32_t M, uint32_t N) {
-    return (1u << 4)              // D: FP32
-           | (1u << 7)            // A: BF16
-           | (1u << 10)           // B: BF16
-           | ((N >> 3) << 17)     // N / 8
-           | ((M >> 4) << 24);    // M / 16
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
+using namespace tc;
 
 // ------------------------------------------------------------------ kernel
 struct TcUnit {
@@ -182,34 +50,19 @@ struct TcArgs {
     unsigned *err;
 };
 
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// TMA tiled load of a 128-row x 64-column BF16 box at (x, y) into 16 KB of shared memory,
-// 128-byte swizzled -- the layout the MMA descriptors read.  Rows past the tensor read as zero.
-__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y,
-                                              uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
 template <int KB, int KMAX>
 struct TcCfg {
     static constexpr int NMAX = 128;                                     // columns per B tile
     static constexpr int S = 3;                                          // B stages
     static constexpr int T = 4;                                          // accumulator buffers
-    static constexpr int REGION = 128 * 128;                             // bytes per 64-wide K block, 128 rows
+    static constexpr int REGION = tc::REGION;
     static constexpr int OFF_A0 = 0;                                     // A data, 2 buffers
     static constexpr int OFF_AN = OFF_A0 + 2 * KB * REGION;              // A norm block (constant)
     static constexpr int OFF_B0 = OFF_AN + REGION;                       // B data, S stages
     static constexpr int OFF_BN = OFF_B0 + S * KB * REGION;              // B norm blocks (32-byte slice per stage)
     static constexpr int OFF_CI = OFF_BN + REGION;                       // T x NMAX column ids
     static constexpr int OFF_MV = OFF_CI + T * NMAX * 4;                 // 128 rows x KMAX (v, id)
-    static constexpr int OFF_BAR = OFF_MV + TC_ROWS * KMAX * 8;
+    static constexpr int OFF_BAR = OFF_MV + ROWS * KMAX * 8;
     static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = 2, BAR_FULL = 4, BAR_EMPTY = BAR_FULL + S,
                          BAR_TFULL = BAR_EMPTY + S, BAR_TEMPTY = BAR_TFULL + T, BAR_CFULL = BAR_TEMPTY + T,
                          NBAR = BAR_CFULL + T;
@@ -217,7 +70,7 @@ struct TcCfg {
     static constexpr int BYTES = OFF_MISC + 16;
     static constexpr int SMEM = BYTES + 1024;                            // + alignment slack
     static_assert(SMEM <= 232448, "shared memory budget");
-    static_assert(T * NMAX <= (int)TC_TMEM_COLS, "TMEM budget");
+    static_assert(T * NMAX <= (int)TMEM_COLS, "TMEM budget");
     static_assert(S <= 4, "norm slices per 128-byte row");
 };
 
@@ -242,7 +95,7 @@ __device__ __forceinline__ void topk_insert(float (&kv)[KMAX], uint32_t (&ki)[KM
 // B job j (one 128-column tile) uses B stage j % S (phase (j / S) % 2) and accumulator buffer /
 // column-id slot j % T (phase (j / T) % 2); unit i uses A buffer i % 2 (phase (i / 2) % 2).
 template <int KB, int KMAX>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 1)
     leaf_gram_tc(const __grid_constant__ CUtensorMap map, const TcArgs a, uint32_t nunits) {
     using C = TcCfg<KB, KMAX>;
     extern __shared__ unsigned char tc_smem_raw[];
@@ -267,29 +120,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int i = 0; i < C::T; i++) {
             mbar_init(bar(C::BAR_TFULL + i), 1);
-            mbar_init(bar(C::BAR_TEMPTY + i), TC_EPI_WARPS * 32);
+            mbar_init(bar(C::BAR_TEMPTY + i), EPI_WARPS * 32);
             mbar_init(bar(C::BAR_CFULL + i), 32);
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
-    if (warp == TC_MMA_WARP) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         sbase + C::OFF_MISC),
-                     "r"(TC_TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (warp == MMA_WARP) {
+        tmem_alloc(sbase + C::OFF_MISC, TMEM_COLS);
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == TC_PRODUCER_WARP) {
+    if (warp == PRODUCER_WARP) {
         // ------------------------------------------------------------ producer (one warp)
         // A's norm block: [1, 1, 1, 1, 0, ...] in logical chunk 0 of every row, zeros in chunk 1
-        for (uint32_t r = lane; r < (uint32_t)TC_ROWS; r += 32) {
+        for (uint32_t r = lane; r < (uint32_t)ROWS; r += 32) {
             const uint32_t one = 0x3F80u;  // bf16 1.0
             const uint32_t base = sbase + C::OFF_AN + r * 128;
             asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((0u ^ (r & 7)) << 4)),
@@ -383,14 +232,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         ci[r] = in ? id[e] : 0xFFFFFFFFu;
                         // -(n_j / 2) as four BF16-exact pieces: the bytes of floor(n_j / 2) and
                         // (n_j mod 2) / 2, in this stage's 32-byte slice (logical chunks 2 st, 2 st + 1)
-                        const uint32_t nj = in ? (uint32_t)nr[e] : 0u, hj = nj >> 1;
-                        const uint32_t b1 = __bfloat16_as_ushort(__float2bfloat16_rn(-(float)(hj & 0xFF0000u)));
-                        const uint32_t b2 = __bfloat16_as_ushort(__float2bfloat16_rn(-(float)(hj & 0x00FF00u)));
-                        const uint32_t b3 = __bfloat16_as_ushort(__float2bfloat16_rn(-(float)(hj & 0x0000FFu)));
-                        const uint32_t b4 = __bfloat16_as_ushort(__float2bfloat16_rn((nj & 1u) ? -0.5f : 0.0f));
+                        const uint2 pc = neg_half_norm_pieces(in ? (uint32_t)nr[e] : 0u);
                         const uint32_t nb = sbase + C::OFF_BN + r * 128;
                         asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st) ^ (r & 7)) << 4)),
-                                     "r"(b1 | (b2 << 16)), "r"(b3 | (b4 << 16)), "r"(0u), "r"(0u)
+                                     "r"(pc.x), "r"(pc.y), "r"(0u), "r"(0u)
                                      : "memory");
                         asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st + 1) ^ (r & 7)) << 4)),
                                      "r"(0u), "r"(0u), "r"(0u), "r"(0u)
@@ -419,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 nr[e] = nnr[e];
             }
         }
-    } else if (warp == TC_MMA_WARP) {
+    } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t j = 0, issued_j = 0;
@@ -437,7 +282,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         stop = true;
                         break;
                     }
-                    tc_fence_after();
+                    fence_after();
                     const uint32_t c0 = t * C::NMAX;
                     const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
                     const uint32_t idesc = idesc_bf16(128, (ncols + 15) & ~15u);
@@ -466,7 +311,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int ew = warp - TC_EPI_WARP0;          // 0..7
+        const int ew = warp - EPI_WARP0;          // 0..7
         const int half = ew >> 2;                    // which column chunks
         const int quarter = warp & 3;                // TMEM lane quarter this warp may access
         const uint32_t r = quarter * 32 + lane;      // row inside the tile
@@ -501,7 +346,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     failed = true;
                     continue;
                 }
-                tc_fence_after();
+                fence_after();
                 const uint32_t c0 = t * C::NMAX;
                 const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
                 const uint32_t *info = colid + tb * C::NMAX;
@@ -590,7 +435,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         }
                     }
                 }
-                tc_fence_before();
+                fence_before();
                 mbar_arrive(bar(C::BAR_TEMPTY + tb));
             }
             if constexpr (KMAX == 2) {
@@ -607,7 +452,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                 for (int p = 0; p < KMAX; p++) mv[r * KMAX + p] = make_float2(kv[p], __uint_as_float(ki[p]));
             }
-            failed = named_barrier_or(1, TC_EPI_WARPS * 32, failed || *abort);
+            failed = named_barrier_or(1, EPI_WARPS * 32, failed || *abort);
             if (half == 0 && row_ok && !failed) {
 #pragma unroll
                 for (int p = 0; p < KMAX; p++) {
@@ -634,17 +479,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             // mv is rewritten by the next unit only after every reader is done
-            failed = named_barrier_or(1, TC_EPI_WARPS * 32, failed || *abort);
+            failed = named_barrier_or(1, EPI_WARPS * 32, failed || *abort);
             if (failed) break;
         }
     }
 
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    if (warp == TC_MMA_WARP) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
-                     : "memory");
+    if (warp == MMA_WARP) {
+        fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
     }
 }
 
@@ -707,32 +551,6 @@ __global__ void member_norms(const uint32_t *members, uint64_t M, const int32_t 
         out[i] = sqnorm[members[i]];
 }
 
-// Leaf-ordered BF16 copy of the members' rows, zero padded to kp columns (exact for byte data):
-// row i holds the point members[i].
-__global__ void stage_rows(const void *X, uint32_t d, uint32_t kp, int dtype, const uint32_t *members, uint64_t M,
-                           __nv_bfloat16 *out) {
-    const uint32_t per_row = kp / 8;  // 16-byte output chunks per row
-    const uint64_t total = M * per_row;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t row = i / per_row;
-        const uint32_t c = (uint32_t)(i % per_row);
-        const uint64_t src = (uint64_t)members[row] * d;
-        uint32_t w[4];
-#pragma unroll
-        for (int h = 0; h < 4; h++) {
-            float lo = 0.0f, hi = 0.0f;
-            const uint32_t t = c * 8 + 2 * h;
-            if (t < d) lo = dtype == PIPNN_U8 ? (float)static_cast<const uint8_t *>(X)[src + t]
-                                              : (float)static_cast<const int8_t *>(X)[src + t];
-            if (t + 1 < d) hi = dtype == PIPNN_U8 ? (float)static_cast<const uint8_t *>(X)[src + t + 1]
-                                                  : (float)static_cast<const int8_t *>(X)[src + t + 1];
-            w[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
-        }
-        reinterpret_cast<uint4 *>(out)[i] = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-}
-
 template <int KB, int KMAX>
 int launch_tc(const CUtensorMap &map, const TcArgs &args, uint64_t ntiles) {
     using C = TcCfg<KB, KMAX>;
@@ -747,7 +565,7 @@ int launch_tc(const CUtensorMap &map, const TcArgs &args, uint64_t ntiles) {
         a.units += t0;
         a.unit_leaf += t0;
         const unsigned grid = (unsigned)(cnt < (uint64_t)sms ? cnt : (uint64_t)sms);
-        kern<<<grid, TC_THREADS, C::SMEM, stream()>>>(map, a, (uint32_t)cnt);
+        kern<<<grid, THREADS, C::SMEM, stream()>>>(map, a, (uint32_t)cnt);
         PIPNN_LAUNCH_CHECK();
     }
     return PIPNN_OK;
@@ -761,30 +579,6 @@ int launch_tc_k(const CUtensorMap &map, const TcArgs &args, uint64_t ntiles, uin
     return launch_tc<KB, 16>(map, args, ntiles);
 }
 
-// Tensor map over an n x kp BF16 matrix: boxes of 128 rows x 64 columns, 128-byte swizzle.
-int encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *base, uint64_t n, uint32_t kp) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            !fn) {
-            cudaGetLastError();
-            return set_error(PIPNN_ECUDA, "cuTensorMapEncodeTiled is unavailable");
-        }
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
-    const cuuint64_t gdim[2] = {kp, n};
-    const cuuint64_t gstride[1] = {(cuuint64_t)kp * 2};
-    const cuuint32_t box[2] = {64, 128};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUresult rc = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(base), gdim,
-                               gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (rc != CUDA_SUCCESS) return set_error(PIPNN_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)rc);
-    return PIPNN_OK;
-}
 }  // namespace
 
 int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t *sqnorm, const uint64_t *off,
@@ -827,12 +621,11 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
     __nv_bfloat16 *staged = nullptr;
     PIPNN_TRY(ws.alloc(&staged, (M ? M : 1) * kp));
     if (M) {
-        stage_rows<<<grid_for(M * (kp / 8), 256), 256, 0, stream()>>>(X, d, kp, dtype, mem, M, staged);
-        PIPNN_LAUNCH_CHECK();
+        PIPNN_TRY(stage_rows_bf16(X, d, kp, dtype, mem, M, staged));
     }
     uint32_t *tile_grp = nullptr, *tile_row0 = nullptr;
     uint64_t ntiles = 0;
-    PIPNN_TRY(make_tiles(leaf_size, L, TC_ROWS, &tile_grp, &tile_row0, &ntiles, ws));
+    PIPNN_TRY(make_tiles(leaf_size, L, ROWS, &tile_grp, &tile_row0, &ntiles, ws));
     TcUnit *units = nullptr;
     PIPNN_TRY(ws.alloc(&units, ntiles));
     if (ntiles) {
@@ -840,7 +633,7 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
         PIPNN_LAUNCH_CHECK();
     }
     CUtensorMap map;
-    PIPNN_TRY(encode_rows_map(&map, staged, M ? M : 1, kp));
+    PIPNN_TRY(encode_rows_map(&map, staged, M ? M : 1, kp, false));
     TcArgs a{};
     a.units = units;
     a.unit_leaf = tile_grp;

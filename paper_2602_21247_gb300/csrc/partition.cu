@@ -6,7 +6,9 @@
 //                        (Philox priority, id); candidates under a per-subproblem threshold are
 //                        collected, then sorted in shared memory (retried if too few)
 //   2. assignment     -- every instance joins its min(fanout(depth), l) nearest leaders,
-//                        equidistant leaders in draw order (allpairs_topk, MODE_ASSIGN)
+//                        equidistant leaders in draw order: on the tensor cores for byte data
+//                        with the PIPNN_LEAF_TC engine (assign_tc.cu), else on the CUDA cores
+//                        (allpairs_topk, MODE_ASSIGN)
 //   3. Merge plan     -- buckets below C_min are packed next-fit in leader-rank order into
 //                        groups of at most C_max (one thread per subproblem walks its ranks)
 //   4. scatter        -- instances move to their leaf / next-level bucket; a point that reaches
@@ -15,6 +17,7 @@
 //                        is cut into ceil(|b|/C_max) runs of its members in id order
 // Leaves are compacted into one CSR array at the end.
 #include "allpairs.cuh"
+#include "tc_common.cuh"
 
 #include <memory>
 
@@ -320,6 +323,10 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         sqn = tmp;
     }
 
+    // tensor-core assignment: one padded BF16 copy of the points, made at the first level that uses it
+    Workspace tc_ws;
+    AssignTcPlan tc_plan;
+
     std::unique_ptr<Level> cur(new Level());
     uint32_t nlevels = 0;
     if (n <= bp->c_max) {
@@ -428,7 +435,14 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         a.fanout = F;
         a.assign = assign;
         a.bucket_cnt = bucket_cnt;
-        PIPNN_TRY(launch_allpairs<MODE_ASSIGN>(dtype, metric, F, a, ntiles));
+        if (bp->leaf_engine == PIPNN_LEAF_TC && assign_tc_eligible(dtype, d, n, F)) {
+            if (!tc_plan.rows) PIPNN_TRY(assign_tc_plan(X, n, d, dtype, tc_ws, &tc_plan));
+            PIPNN_TRY(assign_tc(tc_plan, X, d, dtype, sqn, tile_grp, tile_row0, ntiles, cur->seg_start,
+                                cur->seg_size, cur->inst, lead_off, lead_cnt, lead, total_leaders, F, assign,
+                                bucket_cnt, tw));
+        } else {
+            PIPNN_TRY(launch_allpairs<MODE_ASSIGN>(dtype, metric, F, a, ntiles));
+        }
 
         // 3. Merge plan
         uint64_t *ob_count, *ob_base, OB = 0;
