@@ -57,9 +57,10 @@ enum { PIPNN_L2 = 0, PIPNN_IP = 1 };
  *                   that produce n_j - 2<x_i, x_j> directly (the norm enters as extra K
  *                   columns).  For byte data with d <= 128 every product and partial sum is an
  *                   integer below 2^24, so the result is exact.  The leaf step returns
- *                   PIPNN_EUNSUPPORTED for float data and d > 128; the assignment runs on the
- *                   tensor cores where it applies (byte data, d <= 128, fanout of the level
- *                   <= 16) and on the CUDA cores otherwise. */
+ *                   PIPNN_EUNSUPPORTED for float data and d > 128; the assignment (byte data,
+ *                   d <= 128, fanout of the level <= 16) and the final prune (byte data,
+ *                   d <= 128, l_max <= 127) run on the tensor cores where they apply and on the
+ *                   CUDA cores otherwise. */
 enum { PIPNN_LEAF_SIMT = 0, PIPNN_LEAF_TC = 1 };
 
 /* Hyper-parameters BP of Alg. 4. */
@@ -190,10 +191,12 @@ int pipnn_hashprune_noalloc(const uint32_t *dst, const uint32_t *src, const floa
  * Candidates are ordered by (dissimilarity to the node, id); candidate z is removed by the
  * admitted y when alpha^2 * D(y,z) < D(x,z), evaluated in binary32 with
  * alpha^2 = (float)((double)alpha * alpha).  points, reservoir (n x l_max), count, adj (n x R)
- * and deg (n) are device pointers. */
+ * and deg (n) are device pointers.  engine: PIPNN_LEAF_SIMT, or PIPNN_LEAF_TC, which forms every
+ * node's candidate Gram matrix on the tensor cores where it applies (byte data, d <= 128,
+ * l_max <= 127; elsewhere the CUDA cores).  Both give the same graph. */
 int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
                       const uint64_t *reservoir, const uint32_t *count, uint32_t l_max, uint32_t R,
-                      float alpha, uint32_t *adj, uint32_t *deg);
+                      float alpha, int32_t engine, uint32_t *adj, uint32_t *deg);
 
 /* Alg. 4 end to end: A0 .. A6 on the GPU.  points: host or device (host input is copied to the
  * device inside the call).  graph_on_host = 1 returns the graph in pinned host memory, 0 in

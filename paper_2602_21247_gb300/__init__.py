@@ -93,7 +93,7 @@ def lib():
         L.pipnn_edges_free.restype = None
         L.pipnn_hashprune.argtypes = [vp, vp, vp, u64, vp, u32, u64, u32, vp, vp]
         L.pipnn_hashprune_noalloc.argtypes = [vp, vp, vp, u64, vp, u32, u64, u32, vp, vp]
-        L.pipnn_final_prune.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, u32, f32, vp, vp]
+        L.pipnn_final_prune.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, u32, f32, i32, vp, vp]
         L.pipnn_build.argtypes = [vp, u64, u32, i32, C.POINTER(pipnn_params), u64, i32, C.POINTER(pipnn_graph)]
         L.pipnn_free.argtypes = [C.POINTER(pipnn_graph)]
         L.pipnn_free.restype = None
@@ -246,7 +246,7 @@ def pipnn_hashprune_noalloc(dst, src, dist, sketch, n, l_max, reservoir, count):
     return reservoir, count
 
 
-def pipnn_final_prune(points, reservoir, count, R, alpha, metric=PIPNN_L2):
+def pipnn_final_prune(points, reservoir, count, R, alpha, metric=PIPNN_L2, engine=PIPNN_LEAF_SIMT):
     """A6: returns (adjacency n x R uint32 padded with 0xFFFFFFFF, degree n uint32)."""
     n, d = points.shape
     l_max = reservoir.shape[1]
@@ -254,7 +254,7 @@ def pipnn_final_prune(points, reservoir, count, R, alpha, metric=PIPNN_L2):
     deg = torch.empty(n, dtype=torch.int32, device=points.device).view(torch.uint32)
     pipnn_set_stream()
     _check(lib().pipnn_final_prune(_ptr(points), n, d, dtype_code(points), metric, _ptr(reservoir), _ptr(count),
-                                   l_max, R, alpha, _ptr(adj), _ptr(deg)))
+                                   l_max, R, alpha, engine, _ptr(adj), _ptr(deg)))
     return adj, deg
 
 

@@ -19,8 +19,8 @@ int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, cons
 int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
                     uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt);
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-                const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, uint32_t *adj,
-                uint32_t *deg);
+                const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, int engine,
+                uint32_t *adj, uint32_t *deg);
 int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, uint32_t *adj,
                     uint32_t *deg);
 
@@ -226,7 +226,8 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     rc = dev_alloc_raw((void **)&deg, n * 4);
     if (rc == PIPNN_OK) {
         if (bp->final_prune)
-            rc = final_prune(X, n, d, dtype, metric, sqn_bytes, res, cnt, bp->l_max, bp->R, bp->alpha, adj, deg);
+            rc = final_prune(X, n, d, dtype, metric, sqn_bytes, res, cnt, bp->l_max, bp->R, bp->alpha, bp->leaf_engine,
+                             adj, deg);
         else
             rc = reservoir_graph(n, res, cnt, bp->l_max, bp->R, adj, deg);
     }
@@ -367,14 +368,15 @@ int pipnn_hashprune(const uint32_t *dst, const uint32_t *src, const float *dist,
 
 int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
                       const uint64_t *reservoir, const uint32_t *count, uint32_t l_max, uint32_t R, float alpha,
-                      uint32_t *adj, uint32_t *deg) {
+                      int32_t engine, uint32_t *adj, uint32_t *deg) {
     CallScope cs;
     PIPNN_TRY(cs.init());
     PIPNN_TRY(check_points(points, n, d, dtype, metric));
     if (!reservoir || !count || !adj || !deg) return set_error(PIPNN_EINVAL, "NULL array");
     if (l_max < 1 || l_max > 256 || R < 1 || R > l_max) return set_error(PIPNN_EINVAL, "need 1 <= R <= l_max <= 256");
     if (!(alpha >= 1.0f) || !std::isfinite(alpha)) return set_error(PIPNN_EINVAL, "alpha must be finite and >= 1");
-    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, adj, deg));
+    if (engine != PIPNN_LEAF_SIMT && engine != PIPNN_LEAF_TC) return set_error(PIPNN_EINVAL, "unknown engine %d", engine);
+    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, engine, adj, deg));
     return check_device_error("final prune");
 }
 

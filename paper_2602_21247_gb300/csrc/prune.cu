@@ -11,6 +11,10 @@ namespace pipnn {
 
 int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float *H, uint32_t m, float *S,
                   void *sqnorm);
+bool prune_tc_eligible(int dtype, uint32_t d, uint64_t n, uint32_t l_max);
+int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t *sqn, const uint64_t *res,
+                   const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha2, uint32_t *adj, uint32_t *deg,
+                   Workspace &ws);
 
 namespace {
 constexpr int PR_WARPS = 8;
@@ -306,8 +310,9 @@ __global__ void robust_prune_smem(const void *X, uint64_t n, uint32_t d, const i
             }
             asm volatile("cp.async.wait_all;" ::: "memory");
         } else {
-            // four independent loads per lane are in flight before their stores
-            const uint32_t total = (c + 1) * L.dw;
+            // four independent loads per lane are in flight before their stores; the padding
+            // words of a row (stride > dw) are written as zeros, as whole chunks are read back
+            const uint32_t total = (c + 1) * stride;
             for (uint32_t b0 = 0; b0 < total; b0 += 128) {
                 uint32_t vals[4];
 #pragma unroll
@@ -315,17 +320,21 @@ __global__ void robust_prune_smem(const void *X, uint64_t n, uint32_t d, const i
                     const uint32_t idx = b0 + u * 32 + lane;
                     vals[u] = 0;
                     if (idx < total) {
-                        const uint32_t t = idx / L.dw, w = idx - t * L.dw;
+                        const uint32_t t = idx / stride, w = idx - t * stride;
                         const uint32_t id = t < c ? (uint32_t)K[t] : (uint32_t)v;
-                        if (DT == PIPNN_F32) vals[u] = __float_as_uint(__ldg(static_cast<const float *>(X) + (uint64_t)id * d + w));
-                        else vals[u] = coord_word<DT>(X, id, d, w);
+                        if (w < L.dw) {
+                            if (DT == PIPNN_F32)
+                                vals[u] = __float_as_uint(__ldg(static_cast<const float *>(X) + (uint64_t)id * d + w));
+                            else
+                                vals[u] = coord_word<DT>(X, id, d, w);
+                        }
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const uint32_t idx = b0 + u * 32 + lane;
                     if (idx < total) {
-                        const uint32_t t = idx / L.dw, w = idx - t * L.dw;
+                        const uint32_t t = idx / stride, w = idx - t * stride;
                         const uint32_t row = t < c ? t : l_max;
                         rows[(size_t)row * stride + (w ^ ((row & sm) << 2))] = vals[u];
                     }
@@ -446,8 +455,8 @@ __global__ void reservoir_to_graph(uint64_t n, const uint64_t *res, const uint32
 }  // namespace
 
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-                const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, uint32_t *adj,
-                uint32_t *deg) {
+                const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, int engine,
+                uint32_t *adj, uint32_t *deg) {
     if (l_max > PR_MAX) return set_error(PIPNN_EINVAL, "l_max %u exceeds %d", l_max, PR_MAX);
     Workspace ws;
     const int32_t *sqn = sqnorm_bytes;
@@ -458,6 +467,9 @@ int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, co
         sqn = tmp;
     }
     const float alpha2 = (float)((double)alpha * (double)alpha);
+    if (n == 0) return PIPNN_OK;
+    if (engine == PIPNN_LEAF_TC && prune_tc_eligible(dtype, d, n, l_max))
+        return final_prune_tc(X, n, d, dtype, sqn, res, cnt, l_max, R, alpha2, adj, deg, ws);
     const PruneSmem L = prune_smem_layout(dtype, d, l_max);
     const size_t budget = 200 * 1024;
     if (L.per_warp <= budget) {
