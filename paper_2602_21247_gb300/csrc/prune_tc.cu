@@ -16,11 +16,14 @@
 //  * walk: in rank order a candidate is admitted unless its column mask meets the admitted set
 //    (the removal loop of Alg. 2 and its lazy form coincide), up to R admissions.
 //
-// Persistent CTA (one per SM, 14 warps):
-//   warp 0       producer: node info (ids, norms, BF16 keys), norm pieces, TMA gather4 of the rows
+// Persistent CTA (one per SM, 21 warps):
+//   warp 0       node info: reservoir slots and norms (loaded a node ahead), compaction of the
+//                valid ids, BF16 keys, norm pieces
+//   warp 20      TMA gather4 of the node's rows (ids from the node info)
 //   warp 1       owns TMEM (4 x 128 columns); one thread issues the Gram MMAs
-//   warps 2-9    epilogue: D(x, .), thresholds, ranks, column masks -> a walk slot
-//   warps 10-13  walkers: one node at a time each, writes adj / deg
+//   warps 2-13   epilogue: three groups of four warps (one per TMEM lane quarter, a thread per
+//                row) take turns on nodes: D(x, .), thresholds, ranks, column masks -> walk slot
+//   warps 14-19  walkers: one node at a time each, write adj / deg
 // Waits are bounded as in the other engines (DERR_TIMEOUT; TMEM is still released).
 #include "tc_common.cuh"
 
@@ -30,10 +33,13 @@ namespace {
 
 using namespace tc;
 
-constexpr int PT_WALKERS = 4;
-constexpr int PT_WALK_WARP0 = 2 + EPI_WARPS;                  // 10
-constexpr int PT_THREADS = (2 + EPI_WARPS + PT_WALKERS) * 32;  // 448
-constexpr uint32_t PT_MAXC = 127;                              // candidates per node (+ the node)
+constexpr int PT_GROUPS = 3;                                     // epilogue groups of 4 warps
+constexpr int PT_EPI_WARPS = 4 * PT_GROUPS;
+constexpr int PT_WALKERS = 6;
+constexpr int PT_WALK_WARP0 = 2 + PT_EPI_WARPS;
+constexpr int PT_GATHER_WARP = PT_WALK_WARP0 + PT_WALKERS;
+constexpr int PT_THREADS = (PT_GATHER_WARP + 1) * 32;
+constexpr uint32_t PT_MAXC = 127;                                 // candidates per node (+ the node)
 
 struct PtArgs {
     const uint64_t *res;   // n x l_max reservoir slots
@@ -41,7 +47,7 @@ struct PtArgs {
     const int32_t *sqn;    // exact squared norms
     uint64_t n;
     uint32_t l_max, R;
-    float alpha2;
+    float alpha2, inv_alpha2;
     uint32_t *adj, *deg;
     unsigned *err;
 };
@@ -60,8 +66,8 @@ struct PtCfg {
     static constexpr int OFF_BN = OFF_AN + REGION;          // a 32-byte norm slice per A buffer
     static constexpr int OFF_INFO = OFF_BN + REGION;
     static constexpr int OFF_WS = OFF_INFO + T * I_BYTES;
-    static constexpr int OFF_DX = OFF_WS + W * W_BYTES;     // 2 x 128 u32: D(x, z_r) by row
-    static constexpr int OFF_BAR = OFF_DX + 2 * 128 * 4;
+    static constexpr int OFF_DX = OFF_WS + W * W_BYTES;     // per group 2 x 128 u32: D(x, z_r) by row
+    static constexpr int OFF_BAR = OFF_DX + PT_GROUPS * 2 * 128 * 4;
     static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = A, BAR_CFULL = 2 * A, BAR_TFULL = 2 * A + T,
                          BAR_TEMPTY = 2 * A + 2 * T, BAR_WFULL = 2 * A + 3 * T, BAR_WEMPTY = 2 * A + 3 * T + W,
                          NBAR = 2 * A + 3 * T + 2 * W;
@@ -91,10 +97,12 @@ __device__ __forceinline__ uint32_t pick32(const uint32_t (&g)[32], uint32_t j) 
 // Smallest integer t >= 0 with !(fl(alpha2 * t) < dx): a candidate at distance dx from the node is
 // removed by y exactly when D(y, z) < T.  (alpha2 = +inf gives T = 0: nothing is removed, as
 // inf * t < dx never holds and 0 * inf is NaN.)
-__device__ __forceinline__ uint32_t removal_threshold(uint32_t dx, float alpha2) {
+// The estimate dx * (1 / alpha2) is within a few units of T (relative error ~2^-22 on values
+// below 2^24), and the two bounded walks make it exact.
+__device__ __forceinline__ uint32_t removal_threshold(uint32_t dx, float alpha2, float inv_alpha2) {
     if (dx == 0) return 0;
     const float f = (float)dx;  // dx < 2^24: exact
-    uint32_t t = (uint32_t)fmin((double)dx / (double)alpha2, 16777216.0);
+    uint32_t t = (uint32_t)fminf(__fmul_rn(f, inv_alpha2), 16777216.0f);
     for (int i = 0; i < 8 && t > 0 && !(__fmul_rn(alpha2, (float)(t - 1)) < f); i++) t--;
     for (int i = 0; i < 8 && __fmul_rn(alpha2, (float)t) < f; i++) t++;
     return t;
@@ -125,16 +133,16 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::A; i++) {
-            mbar_init(bar(C::BAR_FULL_A + i), 32);
+            mbar_init(bar(C::BAR_FULL_A + i), 64);  // info warp + gather warp
             mbar_init(bar(C::BAR_EMPTY_A + i), 1);
         }
         for (int i = 0; i < C::T; i++) {
             mbar_init(bar(C::BAR_CFULL + i), 32);
             mbar_init(bar(C::BAR_TFULL + i), 1);
-            mbar_init(bar(C::BAR_TEMPTY + i), EPI_WARPS * 32);
+            mbar_init(bar(C::BAR_TEMPTY + i), 128);
         }
         for (int i = 0; i < C::W; i++) {
-            mbar_init(bar(C::BAR_WFULL + i), EPI_WARPS * 32);
+            mbar_init(bar(C::BAR_WFULL + i), 128);
             mbar_init(bar(C::BAR_WEMPTY + i), 32);
         }
         *abort = 0;
@@ -158,20 +166,57 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((1u ^ (r & 7)) << 4)), "r"(0u),
                          "r"(0u), "r"(0u), "r"(0u)
                          : "memory");
+            // every buffer's 32-byte norm slice starts zero; a node rewrites only its first 8 bytes
+            for (uint32_t q = 0; q < 2u * C::A; q++)
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + C::OFF_BN + r * 128 +
+                                                                              ((q ^ (r & 7)) << 4)),
+                             "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+                             : "memory");
         }
         fence_proxy_async();
+        // Software pipeline: the reservoir slots of node j + 1 and the norms of its valid
+        // candidates are loaded while node j is issued (two dependent global round trips that a
+        // node would otherwise wait for in turn).
+        struct Pre {
+            uint64_t key[4];
+            int32_t nr[4];
+            int32_t nv;
+            uint32_t c;
+        };
+        auto load_keys = [&](uint64_t v, Pre &p) {
+            p.c = 0;
+            p.nv = 0;
+            if (v >= n) return;
+            p.nv = a.sqn[v];
+            const uint32_t c = a.cnt[v];
+            p.c = c < a.l_max ? c : a.l_max;
+            // every slot of the row is read, so these loads do not wait for the count
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t s = 32 * k + lane;
+                p.key[k] = s < a.l_max ? a.res[v * a.l_max + s] : 0ull;
+            }
+        };
+        auto load_norms = [&](Pre &p) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const uint32_t s = 32 * k + lane;
+                const uint32_t id = (uint32_t)(p.key[k] >> 16);
+                p.nr[k] = (s < p.c && (uint64_t)id < n) ? a.sqn[id] : 0;
+            }
+        };
+        Pre cur, nxt;
+        load_keys(blockIdx.x, cur);
+        load_norms(cur);
+        load_keys(blockIdx.x + (uint64_t)gridDim.x, nxt);
         for (uint32_t j = 0;; j++) {
             const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
             if (v >= n) break;
             const uint32_t ua = j % C::A, tb = j % C::T;
-            uint32_t c = a.cnt[v];
-            c = c < a.l_max ? c : a.l_max;
-            uint64_t key[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t s = 32 * k + lane;
-                key[k] = s < c ? a.res[v * a.l_max + s] : 0ull;
-            }
+            Pre nn;
+            load_keys(v + 2 * (uint64_t)gridDim.x, nn);
+            load_norms(nxt);
+            const uint32_t c = cur.c;
             if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_TEMPTY + tb), ((j / C::T) & 1) ^ 1, abort, a.err)))
                 break;
             unsigned char *in = info(tb);
@@ -182,21 +227,21 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const uint32_t s = 32 * k + lane;
-                const uint32_t id = (uint32_t)(key[k] >> 16);
+                const uint32_t id = (uint32_t)(cur.key[k] >> 16);
                 const bool in_range = s < c && (uint64_t)id < n;
                 if (s < c && !in_range) atomicOr(a.err, DERR_RANGE);
                 const unsigned m = __ballot_sync(0xffffffffu, in_range);
                 if (in_range) {
                     const uint32_t pos = cc + __popc(m & ((1u << lane) - 1u));
                     ids[pos] = id;
-                    nrm[pos] = a.sqn[id];
-                    bkey[pos] = (uint16_t)(key[k] >> 48);
+                    nrm[pos] = cur.nr[k];
+                    bkey[pos] = (uint16_t)(cur.key[k] >> 48);
                 }
                 cc += __popc(m);
             }
             if (lane == 0) {
                 ids[cc] = (uint32_t)v;
-                nrm[cc] = a.sqn[v];
+                nrm[cc] = cur.nv;
                 reinterpret_cast<uint32_t *>(in + C::I_MISC)[0] = cc;
                 reinterpret_cast<uint32_t *>(in + C::I_MISC)[1] = (uint32_t)v;
             }
@@ -204,36 +249,21 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             mbar_arrive(bar(C::BAR_CFULL + tb));
             if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + ua), ((j / C::A) & 1) ^ 1, abort, a.err)))
                 break;
-            const uint32_t rows = cc + 1, ng = (rows + 3) / 4;  // gathers of four rows
-            const uint32_t fb = bar(C::BAR_FULL_A + ua);
-            if (lane == 0) mbar_arrive_tx(fb, ng * 512u * KB);
-            __syncwarp();
-            // -(n_r / 2) pieces of every row in this buffer's 32-byte slice; zero past the rows
+            // -(n_r / 2) pieces of every row in this buffer's norm slice; zero past the rows
+            const uint32_t rows = cc + 1;
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 const uint32_t r = 4 * lane + e;
                 const uint2 pc = neg_half_norm_pieces(r < rows ? (uint32_t)nrm[r] : 0u);
-                const uint32_t nb = sbase + C::OFF_BN + r * 128;
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * ua) ^ (r & 7)) << 4)),
-                             "r"(pc.x), "r"(pc.y), "r"(0u), "r"(0u)
-                             : "memory");
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * ua + 1) ^ (r & 7)) << 4)),
-                             "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+                asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(sbase + C::OFF_BN + r * 128 +
+                                                                     (((2 * ua) ^ (r & 7)) << 4)),
+                             "r"(pc.x), "r"(pc.y)
                              : "memory");
             }
             fence_proxy_async();
-            if ((uint32_t)lane < ng) {
-                int32_t y[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const uint32_t r = 4 * lane + e;
-                    y[e] = (int32_t)(r < rows ? ids[r] : (uint32_t)v);
-                }
-                const uint32_t dst = sbase + C::OFF_A0 + ua * KB * REGION + lane * 4 * 128;
-#pragma unroll
-                for (int kb = 0; kb < KB; kb++) tma_gather4(dst + kb * REGION, &xmap, kb * 64, y[0], y[1], y[2], y[3], fb);
-            }
-            if (lane != 0) mbar_arrive(fb);
+            mbar_arrive(bar(C::BAR_FULL_A + ua));
+            cur = nxt;
+            nxt = nn;
         }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
@@ -272,13 +302,14 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
         }
         __syncwarp();
     } else if (warp < PT_WALK_WARP0) {
-        // ------------------------------------------------------------ epilogue (8 warps)
-        const int ew = warp - EPI_WARP0;             // 0..7
-        const int half = ew >> 2;                    // which column chunks
-        const int quarter = warp & 3;                // TMEM lane quarter this warp may access
-        const uint32_t r = quarter * 32 + lane;      // row = candidate slot
+        // ------------------------------------------------------------ epilogue (groups of 4 warps)
+        const uint32_t grp = (warp - EPI_WARP0) >> 2;  // group: nodes j = grp, grp + PT_GROUPS, ...
+        const int quarter = warp & 3;                   // TMEM lane quarter this warp may access
+        const uint32_t r = quarter * 32 + lane;         // row = candidate slot
+        const uint32_t bar_id = 1 + grp;
         bool stop = false;
-        for (uint32_t j = 0;; j++) {
+        for (uint32_t k = 0;; k++) {
+            const uint32_t j = grp + k * PT_GROUPS;
             const uint64_t vv = blockIdx.x + (uint64_t)j * gridDim.x;
             if (vv >= n) break;
             const uint32_t tb = j % C::T, ws = j % C::W;
@@ -291,7 +322,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + C::I_IDS);
             const int32_t *nrm = reinterpret_cast<const int32_t *>(in + C::I_NRM);
             const uint16_t *bkey = reinterpret_cast<const uint16_t *>(in + C::I_BKEY);
-            uint32_t *dx = reinterpret_cast<uint32_t *>(smem + C::OFF_DX) + (j & 1) * 128;
+            uint32_t *dx = reinterpret_cast<uint32_t *>(smem + C::OFF_DX) + (grp * 2 + (k & 1)) * 128;
             unsigned char *wsl = wslot(ws);
             uint32_t c = 0, DX = 0;
             float theta = 0.0f;
@@ -307,25 +338,23 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                     const int32_t nr = nrm[r];
                     const float dxf = __fmaf_rn(-2.0f, acc, (float)nr);  // exact integer
                     DX = (uint32_t)dxf;
-                    const uint32_t T = removal_threshold(DX, a.alpha2);
+                    const uint32_t T = removal_threshold(DX, a.alpha2, a.inv_alpha2);
                     theta = ((float)nr - (float)T) * 0.5f;             // exact (multiple of 1/2)
-                    if (half == 0) {
-                        dx[r] = DX;
-                        bad = bf16_key(dxf) != bkey[r] || (r > 0 && bkey[r - 1] > bkey[r]);
-                    }
+                    dx[r] = DX;
+                    bad = bf16_key(dxf) != bkey[r] || (r > 0 && bkey[r - 1] > bkey[r]);
                 }
             }
-            const bool full_count = named_barrier_or(1, EPI_WARPS * 32, ok && bad);
+            const bool full_count = named_barrier_or(bar_id, 128, ok && bad);
             if (ok) {
                 // E2: rank of z_r in (D(x, z), id, slot) order
-                if (half == 0 && r < c) {
+                if (r < c) {
                     const uint32_t id = ids[r];
-                    uint32_t lo = 0, rank = 0;
+                    uint32_t lo = 0;
                     if (!full_count) {
                         lo = r;
                         while (lo > 0 && bkey[lo - 1] == bkey[r]) lo--;
                     }
-                    rank = lo;
+                    uint32_t rank = lo;
                     for (uint32_t s = lo; s < c && (full_count || bkey[s] == bkey[r]); s++) {
                         const uint32_t ds = dx[s], is = ids[s];
                         rank += (ds < DX || (ds == DX && (is < id || (is == id && s < r)))) ? 1u : 0u;
@@ -333,34 +362,36 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                     wsl[C::W_ORDER + rank] = (unsigned char)r;
                     reinterpret_cast<uint32_t *>(wsl + C::W_IDS)[r] = id;
                 }
-                if (half == 0 && r == 0) {
+                if (r == 0) {
                     reinterpret_cast<uint32_t *>(wsl + C::W_MISC)[0] = c;
                     reinterpret_cast<uint32_t *>(wsl + C::W_MISC)[1] =
                         reinterpret_cast<const uint32_t *>(in + C::I_MISC)[1];
                 }
                 // E3: column mask of z_r -- the candidates y with acc[r][y] > theta_r
-                uint32_t *mrow = reinterpret_cast<uint32_t *>(wsl + C::W_MASK) + r * 4;
-                for (uint32_t q = half; q < 4; q += 2) {
-                    uint32_t m = 0;
+                uint32_t mw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (uint32_t q = 0; q < 4; q++) {
                     if (q * 32 < c) {
                         uint32_t g[32];
                         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * 128 + q * 32, g);
+                        uint32_t m = 0;
 #pragma unroll
                         for (int jj = 0; jj < 32; jj++) m |= __uint_as_float(g[jj]) > theta ? (1u << jj) : 0u;
                         const uint32_t live = c - q * 32;
                         if (live < 32) m &= (1u << live) - 1u;
                         if (r / 32 == q) m &= ~(1u << (r & 31));
+                        mw[q] = m;
                     }
-                    if (r < c) mrow[q] = m;
                 }
+                if (r < c) reinterpret_cast<uint4 *>(wsl + C::W_MASK)[r] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
                 fence_before();
                 mbar_arrive(bar(C::BAR_TEMPTY + tb));
                 mbar_arrive(bar(C::BAR_WFULL + ws));
             }
-            stop = named_barrier_or(1, EPI_WARPS * 32, !ok || *abort);
+            stop = named_barrier_or(bar_id, 128, !ok || *abort);
             if (stop) break;
         }
-    } else {
+    } else if (warp < PT_GATHER_WARP) {
         // ------------------------------------------------------------ walkers
         const uint32_t w = warp - PT_WALK_WARP0;
         for (uint32_t k = 0;; k++) {
@@ -415,6 +446,36 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             __syncwarp();
             mbar_arrive(bar(C::BAR_WEMPTY + w));
         }
+    } else {
+        // ------------------------------------------------------------ row gathers (one warp)
+        for (uint32_t j = 0;; j++) {
+            const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
+            if (v >= n) break;
+            const uint32_t ua = j % C::A, tb = j % C::T;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_CFULL + tb), (j / C::T) & 1, abort, a.err) &&
+                                             mbar_wait(bar(C::BAR_EMPTY_A + ua), ((j / C::A) & 1) ^ 1, abort,
+                                                       a.err)))
+                break;
+            const unsigned char *in = info(tb);
+            const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + C::I_IDS);
+            const uint32_t rows = reinterpret_cast<const uint32_t *>(in + C::I_MISC)[0] + 1;
+            const uint32_t ng = (rows + 3) / 4;  // gathers of four rows
+            const uint32_t fb = bar(C::BAR_FULL_A + ua);
+            if (lane == 0) mbar_arrive_tx(fb, ng * 512u * KB);
+            __syncwarp();
+            if ((uint32_t)lane < ng) {
+                int32_t y[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const uint32_t r = 4 * lane + e;
+                    y[e] = (int32_t)(r < rows ? ids[r] : ids[rows - 1]);
+                }
+                const uint32_t dst = sbase + C::OFF_A0 + ua * KB * REGION + lane * 4 * 128;
+#pragma unroll
+                for (int kb = 0; kb < KB; kb++) tma_gather4(dst + kb * REGION, &xmap, kb * 64, y[0], y[1], y[2], y[3], fb);
+            }
+            if (lane != 0) mbar_arrive(fb);
+        }
     }
 
     fence_before();
@@ -466,6 +527,7 @@ int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32
     a.l_max = l_max;
     a.R = R;
     a.alpha2 = alpha2;
+    a.inv_alpha2 = 1.0f / alpha2;
     a.adj = adj;
     a.deg = deg;
     a.err = device_error_word();
