@@ -1,8 +1,9 @@
 // prune_tc.cu -- A6: Alg. 2 RobustPrune on the tensor cores (byte data, d <= 128, l_max <= 127).
 //
 // For a node x with candidates z_0..z_{c-1} (its reservoir in slot order, invalid ids dropped)
-// one MMA forms the Gram matrix of the c + 1 rows [z_0, .., z_{c-1}, x] with the norm fold of the
-// leaf engine:  acc[r][s] = <x_r, x_s> - n_s / 2,  so  D(r, s) = n_r - 2 acc[r][s]  exactly.
+// one MMA forms the Gram matrix G of the c + 1 rows [z_0, .., z_{c-1}, x] (BF16 operands, FP32
+// accumulation; exact for bytes).  Its diagonal holds the squared norms n_r = G[r][r], so
+// D(r, s) = n_r + n_s - 2 G[r][s] needs no other input.
 // Alg. 2 then needs only comparisons of entries of this matrix:
 //  * order: candidates by (D(x, z), id).  D(x, z_r) is column c of row r.  The reservoir is sorted
 //    by the BF16 rounding of the same distance (then id), and rounding is monotone, so the rank of
@@ -10,20 +11,20 @@
 //    premises are checked per node; if either fails the rank is a full count.
 //  * removal: admitted y removes z iff fl(alpha^2 * D(y, z)) < D(x, z).  fl(alpha^2 * t) is
 //    monotone in t, so there is an integer T_z with  fl(alpha^2 * t) < D(x, z)  <=>  t < T_z,
-//    and D(y, z) = D(z, y); hence y removes z iff acc[z][y] > (n_z - T_z) / 2.  Row z of the
-//    accumulator gives, one compare per entry, the set of candidates that would remove z (its
-//    "column mask").
+//    and D(y, z) = D(z, y); hence y removes z iff G[z][y] - n_y / 2 > (n_z - T_z) / 2.  Row z of
+//    the accumulator gives, with one subtraction and one compare per entry, the set of
+//    candidates that would remove z (its "column mask").
 //  * walk: in rank order a candidate is admitted unless its column mask meets the admitted set
 //    (the removal loop of Alg. 2 and its lazy form coincide), up to R admissions.
 //
-// Persistent CTA (one per SM, 21 warps):
-//   warp 0       node info: reservoir slots and norms (loaded a node ahead), compaction of the
-//                valid ids, BF16 keys, norm pieces
-//   warp 20      TMA gather4 of the node's rows (ids from the node info)
-//   warp 1       owns TMEM (4 x 128 columns); one thread issues the Gram MMAs
-//   warps 2-13   epilogue: three groups of four warps (one per TMEM lane quarter, a thread per
-//                row) take turns on nodes: D(x, .), thresholds, ranks, column masks -> walk slot
-//   warps 14-19  walkers: one node at a time each, write adj / deg
+// Persistent CTA (one per SM, 20 warps):
+//   warps 0-11   epilogue: three groups of four warps (one per TMEM lane quarter, a thread per
+//                row) take turns on nodes: norms, D(x, .), thresholds, ranks, column masks
+//   warp 12      owns TMEM (4 x 128 columns); one thread issues the Gram MMAs
+//   warp 15      node info: reservoir slots (loaded two nodes ahead), compaction of the valid
+//                ids, BF16 keys
+//   warps 17-18  TMA gather4 of the rows of alternate nodes (ids from the node info)
+//   warps 13, 14, 16, 19  walkers: write adj / deg
 // Waits are bounded as in the other engines (DERR_TIMEOUT; TMEM is still released).
 #include "tc_common.cuh"
 
@@ -33,13 +34,23 @@ namespace {
 
 using namespace tc;
 
-constexpr int PT_GROUPS = 3;                                     // epilogue groups of 4 warps
+// Warp roles.  A warp reaches TMEM lanes 32 (w % 4) .. +31 and runs on scheduler w % 4, so the
+// epilogue groups are warps 4g .. 4g + 3, and the other roles are placed so that each scheduler
+// carries a similar load (the rows of lane quarter 0, the nearest candidates, are always
+// occupied; quarter 3 is the lightest).
+constexpr int PT_GROUPS = 3;                 // epilogue groups of 4 warps: warps 0 .. 11
 constexpr int PT_EPI_WARPS = 4 * PT_GROUPS;
-constexpr int PT_WALKERS = 6;
-constexpr int PT_WALK_WARP0 = 2 + PT_EPI_WARPS;
-constexpr int PT_GATHER_WARP = PT_WALK_WARP0 + PT_WALKERS;
-constexpr int PT_THREADS = (PT_GATHER_WARP + 1) * 32;
+constexpr int PT_MMA_WARP = 12;              // scheduler 0
+constexpr int PT_INFO_WARP = 15;             // scheduler 3
+constexpr int PT_WALKERS = 4;                // warps 13, 14, 16, 19
+constexpr int PT_GATHERERS = 2;              // warps 17, 18
+constexpr int PT_THREADS = 20 * 32;
+__host__ __device__ constexpr int walker_of(int warp) {
+    return warp == 13 ? 0 : warp == 14 ? 1 : warp == 16 ? 2 : warp == 19 ? 3 : -1;
+}
+__host__ __device__ constexpr int gatherer_of(int warp) { return warp == 17 ? 0 : warp == 18 ? 1 : -1; }
 constexpr uint32_t PT_MAXC = 127;                                 // candidates per node (+ the node)
+constexpr int W_MASK_OFF = 0, W_IDS_OFF = 2048, W_ORDER_OFF = 2560, W_MISC_OFF = 2688, W_SLOT_BYTES = 2704;
 
 struct PtArgs {
     const uint64_t *res;   // n x l_max reservoir slots
@@ -55,28 +66,29 @@ struct PtArgs {
 template <int KB>
 struct PtCfg {
     static constexpr int A = 4;            // gathered row tiles in flight
-    static constexpr int T = 4;            // accumulator buffers = node-info slots
-    static constexpr int W = PT_WALKERS;   // walk slots (walker w owns slot w)
-    // node info, producer -> epilogue: ids[128] u32, norms[128] i32, BF16 keys[128] u16, c, v
-    static constexpr int I_IDS = 0, I_NRM = 512, I_BKEY = 1024, I_MISC = 1280, I_BYTES = 1296;
+    static constexpr int T = 4;            // accumulator buffers
+    static constexpr int I = 8;            // node-info slots (info and gathers run ahead)
+    static constexpr int W = 2 * PT_WALKERS;  // walk slots (walker w alternates between w and w + PT_WALKERS)
+    // node info, producer -> epilogue: ids[128] u32, BF16 keys[128] u16, c, v, n_x
+    static constexpr int I_IDS = 0, I_BKEY = 512, I_MISC = 768, I_BYTES = 784;
     // walk slot, epilogue -> walker: column masks[128] x 4 u32, ids[128], order[128] u8, c, v
-    static constexpr int W_MASK = 0, W_IDS = 2048, W_ORDER = 2560, W_MISC = 2688, W_BYTES = 2704;
+    static constexpr int W_MASK = W_MASK_OFF, W_IDS = W_IDS_OFF, W_ORDER = W_ORDER_OFF, W_MISC = W_MISC_OFF,
+                         W_BYTES = W_SLOT_BYTES;
     static constexpr int OFF_A0 = 0;
-    static constexpr int OFF_AN = OFF_A0 + A * KB * REGION;
-    static constexpr int OFF_BN = OFF_AN + REGION;          // a 32-byte norm slice per A buffer
-    static constexpr int OFF_INFO = OFF_BN + REGION;
-    static constexpr int OFF_WS = OFF_INFO + T * I_BYTES;
-    static constexpr int OFF_DX = OFF_WS + W * W_BYTES;     // per group 2 x 128 u32: D(x, z_r) by row
-    static constexpr int OFF_BAR = OFF_DX + PT_GROUPS * 2 * 128 * 4;
-    static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = A, BAR_CFULL = 2 * A, BAR_TFULL = 2 * A + T,
-                         BAR_TEMPTY = 2 * A + 2 * T, BAR_WFULL = 2 * A + 3 * T, BAR_WEMPTY = 2 * A + 3 * T + W,
-                         NBAR = 2 * A + 3 * T + 2 * W;
+    static constexpr int OFF_INFO = OFF_A0 + A * KB * REGION;
+    static constexpr int OFF_WS = OFF_INFO + I * I_BYTES;
+    // per group, two node buffers of: D(x, z_r) u32[128], n_r / 2 float[128]
+    static constexpr int OFF_DX = OFF_WS + W * W_BYTES;
+    static constexpr int OFF_BAR = OFF_DX + PT_GROUPS * 2 * 1024;
+    static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = A, BAR_CFULL = 2 * A, BAR_IEMPTY = 2 * A + I,
+                         BAR_TFULL = 2 * A + 2 * I, BAR_TEMPTY = 2 * A + 2 * I + T,
+                         BAR_WFULL = 2 * A + 2 * I + 2 * T, BAR_WEMPTY = 2 * A + 2 * I + 2 * T + W,
+                         NBAR = 2 * A + 2 * I + 2 * T + 2 * W;
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;     // tmem base, abort flag
     static constexpr int BYTES = OFF_MISC + 16;
     static constexpr int SMEM = BYTES + 1024;
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(T * 128 <= (int)TMEM_COLS, "TMEM budget");
-    static_assert(A <= 4, "norm slices per 128-byte row");
     static_assert(I_BYTES % 16 == 0 && W_BYTES % 16 == 0, "slot alignment");
 };
 
@@ -133,11 +145,14 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::A; i++) {
-            mbar_init(bar(C::BAR_FULL_A + i), 64);  // info warp + gather warp
+            mbar_init(bar(C::BAR_FULL_A + i), 32);  // the gather warp
             mbar_init(bar(C::BAR_EMPTY_A + i), 1);
         }
-        for (int i = 0; i < C::T; i++) {
+        for (int i = 0; i < C::I; i++) {
             mbar_init(bar(C::BAR_CFULL + i), 32);
+            mbar_init(bar(C::BAR_IEMPTY + i), 128);
+        }
+        for (int i = 0; i < C::T; i++) {
             mbar_init(bar(C::BAR_TFULL + i), 1);
             mbar_init(bar(C::BAR_TEMPTY + i), 128);
         }
@@ -149,41 +164,22 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
     }
-    if (warp == MMA_WARP) tmem_alloc(sbase + C::OFF_MISC, TMEM_COLS);
+    if (warp == PT_MMA_WARP) tmem_alloc(sbase + C::OFF_MISC, TMEM_COLS);
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == PRODUCER_WARP) {
-        // ------------------------------------------------------------ producer (one warp)
-        for (uint32_t r = lane; r < 128u; r += 32) {
-            const uint32_t one = 0x3F80u;  // bf16 1.0
-            const uint32_t base = sbase + C::OFF_AN + r * 128;
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((0u ^ (r & 7)) << 4)),
-                         "r"(one | (one << 16)), "r"(one | (one << 16)), "r"(0u), "r"(0u)
-                         : "memory");
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((1u ^ (r & 7)) << 4)), "r"(0u),
-                         "r"(0u), "r"(0u), "r"(0u)
-                         : "memory");
-            // every buffer's 32-byte norm slice starts zero; a node rewrites only its first 8 bytes
-            for (uint32_t q = 0; q < 2u * C::A; q++)
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + C::OFF_BN + r * 128 +
-                                                                              ((q ^ (r & 7)) << 4)),
-                             "r"(0u), "r"(0u), "r"(0u), "r"(0u)
-                             : "memory");
-        }
-        fence_proxy_async();
-        // Software pipeline: the reservoir slots of node j + 1 and the norms of its valid
-        // candidates are loaded while node j is issued (two dependent global round trips that a
-        // node would otherwise wait for in turn).
+    if (warp == PT_INFO_WARP) {
+        // ------------------------------------------------------------ node info (one warp)
+        // Software pipeline: the reservoir row, count and node norm of node j + 2 are requested
+        // while node j is compacted, so their latency is hidden behind two nodes of work.
         struct Pre {
             uint64_t key[4];
-            int32_t nr[4];
             int32_t nv;
             uint32_t c;
         };
-        auto load_keys = [&](uint64_t v, Pre &p) {
+        auto load = [&](uint64_t v, Pre &p) {
             p.c = 0;
             p.nv = 0;
             if (v >= n) return;
@@ -197,75 +193,49 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 p.key[k] = s < a.l_max ? a.res[v * a.l_max + s] : 0ull;
             }
         };
-        auto load_norms = [&](Pre &p) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t s = 32 * k + lane;
-                const uint32_t id = (uint32_t)(p.key[k] >> 16);
-                p.nr[k] = (s < p.c && (uint64_t)id < n) ? a.sqn[id] : 0;
-            }
-        };
-        Pre cur, nxt;
-        load_keys(blockIdx.x, cur);
-        load_norms(cur);
-        load_keys(blockIdx.x + (uint64_t)gridDim.x, nxt);
+        Pre p0, p1;
+        load(blockIdx.x, p0);
+        load(blockIdx.x + (uint64_t)gridDim.x, p1);
         for (uint32_t j = 0;; j++) {
             const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
             if (v >= n) break;
-            const uint32_t ua = j % C::A, tb = j % C::T;
-            Pre nn;
-            load_keys(v + 2 * (uint64_t)gridDim.x, nn);
-            load_norms(nxt);
-            const uint32_t c = cur.c;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_TEMPTY + tb), ((j / C::T) & 1) ^ 1, abort, a.err)))
+            const uint32_t ib = j % C::I;
+            Pre p2;
+            load(v + 2 * (uint64_t)gridDim.x, p2);
+            const uint32_t c = p0.c;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_IEMPTY + ib), ((j / C::I) & 1) ^ 1, abort, a.err)))
                 break;
-            unsigned char *in = info(tb);
+            unsigned char *in = info(ib);
             uint32_t *ids = reinterpret_cast<uint32_t *>(in + C::I_IDS);
-            int32_t *nrm = reinterpret_cast<int32_t *>(in + C::I_NRM);
             uint16_t *bkey = reinterpret_cast<uint16_t *>(in + C::I_BKEY);
             uint32_t cc = 0;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const uint32_t s = 32 * k + lane;
-                const uint32_t id = (uint32_t)(cur.key[k] >> 16);
+                const uint32_t id = (uint32_t)(p0.key[k] >> 16);
                 const bool in_range = s < c && (uint64_t)id < n;
                 if (s < c && !in_range) atomicOr(a.err, DERR_RANGE);
                 const unsigned m = __ballot_sync(0xffffffffu, in_range);
                 if (in_range) {
                     const uint32_t pos = cc + __popc(m & ((1u << lane) - 1u));
                     ids[pos] = id;
-                    nrm[pos] = cur.nr[k];
-                    bkey[pos] = (uint16_t)(cur.key[k] >> 48);
+                    bkey[pos] = (uint16_t)(p0.key[k] >> 48);
                 }
                 cc += __popc(m);
             }
             if (lane == 0) {
                 ids[cc] = (uint32_t)v;
-                nrm[cc] = cur.nv;
-                reinterpret_cast<uint32_t *>(in + C::I_MISC)[0] = cc;
-                reinterpret_cast<uint32_t *>(in + C::I_MISC)[1] = (uint32_t)v;
+                uint32_t *misc = reinterpret_cast<uint32_t *>(in + C::I_MISC);
+                misc[0] = cc;
+                misc[1] = (uint32_t)v;
+                misc[2] = (uint32_t)p0.nv;
             }
             __syncwarp();
-            mbar_arrive(bar(C::BAR_CFULL + tb));
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + ua), ((j / C::A) & 1) ^ 1, abort, a.err)))
-                break;
-            // -(n_r / 2) pieces of every row in this buffer's norm slice; zero past the rows
-            const uint32_t rows = cc + 1;
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                const uint32_t r = 4 * lane + e;
-                const uint2 pc = neg_half_norm_pieces(r < rows ? (uint32_t)nrm[r] : 0u);
-                asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(sbase + C::OFF_BN + r * 128 +
-                                                                     (((2 * ua) ^ (r & 7)) << 4)),
-                             "r"(pc.x), "r"(pc.y)
-                             : "memory");
-            }
-            fence_proxy_async();
-            mbar_arrive(bar(C::BAR_FULL_A + ua));
-            cur = nxt;
-            nxt = nn;
+            mbar_arrive(bar(C::BAR_CFULL + ib));
+            p0 = p1;
+            p1 = p2;
         }
-    } else if (warp == MMA_WARP) {
+    } else if (warp == PT_MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t issued_j = 0;
@@ -273,15 +243,15 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             for (uint32_t j = 0;; j++) {
                 const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
                 if (v >= n) break;
-                const uint32_t ua = j % C::A, tb = j % C::T;
-                if (!mbar_wait(bar(C::BAR_CFULL + tb), (j / C::T) & 1, abort, a.err) ||
+                const uint32_t ua = j % C::A, tb = j % C::T, ib = j % C::I;
+                if (!mbar_wait(bar(C::BAR_CFULL + ib), (j / C::I) & 1, abort, a.err) ||
                     !mbar_wait(bar(C::BAR_FULL_A + ua), (j / C::A) & 1, abort, a.err) ||
                     !mbar_wait(bar(C::BAR_TEMPTY + tb), ((j / C::T) & 1) ^ 1, abort, a.err)) {
                     stop = true;
                     break;
                 }
                 fence_after();
-                const uint32_t rows = reinterpret_cast<const uint32_t *>(info(tb) + C::I_MISC)[0] + 1;
+                const uint32_t rows = reinterpret_cast<const uint32_t *>(info(ib) + C::I_MISC)[0] + 1;
                 const uint32_t idesc = idesc_bf16(128, (rows + 15) & ~15u);
                 const uint32_t aB = sbase + C::OFF_A0 + ua * KB * REGION;
                 const uint32_t d = tmem + tb * 128;
@@ -290,8 +260,6 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                     const uint64_t desc = smem_desc_sw128(aB + (kk >> 2) * REGION + (kk & 3) * 32);
                     mma_bf16(d, desc, desc, idesc, kk > 0 ? 1u : 0u);
                 }
-                mma_bf16(d, smem_desc_sw128(sbase + C::OFF_AN), smem_desc_sw128(sbase + C::OFF_BN + ua * 32), idesc,
-                         1u);
                 mma_commit(bar(C::BAR_EMPTY_A + ua));
                 mma_commit(bar(C::BAR_TFULL + tb));
                 any = true;
@@ -301,9 +269,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 mbar_wait(bar(C::BAR_TFULL + issued_j % C::T), (issued_j / C::T) & 1, abort, a.err);
         }
         __syncwarp();
-    } else if (warp < PT_WALK_WARP0) {
+    } else if (warp < PT_EPI_WARPS) {
         // ------------------------------------------------------------ epilogue (groups of 4 warps)
-        const uint32_t grp = (warp - EPI_WARP0) >> 2;  // group: nodes j = grp, grp + PT_GROUPS, ...
+        const uint32_t grp = warp >> 2;                 // group: nodes j = grp, grp + PT_GROUPS, ...
         const int quarter = warp & 3;                   // TMEM lane quarter this warp may access
         const uint32_t r = quarter * 32 + lane;         // row = candidate slot
         const uint32_t bar_id = 1 + grp;
@@ -312,17 +280,17 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             const uint32_t j = grp + k * PT_GROUPS;
             const uint64_t vv = blockIdx.x + (uint64_t)j * gridDim.x;
             if (vv >= n) break;
-            const uint32_t tb = j % C::T, ws = j % C::W;
+            const uint32_t tb = j % C::T, ws = j % C::W, ib = j % C::I;
             const bool ok = !stop && __all_sync(0xffffffffu,
                                                  mbar_wait(bar(C::BAR_TFULL + tb), (j / C::T) & 1, abort, a.err) &&
-                                                     mbar_wait(bar(C::BAR_CFULL + tb), (j / C::T) & 1, abort, a.err) &&
+                                                     mbar_wait(bar(C::BAR_CFULL + ib), (j / C::I) & 1, abort, a.err) &&
                                                      mbar_wait(bar(C::BAR_WEMPTY + ws), ((j / C::W) & 1) ^ 1, abort,
                                                                a.err));
-            const unsigned char *in = info(tb);
+            const unsigned char *in = info(ib);
             const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + C::I_IDS);
-            const int32_t *nrm = reinterpret_cast<const int32_t *>(in + C::I_NRM);
             const uint16_t *bkey = reinterpret_cast<const uint16_t *>(in + C::I_BKEY);
-            uint32_t *dx = reinterpret_cast<uint32_t *>(smem + C::OFF_DX) + (grp * 2 + (k & 1)) * 128;
+            uint32_t *dx = reinterpret_cast<uint32_t *>(smem + C::OFF_DX + (grp * 2 + (k & 1)) * 1024);
+            float *hn = reinterpret_cast<float *>(dx + 128);
             unsigned char *wsl = wslot(ws);
             uint32_t c = 0, DX = 0;
             float theta = 0.0f;
@@ -330,16 +298,21 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             if (ok) {
                 fence_after();
                 c = reinterpret_cast<const uint32_t *>(in + C::I_MISC)[0];
-                // E1: D(x, z_r) from column c of row r; the removal threshold of z_r
+                const float nx = (float)reinterpret_cast<const int32_t *>(in + C::I_MISC)[2];
+                // E1: n_r from the diagonal (column r lies in chunk `quarter`), D(x, z_r) from
+                // column c, the removal threshold of z_r
+                const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + tb * 128;
                 uint32_t g[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * 128 + (c & ~31u), g);
+                tmem_ld32(trow + quarter * 32, g);
+                const float nr = __uint_as_float(pick32(g, lane));  // exact integer < 2^23
+                hn[r] = 0.5f * nr;
+                tmem_ld32(trow + (c & ~31u), g);
                 if (r < c) {
-                    const float acc = __uint_as_float(pick32(g, c & 31u));
-                    const int32_t nr = nrm[r];
-                    const float dxf = __fmaf_rn(-2.0f, acc, (float)nr);  // exact integer
+                    const float gx = __uint_as_float(pick32(g, c & 31u));
+                    const float dxf = __fmaf_rn(-2.0f, gx, nr + nx);    // exact integer < 2^24
                     DX = (uint32_t)dxf;
                     const uint32_t T = removal_threshold(DX, a.alpha2, a.inv_alpha2);
-                    theta = ((float)nr - (float)T) * 0.5f;             // exact (multiple of 1/2)
+                    theta = (nr - (float)T) * 0.5f;                    // exact (multiple of 1/2)
                     dx[r] = DX;
                     bad = bf16_key(dxf) != bkey[r] || (r > 0 && bkey[r - 1] > bkey[r]);
                 }
@@ -367,16 +340,25 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                     reinterpret_cast<uint32_t *>(wsl + C::W_MISC)[1] =
                         reinterpret_cast<const uint32_t *>(in + C::I_MISC)[1];
                 }
-                // E3: column mask of z_r -- the candidates y with acc[r][y] > theta_r
+                mbar_arrive(bar(C::BAR_IEMPTY + ib));  // node info no longer read
+                // E3: column mask of z_r -- the candidates y with G[r][y] - n_y / 2 > theta_r
+                // (both sides multiples of 1/2 below 2^23: exact)
                 uint32_t mw[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
                 for (uint32_t q = 0; q < 4; q++) {
                     if (q * 32 < c) {
                         uint32_t g[32];
                         tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * 128 + q * 32, g);
+                        const float4 *h4 = reinterpret_cast<const float4 *>(hn + q * 32);
                         uint32_t m = 0;
 #pragma unroll
-                        for (int jj = 0; jj < 32; jj++) m |= __uint_as_float(g[jj]) > theta ? (1u << jj) : 0u;
+                        for (int j4 = 0; j4 < 8; j4++) {
+                            const float4 h = h4[j4];
+                            m |= __fsub_rn(__uint_as_float(g[4 * j4 + 0]), h.x) > theta ? (1u << (4 * j4 + 0)) : 0u;
+                            m |= __fsub_rn(__uint_as_float(g[4 * j4 + 1]), h.y) > theta ? (1u << (4 * j4 + 1)) : 0u;
+                            m |= __fsub_rn(__uint_as_float(g[4 * j4 + 2]), h.z) > theta ? (1u << (4 * j4 + 2)) : 0u;
+                            m |= __fsub_rn(__uint_as_float(g[4 * j4 + 3]), h.w) > theta ? (1u << (4 * j4 + 3)) : 0u;
+                        }
                         const uint32_t live = c - q * 32;
                         if (live < 32) m &= (1u << live) - 1u;
                         if (r / 32 == q) m &= ~(1u << (r & 31));
@@ -391,50 +373,53 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             stop = named_barrier_or(bar_id, 128, !ok || *abort);
             if (stop) break;
         }
-    } else if (warp < PT_GATHER_WARP) {
+    } else if (walker_of(warp) >= 0) {
         // ------------------------------------------------------------ walkers
-        const uint32_t w = warp - PT_WALK_WARP0;
+        // Walker w takes nodes j = w, w + PT_WALKERS, ... and alternates between its two walk slots
+        // (w and w + PT_WALKERS).  Per block of 32 ranks the lanes drop, with one vote, every
+        // candidate removed by an earlier admission; then each admission (the first remaining
+        // lane) removes, with one vote, the later lanes whose column mask holds it.
+        const uint32_t w = walker_of(warp);
+        const uint32_t R = a.R;
         for (uint32_t k = 0;; k++) {
-            const uint32_t j = w + k * C::W;
-            const uint64_t vv = blockIdx.x + (uint64_t)j * gridDim.x;
-            if (vv >= n) break;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_WFULL + w), k & 1, abort, a.err))) break;
-            const unsigned char *wsl = wslot(w);
+            const uint32_t j = w + k * PT_WALKERS;
+            if (blockIdx.x + (uint64_t)j * gridDim.x >= n) break;
+            const uint32_t sl = j % C::W;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_WFULL + sl), (j / C::W) & 1, abort, a.err))) break;
+            const unsigned char *wsl = wslot(sl);
             const uint32_t c = reinterpret_cast<const uint32_t *>(wsl + C::W_MISC)[0];
             const uint64_t v = reinterpret_cast<const uint32_t *>(wsl + C::W_MISC)[1];
             const uint4 *mask = reinterpret_cast<const uint4 *>(wsl + C::W_MASK);
             const uint32_t *ids = reinterpret_cast<const uint32_t *>(wsl + C::W_IDS);
             const unsigned char *order = wsl + C::W_ORDER;
-            const uint32_t R = a.R;
             uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0;  // admitted slots
             uint32_t e = 0;
             uint32_t out[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
             for (uint32_t b = 0; b * 32 < c && e < R; b++) {
                 const uint32_t i = b * 32 + lane;
-                const uint32_t tl = i < c ? order[i] : 0u;
-                const uint4 cm = i < c ? mask[tl] : make_uint4(0, 0, 0, 0);
-                const uint32_t nb = c - b * 32 < 32 ? c - b * 32 : 32;
-#pragma unroll 4
-                for (uint32_t jj = 0; jj < nb; jj++) {
-                    const uint32_t t = __shfl_sync(0xffffffffu, tl, jj);
-                    const uint32_t cx = __shfl_sync(0xffffffffu, cm.x, jj), cy = __shfl_sync(0xffffffffu, cm.y, jj);
-                    const uint32_t cz = __shfl_sync(0xffffffffu, cm.z, jj), cw = __shfl_sync(0xffffffffu, cm.w, jj);
-                    if (((cx & A0) | (cy & A1) | (cz & A2) | (cw & A3)) == 0u) {
-                        const uint32_t bit = 1u << (t & 31);
-                        const uint32_t wd = t >> 5;
-                        A0 |= wd == 0 ? bit : 0u;
-                        A1 |= wd == 1 ? bit : 0u;
-                        A2 |= wd == 2 ? bit : 0u;
-                        A3 |= wd == 3 ? bit : 0u;
-                        const uint32_t id = ids[t];
-                        const bool mine = (e & 31) == (uint32_t)lane;
-                        const uint32_t o = e >> 5;
-                        out[0] = (mine && o == 0) ? id : out[0];
-                        out[1] = (mine && o == 1) ? id : out[1];
-                        out[2] = (mine && o == 2) ? id : out[2];
-                        out[3] = (mine && o == 3) ? id : out[3];
-                        if (++e == R) break;
-                    }
+                const bool valid = i < c;
+                const uint32_t tl = valid ? order[i] : 0u;
+                const uint4 cm = valid ? mask[tl] : make_uint4(0, 0, 0, 0);
+                unsigned U = __ballot_sync(0xffffffffu,
+                                           valid && ((cm.x & A0) | (cm.y & A1) | (cm.z & A2) | (cm.w & A3)) == 0u);
+                while (U != 0u && e < R) {
+                    const uint32_t u = __ffs(U) - 1;
+                    const uint32_t t = __shfl_sync(0xffffffffu, tl, u);
+                    const uint32_t wd = t >> 5, bit = 1u << (t & 31);
+                    A0 |= wd == 0 ? bit : 0u;
+                    A1 |= wd == 1 ? bit : 0u;
+                    A2 |= wd == 2 ? bit : 0u;
+                    A3 |= wd == 3 ? bit : 0u;
+                    const uint32_t id = ids[t];
+                    const uint32_t o = e >> 5;
+                    const bool mine = (e & 31) == (uint32_t)lane;
+                    out[0] = (mine && o == 0) ? id : out[0];
+                    out[1] = (mine && o == 1) ? id : out[1];
+                    out[2] = (mine && o == 2) ? id : out[2];
+                    out[3] = (mine && o == 3) ? id : out[3];
+                    e++;
+                    const uint32_t mw = wd == 0 ? cm.x : wd == 1 ? cm.y : wd == 2 ? cm.z : cm.w;
+                    U &= ~__ballot_sync(0xffffffffu, (mw >> (t & 31)) & 1u) & ~(1u << u);
                 }
             }
 #pragma unroll
@@ -444,19 +429,19 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             }
             if (lane == 0) a.deg[v] = e;
             __syncwarp();
-            mbar_arrive(bar(C::BAR_WEMPTY + w));
+            mbar_arrive(bar(C::BAR_WEMPTY + sl));
         }
-    } else {
-        // ------------------------------------------------------------ row gathers (one warp)
-        for (uint32_t j = 0;; j++) {
+    } else if (gatherer_of(warp) >= 0) {
+        // ------------------------------------------------------------ row gathers (two warps)
+        for (uint32_t j = gatherer_of(warp);; j += PT_GATHERERS) {
             const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
             if (v >= n) break;
-            const uint32_t ua = j % C::A, tb = j % C::T;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_CFULL + tb), (j / C::T) & 1, abort, a.err) &&
+            const uint32_t ua = j % C::A, ib = j % C::I;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_CFULL + ib), (j / C::I) & 1, abort, a.err) &&
                                              mbar_wait(bar(C::BAR_EMPTY_A + ua), ((j / C::A) & 1) ^ 1, abort,
                                                        a.err)))
                 break;
-            const unsigned char *in = info(tb);
+            const unsigned char *in = info(ib);
             const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + C::I_IDS);
             const uint32_t rows = reinterpret_cast<const uint32_t *>(in + C::I_MISC)[0] + 1;
             const uint32_t ng = (rows + 3) / 4;  // gathers of four rows
@@ -480,7 +465,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 
     fence_before();
     __syncthreads();
-    if (warp == MMA_WARP) {
+    if (warp == PT_MMA_WARP) {
         fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
     }
