@@ -6,11 +6,14 @@
 // of the whole stream, so the GPU inserts a whole batch at once:
 //   1. count candidates per destination, prefix-sum, scatter each candidate's slot
 //      [ordered bf16 dist:16][src:32][h_dst(src):16] next to its destination's others;
-//   2. one warp per node sorts (old reservoir + new slots) in shared memory and walks them in
-//      ascending order, keeping a slot iff its hash bucket has not been seen yet
-//      (__match_any_sync within a chunk of 32, a bitmap of 2^m bits across chunks), until
-//      l_max are kept.  Batches larger than the shared buffer are merged chunk by chunk.
+//   2. one warp per node sorts (old reservoir + new slots) -- in registers with shuffles when
+//      they fit in 128 (four per lane), else in shared memory -- and walks them in ascending
+//      order, keeping a slot iff its hash bucket has not been seen yet (__match_any_sync within a
+//      chunk of 32, a bitmap of 2^m bits across chunks), until l_max are kept.  Batches larger
+//      than the shared buffer are merged chunk by chunk.
 #include "internal.cuh"
+
+#include <type_traits>
 
 namespace pipnn {
 
@@ -18,7 +21,7 @@ namespace {
 constexpr int HP_WARPS = 8;
 constexpr int HP_BUF = 512;   // slots per warp buffer
 
-__global__ void hp_count(const uint32_t *dst, const uint32_t *src, uint64_t count, uint64_t n, uint64_t *per_node,
+__global__ void hp_count(const uint32_t *dst, const uint32_t *src, uint64_t count, uint64_t n, unsigned *per_node,
                          unsigned *err) {
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < count; e += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t v = dst[e], c = src[e];
@@ -26,7 +29,15 @@ __global__ void hp_count(const uint32_t *dst, const uint32_t *src, uint64_t coun
             atomicOr(err, DERR_RANGE);
             continue;
         }
-        if (v != c) atomicAdd((unsigned long long *)&per_node[v], 1ull);
+        if (v != c) atomicAdd(&per_node[v], 1u);
+    }
+}
+
+// start[v] = per_node[v] (to be prefix-summed); per_node[v] = 0 (it becomes the fill counter).
+__global__ void hp_widen(unsigned *per_node, uint64_t n, uint64_t *start) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        start[v] = per_node[v];
+        per_node[v] = 0;
     }
 }
 
@@ -38,9 +49,52 @@ __global__ void hp_scatter(const uint32_t *dst, const uint32_t *src, const float
         // residualised hash h_v(c): bit i = [Sketch(c)_i >= Sketch(v)_i]  (Eq. 1)
         uint32_t h = 0;
         const float *sv = S + (uint64_t)v * m, *sc = S + (uint64_t)c * m;
-        for (uint32_t i = 0; i < m; i++) h |= (__ldg(sc + i) >= __ldg(sv + i) ? 1u : 0u) << i;
+        if ((m & 3u) == 0) {
+            // rows of a multiple of four floats start 16-byte aligned: vector loads
+            const float4 *v4 = reinterpret_cast<const float4 *>(sv), *c4 = reinterpret_cast<const float4 *>(sc);
+            for (uint32_t i = 0; i < m / 4; i++) {
+                const float4 a = __ldg(c4 + i), b = __ldg(v4 + i);
+                h |= ((a.x >= b.x ? 1u : 0u) | (a.y >= b.y ? 2u : 0u) | (a.z >= b.z ? 4u : 0u) |
+                      (a.w >= b.w ? 8u : 0u)) << (4 * i);
+            }
+        } else {
+            for (uint32_t i = 0; i < m; i++) h |= (__ldg(sc + i) >= __ldg(sv + i) ? 1u : 0u) << i;
+        }
         uint32_t pos = atomicAdd(&fill[v], 1u);
         slots[start[v] + pos] = reservoir_slot(dist[e], c, h);
+    }
+}
+
+// Ascending bitonic sort of 32 * E keys held E per lane (element E * lane + q in K[q]):
+// exchanges within a lane for distances below E, shuffles across lanes for the rest.
+template <int E>
+__device__ __forceinline__ void warp_sort_regs(uint64_t (&K)[E], int lane) {
+#pragma unroll
+    for (uint32_t k = 2; k <= 32u * E; k <<= 1) {
+#pragma unroll
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            if (j >= (uint32_t)E) {
+#pragma unroll
+                for (int q = 0; q < E; q++) {
+                    const uint32_t i = E * lane + q;
+                    const uint64_t o = __shfl_xor_sync(0xffffffffu, K[q], j / E);
+                    const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+                    K[q] = take_min ? (o < K[q] ? o : K[q]) : (o > K[q] ? o : K[q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < E; q++) {
+                    if ((q & j) == 0) {
+                        const uint32_t i = E * lane + q;
+                        const uint64_t lo = K[q], hi = K[q | j];
+                        const bool up = (i & k) == 0;
+                        const bool sw = (lo > hi) == up;
+                        K[q] = sw ? hi : lo;
+                        K[q | j] = sw ? lo : hi;
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -84,18 +138,9 @@ __global__ void __launch_bounds__(HP_WARPS * 32) hp_merge(uint64_t n, uint32_t m
             for (uint32_t t = cur + lane; t < l_max; t += 32) res[v * l_max + t] = ~0ull;
             continue;
         }
-        for (uint32_t t = lane; t < cur; t += 32) buf[t] = res[v * l_max + t];
-        while (a < b) {
-            uint32_t take = (uint32_t)((b - a) < (uint64_t)(HP_BUF - cur) ? (b - a) : (uint64_t)(HP_BUF - cur));
-            for (uint32_t t = lane; t < take; t += 32) buf[cur + t] = slots[a + t];
-            a += take;
-            const uint32_t nb = cur + take;
-            uint32_t P = 32;
-            while (P < nb) P <<= 1;
-            for (uint32_t t = nb + lane; t < P; t += 32) buf[t] = ~0ull;
-            __syncwarp();
-            warp_bitonic_sort(buf, P, lane);
-            // walk ascending, keep the first slot of every unseen hash bucket
+        // walk buf[0 .. nb) ascending, keep the first slot of every unseen hash bucket (compacted
+        // to the front of buf); returns how many were kept, at most l_max
+        auto walk = [&](uint32_t nb) {
             uint32_t out = 0;
             for (uint32_t base = 0; base < nb && out < l_max; base += 32) {
                 const uint32_t i = base + lane;
@@ -115,9 +160,44 @@ __global__ void __launch_bounds__(HP_WARPS * 32) hp_merge(uint64_t n, uint32_t m
                 out += __popc(km);
                 __syncwarp();
             }
-            cur = out < l_max ? out : l_max;
             for (uint32_t w = lane; w < bm_words; w += 32) seen[w] = 0;
             __syncwarp();
+            return out < l_max ? out : l_max;
+        };
+        // old + new slots, E per lane, sorted in registers
+        auto sort_regs = [&](auto tag) {
+            constexpr int E = decltype(tag)::value;
+            const uint32_t nb = cur + (uint32_t)(b - a);
+            uint64_t K[E];
+#pragma unroll
+            for (int q = 0; q < E; q++) {
+                const uint32_t t = E * lane + q;
+                K[q] = t < cur ? res[v * l_max + t] : (t < nb ? slots[a + (t - cur)] : ~0ull);
+            }
+            warp_sort_regs<E>(K, lane);
+#pragma unroll
+            for (int q = 0; q < E; q++) buf[E * lane + q] = K[q];
+            __syncwarp();
+            cur = walk(nb);
+        };
+        // (eight per lane would cover 256 but doubles the kernel's registers, which costs more
+        // occupancy than the larger nodes gain)
+        if ((uint64_t)cur + (b - a) <= 128) {
+            sort_regs(std::integral_constant<int, 4>());
+        } else {
+            for (uint32_t t = lane; t < cur; t += 32) buf[t] = res[v * l_max + t];
+            while (a < b) {
+                uint32_t take = (uint32_t)((b - a) < (uint64_t)(HP_BUF - cur) ? (b - a) : (uint64_t)(HP_BUF - cur));
+                for (uint32_t t = lane; t < take; t += 32) buf[cur + t] = slots[a + t];
+                a += take;
+                const uint32_t nb = cur + take;
+                uint32_t P = 32;
+                while (P < nb) P <<= 1;
+                for (uint32_t t = nb + lane; t < P; t += 32) buf[t] = ~0ull;
+                __syncwarp();
+                warp_bitonic_sort(buf, P, lane);
+                cur = walk(nb);
+            }
         }
         for (uint32_t t = lane; t < l_max; t += 32) res[v * l_max + t] = t < cur ? buf[t] : ~0ull;
         if (lane == 0) cnt[v] = cur;
@@ -145,7 +225,9 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
     PIPNN_TRY(ws.zeros(&fill, n));
     PIPNN_TRY(ws.alloc(&tot, 1));
     if (count) {
-        hp_count<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, count, n, start, err);
+        hp_count<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, count, n, fill, err);
+        PIPNN_LAUNCH_CHECK();
+        hp_widen<<<grid_for(n, 256), 256, 0, stream()>>>(fill, n, start);
         PIPNN_LAUNCH_CHECK();
     }
     PIPNN_TRY(exclusive_scan_u64(start, start, n, tot, ws));
@@ -257,7 +339,9 @@ int hashprune_noalloc_impl(const uint32_t *dst, const uint32_t *src, const float
     } restore;
 
     if (count) {
-        hp_count<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, count, n, start, err);
+        hp_count<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, count, n, fill, err);
+        PIPNN_LAUNCH_CHECK();
+        hp_widen<<<grid_for(n, 256), 256, 0, stream()>>>(fill, n, start);
         PIPNN_LAUNCH_CHECK();
     }
     PIPNN_TRY(exclusive_scan_u64_scratch(start, start, n, total, scan));
