@@ -333,9 +333,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             const uint32_t nct = (s + C::NMAX - 1) / C::NMAX;
             const uint32_t self_col = row0 + r;      // this row's own column inside the leaf
-            // k = 2: running two smallest (v, column) of this half, columns in increasing order
-            float R1 = __int_as_float(0x7f800000), R2 = R1;
-            uint32_t C1 = 0xFFFFFFFFu, C2 = 0xFFFFFFFFu;
+            // k = 2: running two smallest (D << 32 | column) of this half, and per tile the two
+            // smallest 32-bit keys (D << 7 | column in the tile) -- see the tile loop below
+            uint64_t RK1 = ~0ull, RK2 = ~0ull;
+            const int32_t n_i = row_ok ? a.member_norm[off + row0 + r] : 0;
+            const float nb23 = (float)n_i + 8388608.0f;  // n_i + 2^23, exact
             for (uint32_t t = 0; t < nct; t++, j++) {
                 const uint32_t tb = j % C::T, ph = (j / C::T) & 1;
                 if (failed) continue;
@@ -350,6 +352,57 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t c0 = t * C::NMAX;
                 const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
                 const uint32_t *info = colid + tb * C::NMAX;
+                if constexpr (KMAX == 2) {
+                    // D_ij = n_i - 2 acc is an integer below 2^23 (d <= 128 bytes), so
+                    // fma(-2, acc, n_i + 2^23) = D + 2^23 exactly and its bit pattern is
+                    // 0x4B000000 + D: times 128 plus the column in the tile it is a 32-bit key whose
+                    // order is (D, column) -- ties to the smaller column, i.e. the smaller id.
+                    // Two smallest per chain: k2 = min(k2, max(k1, key)), k1 = min(k1, key).
+                    uint32_t T1 = ~0u, T2 = ~0u;
+                    for (uint32_t q = half; q * 32 < ncols; q += 2) {
+                        uint32_t gv[32];
+                        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX + q * 32, gv);
+                        uint32_t key[32];
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj++)
+                            key[jj] = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(gv[jj]), nb23)) * 128u +
+                                      (q * 32 + jj);
+                        const uint32_t base = c0 + q * 32;
+                        // the row's own column and columns past the leaf never qualify (both tests
+                        // are uniform over the warp: a warp's rows are 32 consecutive columns)
+                        if (self_col - base < 32u || base + 32 > s) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; jj++)
+                                if (base + jj == self_col || base + jj >= s) key[jj] = ~0u;
+                        }
+                        uint32_t k1[4], k2[4];
+#pragma unroll
+                        for (int ch = 0; ch < 4; ch++) {
+                            k1[ch] = key[ch];
+                            k2[ch] = ~0u;
+                        }
+#pragma unroll
+                        for (int jj = 4; jj < 32; jj++) {
+                            const int ch = jj & 3;
+                            k2[ch] = min(k2[ch], max(k1[ch], key[jj]));
+                            k1[ch] = min(k1[ch], key[jj]);
+                        }
+#pragma unroll
+                        for (int ch = 0; ch < 4; ch++) {
+                            const uint32_t m2 = min(max(T1, k1[ch]), min(T2, k2[ch]));
+                            T1 = min(T1, k1[ch]);
+                            T2 = m2;
+                        }
+                    }
+                    // the tile's pair as (D << 32 | column in the leaf), merged into the running pair
+                    const uint64_t K1 = T1 == ~0u ? ~0ull
+                                                  : ((uint64_t)((T1 & 0x7FFFFFFFu) >> 7) << 32) | (c0 + (T1 & 127u));
+                    const uint64_t K2 = T2 == ~0u ? ~0ull
+                                                  : ((uint64_t)((T2 & 0x7FFFFFFFu) >> 7) << 32) | (c0 + (T2 & 127u));
+                    const uint64_t m2 = min(max(RK1, K1), min(RK2, K2));
+                    RK1 = min(RK1, K1);
+                    RK2 = m2;
+                } else {
                 for (uint32_t q = half; q * 32 < ncols; q += 2) {
                     uint32_t gv[32];
                     tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX + q * 32, gv);
@@ -358,64 +411,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                     float v[32];
 #pragma unroll
                     for (int jj = 0; jj < 32; jj++) v[jj] = -__uint_as_float(gv[jj]);
-                    const uint32_t base = c0 + q * 32;
-                    if constexpr (KMAX == 2) {
-                        // the row's own column and columns past the leaf never qualify
-                        if (self_col - base < 32u || base + 32 > s) {
-#pragma unroll
-                            for (int jj = 0; jj < 32; jj++)
-                                if (base + jj == self_col || base + jj >= s) v[jj] = __int_as_float(0x7f800000);
-                        }
-                        // two smallest of the chunk: four independent in-order scans of 8, merged in
-                        // order; strict comparisons keep the earlier (smaller-id) column on ties
-                        float a1[4], a2[4];
-                        uint32_t i1[4], i2[4];
-#pragma unroll
-                        for (int ch = 0; ch < 4; ch++) {
-                            a1[ch] = __int_as_float(0x7f800000);
-                            a2[ch] = a1[ch];
-                            i1[ch] = 0;
-                            i2[ch] = 0;
-#pragma unroll
-                            for (int e = 0; e < 8; e++) {
-                                const float x = v[ch * 8 + e];
-                                const uint32_t xi = ch * 8 + e;
-                                const bool lt1 = x < a1[ch], lt2 = x < a2[ch];
-                                a2[ch] = lt1 ? a1[ch] : (lt2 ? x : a2[ch]);
-                                i2[ch] = lt1 ? i1[ch] : (lt2 ? xi : i2[ch]);
-                                a1[ch] = lt1 ? x : a1[ch];
-                                i1[ch] = lt1 ? xi : i1[ch];
-                            }
-                        }
-#pragma unroll
-                        for (int ch = 1; ch < 4; ch++) {
-                            // merge chain ch (later columns) into chain 0
-                            if (a1[ch] < a1[0]) {
-                                const bool b = a2[ch] < a1[0];
-                                a2[0] = b ? a2[ch] : a1[0];
-                                i2[0] = b ? i2[ch] : i1[0];
-                                a1[0] = a1[ch];
-                                i1[0] = i1[ch];
-                            } else if (a1[ch] < a2[0]) {
-                                a2[0] = a1[ch];
-                                i2[0] = i1[ch];
-                            }
-                        }
-                        // merge the chunk into the running pair (running columns come first)
-                        if (a1[0] < R2) {
-                            if (a1[0] < R1) {
-                                const bool b = a2[0] < R1;
-                                R2 = b ? a2[0] : R1;
-                                C2 = b ? base + i2[0] : C1;
-                                R1 = a1[0];
-                                C1 = base + i1[0];
-                            } else {
-                                R2 = a1[0];
-                                C2 = base + i1[0];
-                            }
-                        }
-                        continue;
-                    }
                     float m0 = fminf(fminf(v[0], v[1]), fminf(v[2], v[3]));
                     float m1 = fminf(fminf(v[4], v[5]), fminf(v[6], v[7]));
                     float m2 = fminf(fminf(v[8], v[9]), fminf(v[10], v[11]));
@@ -435,17 +430,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                     }
                 }
+                }
                 fence_before();
                 mbar_arrive(bar(C::BAR_TEMPTY + tb));
             }
             if constexpr (KMAX == 2) {
-                // columns -> member ids (the leaf's members are in ascending id order)
-                kv[0] = R1;
-                ki[0] = C1 < s ? a.members[off + C1] : 0xFFFFFFFFu;
-                kv[1] = R2;
-                ki[1] = C2 < s ? a.members[off + C2] : 0xFFFFFFFFu;
-                if (ki[0] == 0xFFFFFFFFu) kv[0] = __int_as_float(0x7f800000);
-                if (ki[1] == 0xFFFFFFFFu) kv[1] = __int_as_float(0x7f800000);
+                // columns -> member ids (the leaf's members are in ascending id order); kv holds
+                // v / 2 = (D - n_i) / 2, exact
+                const uint32_t C1 = (uint32_t)RK1, C2 = (uint32_t)RK2;
+                ki[0] = RK1 != ~0ull && C1 < s ? a.members[off + C1] : 0xFFFFFFFFu;
+                ki[1] = RK2 != ~0ull && C2 < s ? a.members[off + C2] : 0xFFFFFFFFu;
+                kv[0] = ki[0] == 0xFFFFFFFFu ? __int_as_float(0x7f800000)
+                                             : ((float)(uint32_t)(RK1 >> 32) - (float)n_i) * 0.5f;
+                kv[1] = ki[1] == 0xFFFFFFFFu ? __int_as_float(0x7f800000)
+                                             : ((float)(uint32_t)(RK2 >> 32) - (float)n_i) * 0.5f;
             }
             // merge the two halves of each row, then emit
             if (half == 1) {
