@@ -42,6 +42,7 @@ struct TcArgs {
     const TcUnit *units;
     const uint32_t *members;     // leaf members, ascending ids inside every leaf
     const int32_t *member_norm;  // squared norm of every leaf member, in member order
+    const uint2 *member_pieces;  // -(n / 2) of every leaf member as four BF16 pieces
     const uint64_t *cand_off;    // per unit: first output slot of the unit's leaf
     const uint32_t *unit_leaf;   // per unit: leaf index (for cand_off)
     uint32_t k;
@@ -147,6 +148,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((1u ^ (r & 7)) << 4)), "r"(0u),
                          "r"(0u), "r"(0u), "r"(0u)
                          : "memory");
+            // every stage's 32-byte norm slice starts zero; a B job rewrites only its first 8 bytes
+            for (uint32_t q = 0; q < 2u * C::S; q++)
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + C::OFF_BN + r * 128 +
+                                                                              ((q ^ (r & 7)) << 4)),
+                             "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+                             : "memory");
         }
         fence_proxy_async();
         // job stream: per unit one A job, then one B job per 128-column tile.  The member ids
@@ -188,24 +195,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             return unit_job(c.i + 1, c.u + gridDim.x);
         };
-        auto load_ids = [&](const Job &q, uint32_t (&id)[4], int32_t (&nr)[4]) {
+        // column ids are only needed by the general-k epilogue
+        auto load_ids = [&](const Job &q, uint32_t (&id)[4], uint2 (&nr)[4]) {
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 const uint32_t r = q.first + 4 * lane + e;
-                const bool in = q.kind != 2 && r < q.s;
-                id[e] = (q.kind == 1 && in) ? a.members[q.off + r] : 0u;
-                nr[e] = (q.kind == 1 && in) ? a.member_norm[q.off + r] : 0;
+                const bool in = q.kind == 1 && r < q.s;
+                id[e] = (KMAX > 2 && in) ? a.members[q.off + r] : 0u;
+                nr[e] = in ? a.member_pieces[q.off + r] : make_uint2(0u, 0u);
             }
         };
         Job cur = unit_job(0, blockIdx.x);
         uint32_t id[4];
-        int32_t nr[4];
+        uint2 nr[4];
         load_ids(cur, id, nr);
         uint32_t j = 0;
         while (cur.kind != 2) {
             const Job nxt = next_job(cur);
             uint32_t nid[4];
-            int32_t nnr[4];
+            uint2 nnr[4];
             load_ids(nxt, nid, nnr);
             bool ok;
             if (cur.kind == 0) {
@@ -228,17 +236,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const uint32_t r = 4 * lane + e;
-                        const bool in = cur.first + r < cur.s;
-                        ci[r] = in ? id[e] : 0xFFFFFFFFu;
-                        // -(n_j / 2) as four BF16-exact pieces: the bytes of floor(n_j / 2) and
-                        // (n_j mod 2) / 2, in this stage's 32-byte slice (logical chunks 2 st, 2 st + 1)
-                        const uint2 pc = neg_half_norm_pieces(in ? (uint32_t)nr[e] : 0u);
-                        const uint32_t nb = sbase + C::OFF_BN + r * 128;
-                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st) ^ (r & 7)) << 4)),
-                                     "r"(pc.x), "r"(pc.y), "r"(0u), "r"(0u)
-                                     : "memory");
-                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st + 1) ^ (r & 7)) << 4)),
-                                     "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+                        if (KMAX > 2) ci[r] = cur.first + r < cur.s ? id[e] : 0xFFFFFFFFu;
+                        // -(n_j / 2) as four BF16-exact pieces (zero past the leaf) in the first 8
+                        // bytes of this stage's 32-byte slice (logical chunk 2 st)
+                        asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(sbase + C::OFF_BN + r * 128 +
+                                                                             (((2 * st) ^ (r & 7)) << 4)),
+                                     "r"(nr[e].x), "r"(nr[e].y)
                                      : "memory");
                     }
                     fence_proxy_async();
@@ -359,13 +362,22 @@ __global__ void __launch_bounds__(THREADS, 1)
                     // order is (D, column) -- ties to the smaller column, i.e. the smaller id.
                     // Two smallest per chain: k2 = min(k2, max(k1, key)), k1 = min(k1, key).
                     uint32_t T1 = ~0u, T2 = ~0u;
-                    for (uint32_t q = half; q * 32 < ncols; q += 2) {
-                        uint32_t gv[32];
-                        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX + q * 32, gv);
+                    // this half's chunks of the tile (q = half, half + 2): both loads in flight
+                    // before one wait
+                    uint32_t gv[2][32];
+                    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX;
+                    const bool two = (half + 2) * 32 < ncols;
+                    if (half * 32 < ncols) tmem_ld32_async(tbase + half * 32, gv[0]);
+                    if (two) tmem_ld32_async(tbase + (half + 2) * 32, gv[1]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const uint32_t q = half + 2 * h;
+                        if (q * 32 >= ncols) break;
                         uint32_t key[32];
 #pragma unroll
                         for (int jj = 0; jj < 32; jj++)
-                            key[jj] = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(gv[jj]), nb23)) * 128u +
+                            key[jj] = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(gv[h][jj]), nb23)) * 128u +
                                       (q * 32 + jj);
                         const uint32_t base = c0 + q * 32;
                         // the row's own column and columns past the leaf never qualify (both tests
@@ -544,9 +556,13 @@ __global__ void max_leaf_size(const uint32_t *size, uint64_t L, unsigned *out) {
     atomicMax(out, m);
 }
 
-__global__ void member_norms(const uint32_t *members, uint64_t M, const int32_t *sqnorm, int32_t *out) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < M; i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = sqnorm[members[i]];
+__global__ void member_norms(const uint32_t *members, uint64_t M, const int32_t *sqnorm, int32_t *out,
+                             uint2 *pieces) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < M; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int32_t nrm = sqnorm[members[i]];
+        out[i] = nrm;
+        pieces[i] = neg_half_norm_pieces((uint32_t)nrm);
+    }
 }
 
 template <int KB, int KMAX>
@@ -606,13 +622,15 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
     uint32_t *smem_members = nullptr;
     PIPNN_TRY(ws.alloc(&smem_members, M));
     int32_t *mnorm = nullptr;
+    uint2 *mpieces = nullptr;
     PIPNN_TRY(ws.alloc(&mnorm, M));
+    PIPNN_TRY(ws.alloc(&mpieces, M));
     if (M) {
         PIPNN_CUDA(cudaMemcpyAsync(smem_members, mem, M * 4, cudaMemcpyDeviceToDevice, stream()));
         sort_leaf_members<<<grid_for(L, 1, 152u * 16u), 1024, 0, stream()>>>(off, L, smem_members);
         PIPNN_LAUNCH_CHECK();
         mem = smem_members;
-        member_norms<<<grid_for(M, 256), 256, 0, stream()>>>(mem, M, sqnorm, mnorm);
+        member_norms<<<grid_for(M, 256), 256, 0, stream()>>>(mem, M, sqnorm, mnorm, mpieces);
         PIPNN_LAUNCH_CHECK();
     }
     if (M >= 0x7FFFFF00ull) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes < 2^31 leaf members");
@@ -637,6 +655,7 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
     a.unit_leaf = tile_grp;
     a.members = mem;
     a.member_norm = mnorm;
+    a.member_pieces = mpieces;
     a.cand_off = cand_off;
     a.k = k;
     a.out_dst = out_dst;
