@@ -46,6 +46,7 @@ struct AsUnit {
 struct AsArgs {
     const AsUnit *units;
     const uint32_t *inst;       // instance -> point id
+    const int32_t *inst_norm;   // instance -> exact squared norm of its point
     const int32_t *lead_norm;   // exact squared norm of every leader row
     uint32_t fanout;            // F <= KMAX; stride of assign
     uint16_t *assign;           // instance -> F leader ranks
@@ -87,6 +88,15 @@ __device__ __forceinline__ uint32_t pick32(const uint32_t (&g)[32], uint32_t j) 
 #pragma unroll
     for (int i = 0; i < 2; i++) e[i] = (j & 2u) ? c[i + 2] : c[i];
     return (j & 1u) ? e[1] : e[0];
+}
+
+// Sorted ascending list of K keys: insert x, the largest drops out.  Branch free, every slot
+// computed from the old list (depth two).
+template <int K, typename T>
+__device__ __forceinline__ void key_insert(T (&L)[K], T x) {
+#pragma unroll
+    for (int p = K - 1; p > 0; p--) L[p] = min(L[p], max(L[p - 1], x));
+    L[0] = min(L[0], x);
 }
 
 // Sorted list, best first.  Inserts (w, c) given gt[p] = "(w, c) goes before entry p"; the last
@@ -343,6 +353,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (uint32_t i = 0, u = blockIdx.x; u < nunits; i++, u += gridDim.x) {
             const AsUnit un = a.units[u];
             const bool row_ok = un.row0 + r < un.nrows;
+            // F <= 4: the KMAX smallest (D << 32 | rank), D = n_x - 2 w the squared distance
+            uint64_t RK[KMAX];
+            float nb23 = 0.0f;
+            if constexpr (KMAX <= 4) {
+#pragma unroll
+                for (int p = 0; p < KMAX; p++) RK[p] = ~0ull;
+                nb23 = (float)(row_ok ? a.inst_norm[un.inst0 + un.row0 + r] : 0) + 8388608.0f;  // n_x + 2^23
+            }
             // KMAX - F padding entries (+inf) in front, then the F live ones
             float kv[KMAX];
             uint32_t ki[KMAX];
@@ -364,6 +382,47 @@ __global__ void __launch_bounds__(THREADS, 1)
                 fence_after();
                 const uint32_t c0 = t * C::NMAX;
                 const uint32_t nc = un.ncols - c0 < (uint32_t)C::NMAX ? un.ncols - c0 : C::NMAX;
+                if constexpr (KMAX <= 4) {
+                    // D = n_x - 2 w is an integer below 2^23 (d <= 128 bytes): fma(-2, w, n_x + 2^23)
+                    // is exact with bit pattern 0x4B000000 + D, so bits * 128 + column is a 32-bit
+                    // key ordered by (D, rank); the tile's KMAX smallest via a min/max network
+                    uint32_t L0[KMAX], L1[KMAX];
+#pragma unroll
+                    for (int p = 0; p < KMAX; p++) L0[p] = L1[p] = ~0u;
+                    uint32_t g[2][32];
+                    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX;
+                    const bool two = (half + 2) * 32 < nc;
+                    if (half * 32 < nc) tmem_ld32_async(tbase + half * 32, g[0]);
+                    if (two) tmem_ld32_async(tbase + (half + 2) * 32, g[1]);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const uint32_t q = half + 2 * h;
+                        if (q * 32 >= nc) break;
+                        const uint32_t live = nc - q * 32;
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj += 2) {
+                            uint32_t k0 = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(g[h][jj]), nb23)) * 128u +
+                                          (q * 32 + jj);
+                            uint32_t k1 = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(g[h][jj + 1]), nb23)) *
+                                              128u + (q * 32 + jj + 1);
+                            k0 = (uint32_t)jj < live ? k0 : ~0u;
+                            k1 = (uint32_t)jj + 1 < live ? k1 : ~0u;
+                            key_insert<KMAX>(L0, k0);
+                            key_insert<KMAX>(L1, k1);
+                        }
+                    }
+#pragma unroll
+                    for (int p = 0; p < KMAX; p++) key_insert<KMAX>(L0, L1[p]);
+                    // the tile's keys as (D << 32 | rank), merged into the running list
+#pragma unroll
+                    for (int p = 0; p < KMAX; p++) {
+                        const uint64_t K = L0[p] == ~0u ? ~0ull
+                                                        : ((uint64_t)((L0[p] & 0x7FFFFFFFu) >> 7) << 32) |
+                                                              (c0 + (L0[p] & 127u));
+                        key_insert<KMAX>(RK, K);
+                    }
+                } else {
                 for (uint32_t q = half; q * 32 < nc; q += 2) {
                     uint32_t g[32];
                     tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX + q * 32, g);
@@ -385,10 +444,33 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                     }
                 }
+                }
                 fence_before();
                 mbar_arrive(bar(C::BAR_TEMPTY + tb));
             }
             // merge the two halves of each row, then emit
+            if constexpr (KMAX <= 4) {
+                uint64_t *mk = reinterpret_cast<uint64_t *>(mv);
+                if (half == 1) {
+#pragma unroll
+                    for (int p = 0; p < KMAX; p++) mk[r * KMAX + p] = RK[p];
+                }
+                failed = named_barrier_or(1, EPI_WARPS * 32, failed || *abort);
+                if (half == 0 && row_ok && !failed) {
+#pragma unroll
+                    for (int p = 0; p < KMAX; p++) key_insert<KMAX>(RK, mk[r * KMAX + p]);
+                    const uint32_t f = F < un.ncols ? F : un.ncols;
+                    const uint64_t out = (un.inst0 + un.row0 + r) * (uint64_t)F;
+#pragma unroll
+                    for (int p = 0; p < KMAX; p++) {
+                        const uint32_t rank = (uint32_t)RK[p];
+                        if ((uint32_t)p < f && RK[p] != ~0ull && rank < AS_HIST) {
+                            a.assign[out + p] = (uint16_t)rank;
+                            atomicAdd(&hist[rank], 1u);
+                        }
+                    }
+                }
+            } else {
             if (half == 1) {
 #pragma unroll
                 for (int p = 0; p < KMAX; p++) mv[r * KMAX + p] = make_float2(kv[p], __uint_as_float(ki[p]));
@@ -411,6 +493,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         atomicAdd(&hist[ki[p]], 1u);
                     }
                 }
+            }
             }
             // mv is rewritten, and the histogram counted into, only after every thread is done
             failed = named_barrier_or(1, EPI_WARPS * 32, failed || *abort);
@@ -502,13 +585,13 @@ int assign_tc_plan(const void *X, uint64_t n, uint32_t d, int dtype, Workspace &
 int assign_tc(const AssignTcPlan &plan, const void *X, uint32_t d, int dtype, const int32_t *sqnorm,
               const uint32_t *tile_grp, const uint32_t *tile_row0, uint64_t ntiles, const uint64_t *seg_start,
               const uint32_t *seg_size, const uint32_t *inst, const uint64_t *lead_off, const uint32_t *lead_cnt,
-              const uint32_t *lead, uint64_t total_leaders, uint32_t F, uint16_t *assign, uint32_t *bucket_cnt,
-              Workspace &ws) {
+              const uint32_t *lead, uint64_t total_leaders, uint64_t ninst, uint32_t F, uint16_t *assign,
+              uint32_t *bucket_cnt, Workspace &ws) {
     if (F < 1 || F > ASSIGN_TC_MAX_F) return set_error(PIPNN_EINVAL, "fanout %u outside 1..%u", F, ASSIGN_TC_MAX_F);
     if (ntiles == 0) return PIPNN_OK;
     if (total_leaders >= 0x7FFFFF00ull) return set_error(PIPNN_EUNSUPPORTED, "too many leaders in one level");
     __nv_bfloat16 *lrows = nullptr;
-    int32_t *lnorm = nullptr;
+    int32_t *lnorm = nullptr, *inorm = nullptr;
     AsUnit *units = nullptr;
     PIPNN_TRY(ws.alloc(&lrows, total_leaders * plan.kp));
     PIPNN_TRY(ws.alloc(&lnorm, total_leaders));
@@ -516,6 +599,13 @@ int assign_tc(const AssignTcPlan &plan, const void *X, uint32_t d, int dtype, co
     PIPNN_TRY(stage_rows_bf16(X, d, plan.kp, dtype, lead, total_leaders, lrows));
     gather_norms<<<grid_for(total_leaders, 256), 256, 0, stream()>>>(lead, total_leaders, sqnorm, lnorm);
     PIPNN_LAUNCH_CHECK();
+    if (F <= 4) {
+        PIPNN_TRY(ws.alloc(&inorm, ninst ? ninst : 1));
+        if (ninst) {
+            gather_norms<<<grid_for(ninst, 256), 256, 0, stream()>>>(inst, ninst, sqnorm, inorm);
+            PIPNN_LAUNCH_CHECK();
+        }
+    }
     build_as_units<<<grid_for(ntiles, 256), 256, 0, stream()>>>(tile_grp, tile_row0, ntiles, seg_start, seg_size,
                                                                 lead_off, lead_cnt, units);
     PIPNN_LAUNCH_CHECK();
@@ -524,6 +614,7 @@ int assign_tc(const AssignTcPlan &plan, const void *X, uint32_t d, int dtype, co
     AsArgs a{};
     a.units = units;
     a.inst = inst;
+    a.inst_norm = inorm;
     a.lead_norm = lnorm;
     a.fanout = F;
     a.assign = assign;

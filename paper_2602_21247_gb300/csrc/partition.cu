@@ -438,7 +438,7 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         if (bp->leaf_engine == PIPNN_LEAF_TC && assign_tc_eligible(dtype, d, n, F)) {
             if (!tc_plan.rows) PIPNN_TRY(assign_tc_plan(X, n, d, dtype, tc_ws, &tc_plan));
             PIPNN_TRY(assign_tc(tc_plan, X, d, dtype, sqn, tile_grp, tile_row0, ntiles, cur->seg_start,
-                                cur->seg_size, cur->inst, lead_off, lead_cnt, lead, total_leaders, F, assign,
+                                cur->seg_size, cur->inst, lead_off, lead_cnt, lead, total_leaders, N, F, assign,
                                 bucket_cnt, tw));
         } else {
             PIPNN_TRY(launch_allpairs<MODE_ASSIGN>(dtype, metric, F, a, ntiles));

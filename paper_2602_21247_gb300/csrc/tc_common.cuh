@@ -248,7 +248,7 @@ int assign_tc_plan(const void *X, uint64_t n, uint32_t d, int dtype, Workspace &
 int assign_tc(const AssignTcPlan &plan, const void *X, uint32_t d, int dtype, const int32_t *sqnorm,
               const uint32_t *tile_grp, const uint32_t *tile_row0, uint64_t ntiles, const uint64_t *seg_start,
               const uint32_t *seg_size, const uint32_t *inst, const uint64_t *lead_off, const uint32_t *lead_cnt,
-              const uint32_t *lead, uint64_t total_leaders, uint32_t F, uint16_t *assign, uint32_t *bucket_cnt,
-              Workspace &ws);
+              const uint32_t *lead, uint64_t total_leaders, uint64_t ninst, uint32_t F, uint16_t *assign,
+              uint32_t *bucket_cnt, Workspace &ws);
 
 }  // namespace pipnn
