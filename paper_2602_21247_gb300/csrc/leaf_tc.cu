@@ -214,11 +214,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             const Job nxt = next_job(cur);
             uint32_t nid[4];
             uint2 nnr[4];
-            load_ids(nxt, nid, nnr);
             bool ok;
             if (cur.kind == 0) {
                 const uint32_t ua = cur.i & 1;
                 ok = mbar_wait(bar(C::BAR_EMPTY_A + ua), ((cur.i >> 1) & 1) ^ 1, abort, a.err);
+                // the next job's ids and norm pieces: requested here, consumed next iteration
+                load_ids(nxt, nid, nnr);
                 if (ok && lane == 0) {
                     const uint32_t fb = bar(C::BAR_FULL_A + ua);
                     mbar_arrive_tx(fb, KB * C::REGION);
@@ -246,6 +247,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     fence_proxy_async();
                     mbar_arrive(bar(C::BAR_CFULL + tb));
+                }
+                // requested after the proxy fence, which would otherwise wait for them
+                load_ids(nxt, nid, nnr);
+                if (ok) {
                     const uint32_t fb = bar(C::BAR_FULL + st);
                     if (lane == 0) {
                         mbar_arrive_tx(fb, KB * C::REGION);

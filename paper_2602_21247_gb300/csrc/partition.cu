@@ -192,6 +192,7 @@ __global__ void classify_buckets(uint64_t OB, const uint8_t *ob_kind, const uint
     }
 }
 
+template <int FMAX>
 __global__ void scatter_instances(uint64_t N, uint32_t F, const uint32_t *inst, const uint32_t *inst_seg,
                                   const uint64_t *lead_off, const uint32_t *lead_cnt, const uint16_t *assign,
                                   const uint32_t *rank_ob, const uint8_t *ob_kind, const uint32_t *ob_raw,
@@ -202,11 +203,15 @@ __global__ void scatter_instances(uint64_t N, uint32_t F, const uint32_t *inst, 
         const uint32_t s = inst_seg[i];
         const uint32_t f = F < lead_cnt[s] ? F : lead_cnt[s];
         const uint32_t pt = inst[i];
-        uint32_t seen[32];
-        for (uint32_t j = 0; j < f; j++) {
+        // the instance's groups so far, in registers (FMAX >= f; fully unrolled indexing)
+        uint32_t seen[FMAX];
+#pragma unroll
+        for (int j = 0; j < FMAX; j++) {
+            if ((uint32_t)j >= f) break;
             const uint32_t ob = rank_ob[lead_off[s] + assign[i * F + j]];
             bool dup = false;
-            for (uint32_t q = 0; q < j; q++) dup = dup || seen[q] == ob;
+#pragma unroll
+            for (int q = 0; q < j; q++) dup = dup || seen[q] == ob;
             seen[j] = ob;
             if (dup || ob == OB_NONE) continue;
             const uint32_t pos = atomicAdd(&ob_fill[ob], 1u);
@@ -504,11 +509,20 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         PIPNN_TRY(tw.alloc(&guard_pos, n_guard));
         PIPNN_TRY(tw.alloc(&guard_size, n_guard));
         // guards add at least two runs each; the exact count is known after the scatter
-        scatter_instances<<<grid_for(N, 256), 256, 0, stream()>>>(N, F, cur->inst, cur->inst_seg, lead_off, lead_cnt,
-                                                                  assign, rank_ob, ob_kind, ob_raw, leafsz, nextsz,
-                                                                  is_rec, ob_fill, lv.mem, next->inst, next->inst_seg,
-                                                                  err);
-        PIPNN_LAUNCH_CHECK();
+        {
+            const unsigned sg = grid_for(N, 256);
+#define PIPNN_SCATTER(FM)                                                                                         \
+    scatter_instances<FM><<<sg, 256, 0, stream()>>>(N, F, cur->inst, cur->inst_seg, lead_off, lead_cnt, assign,   \
+                                                    rank_ob, ob_kind, ob_raw, leafsz, nextsz, is_rec, ob_fill,      \
+                                                    lv.mem, next->inst, next->inst_seg, err)
+            if (F <= 2) PIPNN_SCATTER(2);
+            else if (F <= 4) PIPNN_SCATTER(4);
+            else if (F <= 8) PIPNN_SCATTER(8);
+            else if (F <= 16) PIPNN_SCATTER(16);
+            else PIPNN_SCATTER(32);
+#undef PIPNN_SCATTER
+            PIPNN_LAUNCH_CHECK();
+        }
         uint64_t *lstart_tmp;
         uint32_t *lsize_tmp;
         PIPNN_TRY(tw.alloc(&lstart_tmp, n_leafobs));

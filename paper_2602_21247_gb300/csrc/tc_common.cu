@@ -5,26 +5,49 @@ namespace pipnn {
 
 namespace {
 
-// One thread per 16-byte output chunk (8 BF16 values) of the padded copy.
-__global__ void stage_rows_kernel(const void *X, uint32_t d, uint32_t kp, int dtype, const uint32_t *ids,
-                                  uint64_t M, __nv_bfloat16 *out) {
+// Eight bytes -> eight BF16 values (exact for u8 / i8), as four packed words.
+template <int DT>
+__device__ __forceinline__ void bytes_to_bf16x8(uint32_t lo, uint32_t hi, uint32_t (&w)[4]) {
+    const uint32_t b[2] = {lo, hi};
+#pragma unroll
+    for (int h = 0; h < 4; h++) {
+        const uint32_t word = b[h >> 1], sh = (h & 1) * 16;
+        const uint32_t x0 = (word >> sh) & 0xFFu, x1 = (word >> (sh + 8)) & 0xFFu;
+        const float f0 = DT == PIPNN_U8 ? (float)x0 : (float)(int8_t)x0;
+        const float f1 = DT == PIPNN_U8 ? (float)x1 : (float)(int8_t)x1;
+        w[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f0)) |
+               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f1)) << 16);
+    }
+}
+
+// One thread per 16-byte output chunk (8 BF16 values) of the padded copy.  Rows whose width is a
+// multiple of 8 bytes are read 8 bytes at a time; others byte by byte.
+template <int DT, bool WIDE>
+__global__ void stage_rows_kernel(const void *X, uint32_t d, uint32_t kp, const uint32_t *ids, uint64_t M,
+                                  __nv_bfloat16 *out) {
     const uint32_t per_row = kp / 8;
     const uint64_t total = M * per_row;
+    const uint8_t *Xb = static_cast<const uint8_t *>(X);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t row = i / per_row;
         const uint32_t c = (uint32_t)(i % per_row);
         const uint64_t src = (uint64_t)(ids ? ids[row] : row) * d;
-        uint32_t w[4];
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (WIDE) {
+            if (c * 8 < d) {
+                const uint2 v = *reinterpret_cast<const uint2 *>(Xb + src + c * 8);
+                bytes_to_bf16x8<DT>(v.x, v.y, w);
+            }
+        } else {
+            uint32_t lo = 0, hi = 0;
 #pragma unroll
-        for (int h = 0; h < 4; h++) {
-            float lo = 0.0f, hi = 0.0f;
-            const uint32_t t = c * 8 + 2 * h;
-            if (t < d) lo = dtype == PIPNN_U8 ? (float)static_cast<const uint8_t *>(X)[src + t]
-                                              : (float)static_cast<const int8_t *>(X)[src + t];
-            if (t + 1 < d) hi = dtype == PIPNN_U8 ? (float)static_cast<const uint8_t *>(X)[src + t + 1]
-                                                  : (float)static_cast<const int8_t *>(X)[src + t + 1];
-            w[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
-                   ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+            for (int t = 0; t < 8; t++) {
+                const uint32_t col = c * 8 + t;
+                const uint32_t x = col < d ? Xb[src + col] : 0u;
+                if (t < 4) lo |= x << (8 * t);
+                else hi |= x << (8 * (t - 4));
+            }
+            bytes_to_bf16x8<DT>(lo, hi, w);
         }
         reinterpret_cast<uint4 *>(out)[i] = make_uint4(w[0], w[1], w[2], w[3]);
     }
@@ -37,7 +60,15 @@ int stage_rows_bf16(const void *X, uint32_t d, uint32_t kp, int dtype, const uin
     if (dtype != PIPNN_U8 && dtype != PIPNN_I8) return set_error(PIPNN_EUNSUPPORTED, "BF16 staging takes byte data");
     if (kp % 64 != 0 || kp < d) return set_error(PIPNN_EINVAL, "padded width %u", kp);
     if (M == 0) return PIPNN_OK;
-    stage_rows_kernel<<<grid_for(M * (kp / 8), 256), 256, 0, stream()>>>(X, d, kp, dtype, ids, M, out);
+    const unsigned g = grid_for(M * (kp / 8), 256);
+    const bool wide = d % 8 == 0 && (reinterpret_cast<uintptr_t>(X) & 7) == 0;
+    if (dtype == PIPNN_U8) {
+        if (wide) stage_rows_kernel<PIPNN_U8, true><<<g, 256, 0, stream()>>>(X, d, kp, ids, M, out);
+        else stage_rows_kernel<PIPNN_U8, false><<<g, 256, 0, stream()>>>(X, d, kp, ids, M, out);
+    } else {
+        if (wide) stage_rows_kernel<PIPNN_I8, true><<<g, 256, 0, stream()>>>(X, d, kp, ids, M, out);
+        else stage_rows_kernel<PIPNN_I8, false><<<g, 256, 0, stream()>>>(X, d, kp, ids, M, out);
+    }
     PIPNN_LAUNCH_CHECK();
     return PIPNN_OK;
 }
