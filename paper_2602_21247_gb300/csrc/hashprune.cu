@@ -41,27 +41,65 @@ __global__ void hp_widen(unsigned *per_node, uint64_t n, uint64_t *start) {
     }
 }
 
+// Residualised hash h_v(c) (Eq. 1): bit i = [Sketch(c)_i >= Sketch(v)_i]; with both sketch rows
+// loaded once, also h_c(v), whose bit i is [Sketch(v)_i >= Sketch(c)_i].
+__device__ __forceinline__ void hash_pair(const float *S, uint32_t m, uint32_t v, uint32_t c, uint32_t &h_vc,
+                                          uint32_t &h_cv) {
+    h_vc = 0;
+    h_cv = 0;
+    const float *sv = S + (uint64_t)v * m, *sc = S + (uint64_t)c * m;
+    if ((m & 3u) == 0) {
+        // rows of a multiple of four floats start 16-byte aligned: vector loads
+        const float4 *v4 = reinterpret_cast<const float4 *>(sv), *c4 = reinterpret_cast<const float4 *>(sc);
+        for (uint32_t i = 0; i < m / 4; i++) {
+            const float4 a = __ldg(c4 + i), b = __ldg(v4 + i);
+            h_vc |= ((a.x >= b.x ? 1u : 0u) | (a.y >= b.y ? 2u : 0u) | (a.z >= b.z ? 4u : 0u) |
+                     (a.w >= b.w ? 8u : 0u)) << (4 * i);
+            h_cv |= ((b.x >= a.x ? 1u : 0u) | (b.y >= a.y ? 2u : 0u) | (b.z >= a.z ? 4u : 0u) |
+                     (b.w >= a.w ? 8u : 0u)) << (4 * i);
+        }
+    } else {
+        for (uint32_t i = 0; i < m; i++) {
+            const float a = __ldg(sc + i), b = __ldg(sv + i);
+            h_vc |= (a >= b ? 1u : 0u) << i;
+            h_cv |= (b >= a ? 1u : 0u) << i;
+        }
+    }
+}
+
+// Two consecutive candidates per thread.  The leaf pick emits every pair in both directions next
+// to each other, (v, c) then (c, v): such a mirrored pair needs the two sketch rows only once.
 __global__ void hp_scatter(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, uint64_t n,
                            const float *S, uint32_t m, const uint64_t *start, unsigned *fill, uint64_t *slots) {
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < count; e += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t v = dst[e], c = src[e];
-        if (v >= n || c >= n || v == c) continue;
-        // residualised hash h_v(c): bit i = [Sketch(c)_i >= Sketch(v)_i]  (Eq. 1)
-        uint32_t h = 0;
-        const float *sv = S + (uint64_t)v * m, *sc = S + (uint64_t)c * m;
-        if ((m & 3u) == 0) {
-            // rows of a multiple of four floats start 16-byte aligned: vector loads
-            const float4 *v4 = reinterpret_cast<const float4 *>(sv), *c4 = reinterpret_cast<const float4 *>(sc);
-            for (uint32_t i = 0; i < m / 4; i++) {
-                const float4 a = __ldg(c4 + i), b = __ldg(v4 + i);
-                h |= ((a.x >= b.x ? 1u : 0u) | (a.y >= b.y ? 2u : 0u) | (a.z >= b.z ? 4u : 0u) |
-                      (a.w >= b.w ? 8u : 0u)) << (4 * i);
+    const uint64_t npairs = (count + 1) / 2;
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < npairs; p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t e0 = 2 * p, e1 = e0 + 1;
+        const bool has1 = e1 < count;
+        const uint32_t v0 = dst[e0], c0 = src[e0];
+        const uint32_t v1 = has1 ? dst[e1] : 0u, c1 = has1 ? src[e1] : 0u;
+        const float w0 = dist[e0], w1 = has1 ? dist[e1] : 0.0f;
+        const bool ok0 = v0 < n && c0 < n && v0 != c0;
+        const bool ok1 = has1 && v1 < n && c1 < n && v1 != c1;
+        uint32_t h0 = 0, h1 = 0;
+        if (ok0) {
+            uint32_t back;
+            hash_pair(S, m, v0, c0, h0, back);
+            if (ok1) {
+                if (v1 == c0 && c1 == v0) h1 = back;
+                else hash_pair(S, m, v1, c1, h1, back);
             }
-        } else {
-            for (uint32_t i = 0; i < m; i++) h |= (__ldg(sc + i) >= __ldg(sv + i) ? 1u : 0u) << i;
+        } else if (ok1) {
+            uint32_t back;
+            hash_pair(S, m, v1, c1, h1, back);
         }
-        uint32_t pos = atomicAdd(&fill[v], 1u);
-        slots[start[v] + pos] = reservoir_slot(dist[e], c, h);
+        if (ok0) {
+            const uint32_t pos = atomicAdd(&fill[v0], 1u);
+            slots[start[v0] + pos] = reservoir_slot(w0, c0, h0);
+        }
+        if (ok1) {
+            const uint32_t pos = atomicAdd(&fill[v1], 1u);
+            slots[start[v1] + pos] = reservoir_slot(w1, c1, h1);
+        }
     }
 }
 
@@ -117,7 +155,7 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t *buf, uint32_t P, int
     }
 }
 
-__global__ void __launch_bounds__(HP_WARPS * 32) hp_merge(uint64_t n, uint32_t m, uint32_t l_max,
+__global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_t m, uint32_t l_max,
                                                          const uint64_t *start, const uint64_t *slots,
                                                          uint64_t *res, uint32_t *cnt) {
     extern __shared__ __align__(16) unsigned char hp_smem[];
@@ -182,8 +220,43 @@ __global__ void __launch_bounds__(HP_WARPS * 32) hp_merge(uint64_t n, uint32_t m
         };
         // (eight per lane would cover 256 but doubles the kernel's registers, which costs more
         // occupancy than the larger nodes gain)
-        if ((uint64_t)cur + (b - a) <= 128) {
+        const uint64_t total = (uint64_t)cur + (b - a);
+        if (total <= 128) {
             sort_regs(std::integral_constant<int, 4>());
+        } else if (total <= 256) {
+            // two runs of 128 sorted in registers (the second written descending), then the 8
+            // merge stages of a 256-element bitonic network in shared memory
+            const uint32_t nb = (uint32_t)total;
+#pragma unroll
+            for (int run = 0; run < 2; run++) {
+                uint64_t K[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t t = 128 * run + 4 * lane + q;
+                    K[q] = t < cur ? res[v * l_max + t] : (t < nb ? slots[a + (t - cur)] : ~0ull);
+                }
+                warp_sort_regs<4>(K, lane);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t i = 4 * lane + q;
+                    buf[run == 0 ? i : 255 - i] = K[q];
+                }
+            }
+            __syncwarp();
+            for (uint32_t jm = 128; jm > 0; jm >>= 1) {
+                for (uint32_t i = lane; i < 256; i += 32) {
+                    const uint32_t ixj = i ^ jm;
+                    if (ixj > i) {
+                        const uint64_t x = buf[i], y = buf[ixj];
+                        if (x > y) {
+                            buf[i] = y;
+                            buf[ixj] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            cur = walk(nb);
         } else {
             for (uint32_t t = lane; t < cur; t += 32) buf[t] = res[v * l_max + t];
             while (a < b) {
@@ -235,7 +308,8 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
     PIPNN_TRY(read_u64(tot, &E));
     PIPNN_TRY(ws.alloc(&slots, E));
     if (count) {
-        hp_scatter<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m, start, fill, slots);
+        hp_scatter<<<grid_for((count + 1) / 2, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m, start, fill,
+                                                                          slots);
         PIPNN_LAUNCH_CHECK();
     }
     size_t smem = hashprune_smem_bytes(m);
@@ -347,7 +421,8 @@ int hashprune_noalloc_impl(const uint32_t *dst, const uint32_t *src, const float
     PIPNN_TRY(exclusive_scan_u64_scratch(start, start, n, total, scan));
     PIPNN_CUDA(cudaMemcpyAsync(start + n, total, 8, cudaMemcpyDeviceToDevice, stream()));
     if (count) {
-        hp_scatter<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m, start, fill, slots);
+        hp_scatter<<<grid_for((count + 1) / 2, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m, start, fill,
+                                                                          slots);
         PIPNN_LAUNCH_CHECK();
     }
     const size_t smem = hashprune_smem_bytes(m);
