@@ -523,12 +523,16 @@ __global__ void build_units(const uint32_t *tile_grp, const uint32_t *tile_row0,
 // TC_MAX_LEAF members; the host rejects larger ones).
 constexpr uint32_t TC_MAX_LEAF = 4096;
 
+// Leaves of up to WS_MAX members are sorted by one warp each in registers (sort_leaf_members_warp);
+// the block-wide sort takes the larger ones.
+constexpr uint32_t WS_MAX = 1024;
+
 __global__ void __launch_bounds__(1024) sort_leaf_members(const uint64_t *off, uint64_t L, uint32_t *mem) {
     __shared__ uint32_t sh[TC_MAX_LEAF];
     for (uint64_t b = blockIdx.x; b < L; b += gridDim.x) {
         const uint64_t o = off[b];
         const uint32_t n = (uint32_t)(off[b + 1] - o);
-        if (n < 2 || n > TC_MAX_LEAF) continue;
+        if (n <= WS_MAX || n > TC_MAX_LEAF) continue;
         uint32_t P = 1;
         while (P < n) P <<= 1;
         for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < n ? mem[o + i] : 0xFFFFFFFFu;
@@ -551,6 +555,75 @@ __global__ void __launch_bounds__(1024) sort_leaf_members(const uint64_t *off, u
         }
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) mem[o + i] = sh[i];
         __syncthreads();
+    }
+}
+
+// Ascending bitonic sort of 32 * E keys held E per lane (element E * lane + q in K[q]): exchanges
+// within a lane for distances below E, shuffles across lanes for the rest.
+template <int E>
+__device__ __forceinline__ void warp_sort_u32(uint32_t (&K)[E], int lane) {
+#pragma unroll
+    for (uint32_t k = 2; k <= 32u * E; k <<= 1) {
+#pragma unroll
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            if (j >= (uint32_t)E) {
+#pragma unroll
+                for (int q = 0; q < E; q++) {
+                    const uint32_t i = E * lane + q;
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, K[q], j / E);
+                    const bool take_min = ((i & j) == 0) == ((i & k) == 0);
+                    K[q] = take_min ? min(o, K[q]) : max(o, K[q]);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < E; q++) {
+                    if ((q & j) == 0) {
+                        const uint32_t i = E * lane + q;
+                        const uint32_t lo = K[q], hi = K[q | j];
+                        const bool up = (i & k) == 0;
+                        K[q] = up ? min(lo, hi) : max(lo, hi);
+                        K[q | j] = up ? max(lo, hi) : min(lo, hi);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// One leaf of 2..32E members by one warp: coalesced loads into a skewed shared buffer, E
+// consecutive elements per lane, register sort, and back.
+template <int E>
+__device__ __forceinline__ void warp_sort_leaf(uint32_t *mem, uint64_t o, uint32_t n, uint32_t *buf, int lane) {
+    constexpr uint32_t P = 32u * E;
+    auto at = [](uint32_t i) { return i + (i >> 5); };  // skew: lane l's run starts in bank l
+    for (uint32_t i = lane; i < P; i += 32) buf[at(i)] = i < n ? mem[o + i] : 0xFFFFFFFFu;
+    __syncwarp();
+    uint32_t K[E];
+#pragma unroll
+    for (int q = 0; q < E; q++) K[q] = buf[at(E * lane + q)];
+    __syncwarp();
+    warp_sort_u32<E>(K, lane);
+#pragma unroll
+    for (int q = 0; q < E; q++) buf[at(E * lane + q)] = K[q];
+    __syncwarp();
+    for (uint32_t i = lane; i < n; i += 32) mem[o + i] = buf[at(i)];
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256, 2) sort_leaf_members_warp(const uint64_t *off, uint64_t L, uint32_t *mem) {
+    __shared__ uint32_t sbuf[8][WS_MAX + WS_MAX / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *buf = sbuf[warp];
+    for (uint64_t b = blockIdx.x * 8ull + warp; b < L; b += gridDim.x * 8ull) {
+        const uint64_t o = off[b];
+        const uint32_t n = (uint32_t)(off[b + 1] - o);
+        if (n < 2 || n > WS_MAX) continue;
+        if (n <= 32) warp_sort_leaf<1>(mem, o, n, buf, lane);
+        else if (n <= 64) warp_sort_leaf<2>(mem, o, n, buf, lane);
+        else if (n <= 128) warp_sort_leaf<4>(mem, o, n, buf, lane);
+        else if (n <= 256) warp_sort_leaf<8>(mem, o, n, buf, lane);
+        else if (n <= 512) warp_sort_leaf<16>(mem, o, n, buf, lane);
+        else warp_sort_leaf<32>(mem, o, n, buf, lane);
     }
 }
 
@@ -632,6 +705,8 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
     PIPNN_TRY(ws.alloc(&mpieces, M));
     if (M) {
         PIPNN_CUDA(cudaMemcpyAsync(smem_members, mem, M * 4, cudaMemcpyDeviceToDevice, stream()));
+        sort_leaf_members_warp<<<grid_for(L, 8, 152u * 32u), 256, 0, stream()>>>(off, L, smem_members);
+        PIPNN_LAUNCH_CHECK();
         sort_leaf_members<<<grid_for(L, 1, 152u * 16u), 1024, 0, stream()>>>(off, L, smem_members);
         PIPNN_LAUNCH_CHECK();
         mem = smem_members;

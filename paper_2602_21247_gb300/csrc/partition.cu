@@ -385,17 +385,18 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         PIPNN_TRY(tw.alloc(&thr, S));
         PIPNN_TRY(tw.alloc(&active, S));
         PIPNN_TRY(tw.alloc(&ccnt, S));
-        PIPNN_TRY(tw.alloc(&tot, 1));
+        PIPNN_TRY(tw.alloc(&tot, 8));  // scan totals, read back several at a time
         PIPNN_TRY(tw.zeros(&nbad, 1));
         const unsigned gs = grid_for(S, 256);
         seg_setup<<<gs, 256, 0, stream()>>>(S, cur->seg_size, bp->p_samp, bp->max_leaders, lead_cnt, lead_cnt64,
                                             cand_cap, mult, thr, active, ccnt);
         PIPNN_LAUNCH_CHECK();
-        uint64_t total_leaders = 0, total_cand = 0;
+        uint64_t h2[2];
         PIPNN_TRY(exclusive_scan_u64(lead_cnt64, lead_off, S, tot, tw));
-        PIPNN_TRY(read_u64(tot, &total_leaders));
-        PIPNN_TRY(exclusive_scan_u64(cand_cap, cand_off, S, tot, tw));
-        PIPNN_TRY(read_u64(tot, &total_cand));
+        PIPNN_TRY(exclusive_scan_u64(cand_cap, cand_off, S, tot + 1, tw));
+        PIPNN_CUDA(cudaMemcpyAsync(h2, tot, sizeof(h2), cudaMemcpyDeviceToHost, stream()));
+        PIPNN_CUDA(cudaStreamSynchronize(stream()));
+        const uint64_t total_leaders = h2[0], total_cand = h2[1];
         PIPNN_TRY(tw.alloc(&cbuf, total_cand));
         PIPNN_TRY(tw.alloc(&lead, total_leaders));
         PIPNN_TRY(tw.zeros(&bucket_cnt, total_leaders));
@@ -481,17 +482,15 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         classify_buckets<<<grid_for(OB, 256), 256, 0, stream()>>>(OB, ob_kind, ob_raw, leafsz, nextsz, is_leaf,
                                                                   is_rec, is_guard);
         PIPNN_LAUNCH_CHECK();
-        uint64_t leaf_members_raw = 0, N_next = 0, n_leafobs = 0, n_rec = 0, n_guard = 0;
+        uint64_t h5[5];
         PIPNN_TRY(exclusive_scan_u64(leafsz, leafsz, OB, tot, tw));
-        PIPNN_TRY(read_u64(tot, &leaf_members_raw));
-        PIPNN_TRY(exclusive_scan_u64(nextsz, nextsz, OB, tot, tw));
-        PIPNN_TRY(read_u64(tot, &N_next));
-        PIPNN_TRY(exclusive_scan_u64(is_leaf, is_leaf, OB, tot, tw));
-        PIPNN_TRY(read_u64(tot, &n_leafobs));
-        PIPNN_TRY(exclusive_scan_u64(is_rec, is_rec, OB, tot, tw));
-        PIPNN_TRY(read_u64(tot, &n_rec));
-        PIPNN_TRY(exclusive_scan_u64(is_guard, is_guard, OB, tot, tw));
-        PIPNN_TRY(read_u64(tot, &n_guard));
+        PIPNN_TRY(exclusive_scan_u64(nextsz, nextsz, OB, tot + 1, tw));
+        PIPNN_TRY(exclusive_scan_u64(is_leaf, is_leaf, OB, tot + 2, tw));
+        PIPNN_TRY(exclusive_scan_u64(is_rec, is_rec, OB, tot + 3, tw));
+        PIPNN_TRY(exclusive_scan_u64(is_guard, is_guard, OB, tot + 4, tw));
+        PIPNN_CUDA(cudaMemcpyAsync(h5, tot, sizeof(h5), cudaMemcpyDeviceToHost, stream()));
+        PIPNN_CUDA(cudaStreamSynchronize(stream()));
+        const uint64_t leaf_members_raw = h5[0], N_next = h5[1], n_leafobs = h5[2], n_rec = h5[3], n_guard = h5[4];
 
         // 4. scatter
         std::unique_ptr<Level> next(new Level());
