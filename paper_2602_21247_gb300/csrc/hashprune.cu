@@ -69,8 +69,10 @@ __device__ __forceinline__ void hash_pair(const float *S, uint32_t m, uint32_t v
 
 // Two consecutive candidates per thread.  The leaf pick emits every pair in both directions next
 // to each other, (v, c) then (c, v): such a mirrored pair needs the two sketch rows only once.
+// cursor[v] starts at v's first slot (the exclusive prefix sum) and is advanced atomically, so
+// afterwards it holds the first slot of v + 1 and v's run is [cursor[v - 1], cursor[v]).
 __global__ void hp_scatter(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, uint64_t n,
-                           const float *S, uint32_t m, const uint64_t *start, unsigned *fill, uint64_t *slots) {
+                           const float *S, uint32_t m, unsigned long long *cursor, uint64_t *slots) {
     const uint64_t npairs = (count + 1) / 2;
     for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < npairs; p += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t e0 = 2 * p, e1 = e0 + 1;
@@ -92,14 +94,8 @@ __global__ void hp_scatter(const uint32_t *dst, const uint32_t *src, const float
             uint32_t back;
             hash_pair(S, m, v1, c1, h1, back);
         }
-        if (ok0) {
-            const uint32_t pos = atomicAdd(&fill[v0], 1u);
-            slots[start[v0] + pos] = reservoir_slot(w0, c0, h0);
-        }
-        if (ok1) {
-            const uint32_t pos = atomicAdd(&fill[v1], 1u);
-            slots[start[v1] + pos] = reservoir_slot(w1, c1, h1);
-        }
+        if (ok0) slots[atomicAdd(&cursor[v0], 1ull)] = reservoir_slot(w0, c0, h0);
+        if (ok1) slots[atomicAdd(&cursor[v1], 1ull)] = reservoir_slot(w1, c1, h1);
     }
 }
 
@@ -169,8 +165,9 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
     for (uint64_t v = (uint64_t)blockIdx.x * HP_WARPS + warp; v < n; v += (uint64_t)gridDim.x * HP_WARPS) {
         uint32_t cur = cnt[v];
         if (cur > l_max) cur = l_max;
-        uint64_t a = start[v];
-        const uint64_t b = start[v + 1];
+        // start[] is the scatter's advanced cursor: v's run is [start[v - 1], start[v])
+        uint64_t a = v ? start[v - 1] : 0ull;
+        const uint64_t b = start[v];
         if (a == b) {
             // no new candidates: the reservoir is unchanged (normalise the padding)
             for (uint32_t t = cur + lane; t < l_max; t += 32) res[v * l_max + t] = ~0ull;
@@ -308,7 +305,8 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
     PIPNN_TRY(read_u64(tot, &E));
     PIPNN_TRY(ws.alloc(&slots, E));
     if (count) {
-        hp_scatter<<<grid_for((count + 1) / 2, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m, start, fill,
+        hp_scatter<<<grid_for((count + 1) / 2, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m,
+                                                                          reinterpret_cast<unsigned long long *>(start),
                                                                           slots);
         PIPNN_LAUNCH_CHECK();
     }
@@ -421,7 +419,8 @@ int hashprune_noalloc_impl(const uint32_t *dst, const uint32_t *src, const float
     PIPNN_TRY(exclusive_scan_u64_scratch(start, start, n, total, scan));
     PIPNN_CUDA(cudaMemcpyAsync(start + n, total, 8, cudaMemcpyDeviceToDevice, stream()));
     if (count) {
-        hp_scatter<<<grid_for((count + 1) / 2, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m, start, fill,
+        hp_scatter<<<grid_for((count + 1) / 2, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m,
+                                                                          reinterpret_cast<unsigned long long *>(start),
                                                                           slots);
         PIPNN_LAUNCH_CHECK();
     }
