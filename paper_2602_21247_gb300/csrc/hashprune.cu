@@ -6,11 +6,13 @@
 // of the whole stream, so the GPU inserts a whole batch at once:
 //   1. count candidates per destination, prefix-sum, scatter each candidate's slot
 //      [ordered bf16 dist:16][src:32][h_dst(src):16] next to its destination's others;
-//   2. one warp per node sorts (old reservoir + new slots) -- in registers with shuffles when
-//      they fit in 128 (four per lane), else in shared memory -- and walks them in ascending
-//      order, keeping a slot iff its hash bucket has not been seen yet (__match_any_sync within a
-//      chunk of 32, a bitmap of 2^m bits across chunks), until l_max are kept.  Batches larger
-//      than the shared buffer are merged chunk by chunk.
+//   2. one warp per node first drops exact duplicate slots (the same pair reached through several
+//      leaves: about four of every five candidates of a build) with a shared-memory hash set,
+//      sorts the distinct ones in registers with shuffles, and walks them in ascending order,
+//      keeping a slot iff its hash bucket has not been seen yet (__match_any_sync within a chunk
+//      of 32, a bitmap of 2^m bits across chunks), until l_max are kept.  Nodes with more than
+//      128 distinct slots sort everything (in registers up to 256, else in shared memory, chunk
+//      by chunk for batches larger than the buffer).
 #include "internal.cuh"
 
 #include <type_traits>
@@ -20,6 +22,8 @@ namespace pipnn {
 namespace {
 constexpr int HP_WARPS = 8;
 constexpr int HP_BUF = 512;   // slots per warp buffer
+constexpr uint32_t HP_HT = 256;       // per-warp hash set of distinct slots
+constexpr uint32_t HP_DISTINCT = 128; // distinct slots the fast path sorts in registers
 
 __global__ void hp_count(const uint32_t *dst, const uint32_t *src, uint64_t count, uint64_t n, unsigned *per_node,
                          unsigned *err) {
@@ -159,7 +163,11 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
     const uint32_t bm_words = m >= 5 ? (1u << (m - 5)) : 1u;
     uint64_t *buf = reinterpret_cast<uint64_t *>(hp_smem) + (size_t)warp * HP_BUF;
     uint32_t *seen = reinterpret_cast<uint32_t *>(hp_smem + (size_t)HP_WARPS * HP_BUF * 8) + (size_t)warp * bm_words;
+    unsigned long long *ht = reinterpret_cast<unsigned long long *>(
+                                 hp_smem + (size_t)HP_WARPS * HP_BUF * 8 + (((size_t)HP_WARPS * bm_words * 4 + 7) & ~(size_t)7)) +
+                             (size_t)warp * HP_HT;
     for (uint32_t w = lane; w < bm_words; w += 32) seen[w] = 0;
+    for (uint32_t w = lane; w < HP_HT; w += 32) ht[w] = ~0ull;
     __syncwarp();
 
     for (uint64_t v = (uint64_t)blockIdx.x * HP_WARPS + warp; v < n; v += (uint64_t)gridDim.x * HP_WARPS) {
@@ -199,6 +207,55 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
             __syncwarp();
             return out < l_max ? out : l_max;
         };
+        // fast path: the distinct slots (old reservoir and new run) through the hash set, sorted
+        // in registers when at most HP_DISTINCT; exact duplicates are interchangeable, so dropping
+        // them leaves the walk's result unchanged.  (A valid slot is never all ones: its id is < n.)
+        const uint64_t total = (uint64_t)cur + (b - a);
+        uint32_t u = 0;
+        bool fast = true;
+        for (uint64_t base = 0; base < total; base += 32) {
+            const uint64_t t = base + lane;
+            const bool valid = t < total;
+            const uint64_t key = valid ? (t < cur ? res[v * l_max + t] : slots[a + (t - cur)]) : ~0ull;
+            bool fresh = false;
+            if (valid) {
+                uint32_t h = (uint32_t)(((key ^ (key >> 31)) * 0x9E3779B97F4A7C15ull) >> 56);
+                for (uint32_t it = 0; it < HP_HT; it++) {
+                    const unsigned long long old = atomicCAS(&ht[h], ~0ull, (unsigned long long)key);
+                    if (old == ~0ull) {
+                        fresh = true;
+                        break;
+                    }
+                    if (old == key) break;
+                    h = (h + 1) & (HP_HT - 1);
+                }
+            }
+            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+            const uint32_t pos = u + __popc(fm & ((1u << lane) - 1u));
+            if (fresh && pos < HP_DISTINCT) buf[pos] = key;
+            u += __popc(fm);
+            if (u > HP_DISTINCT) {  // uniform: the table then holds at most HP_DISTINCT + 32 < HP_HT
+                fast = false;
+                break;
+            }
+        }
+        for (uint32_t w = lane; w < HP_HT; w += 32) ht[w] = ~0ull;
+        __syncwarp();
+        auto sort_distinct = [&](auto tag) {
+            constexpr int E = decltype(tag)::value;
+            uint64_t K[E];
+#pragma unroll
+            for (int q = 0; q < E; q++) {
+                const uint32_t t = E * lane + q;
+                K[q] = t < u ? buf[t] : ~0ull;
+            }
+            __syncwarp();
+            warp_sort_regs<E>(K, lane);
+#pragma unroll
+            for (int q = 0; q < E; q++) buf[E * lane + q] = K[q];
+            __syncwarp();
+            cur = walk(u);
+        };
         // old + new slots, E per lane, sorted in registers
         auto sort_regs = [&](auto tag) {
             constexpr int E = decltype(tag)::value;
@@ -217,8 +274,11 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
         };
         // (eight per lane would cover 256 but doubles the kernel's registers, which costs more
         // occupancy than the larger nodes gain)
-        const uint64_t total = (uint64_t)cur + (b - a);
-        if (total <= 128) {
+        if (fast) {
+            if (u <= 32) sort_distinct(std::integral_constant<int, 1>());
+            else if (u <= 64) sort_distinct(std::integral_constant<int, 2>());
+            else sort_distinct(std::integral_constant<int, 4>());
+        } else if (total <= 128) {
             sort_regs(std::integral_constant<int, 4>());
         } else if (total <= 256) {
             // two runs of 128 sorted in registers (the second written descending), then the 8
@@ -278,7 +338,8 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
 
 size_t hashprune_smem_bytes(uint32_t m) {
     uint32_t bm_words = m >= 5 ? (1u << (m - 5)) : 1u;
-    return (size_t)HP_WARPS * (HP_BUF * 8 + bm_words * 4);
+    return (size_t)HP_WARPS * HP_BUF * 8 + (((size_t)HP_WARPS * bm_words * 4 + 7) & ~(size_t)7) +
+           (size_t)HP_WARPS * HP_HT * 8;
 }
 
 int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
