@@ -17,15 +17,25 @@
 //  * walk: in rank order a candidate is admitted unless its column mask meets the admitted set
 //    (the removal loop of Alg. 2 and its lazy form coincide), up to R admissions.
 //
-// Persistent CTA (one per SM, 20 warps):
-//   warps 0-11   epilogue: three groups of four warps (one per TMEM lane quarter, a thread per
-//                row) take turns on nodes: norms, D(x, .), thresholds, ranks, column masks
+// Tiles.  Most reservoirs of a build are small (after duplicate candidates collapse, a node keeps
+// ~20), so nodes with at most 31 valid candidates are packed four to a 128-row tile: node q owns
+// rows 32q .. 32q + c_q (its candidates, then itself), i.e. exactly TMEM lane quarter q, and the
+// columns it needs are the same 32.  The 128 x 128 Gram of a packed tile costs the tensor cores
+// little; only its four diagonal 32 x 32 blocks are read.  A larger node gets a tile of its own.
+//
+// Persistent CTA (one per SM, 16 warps):
+//   warps 0-11   epilogue: three groups of four warps (one per TMEM lane quarter) take turns on
+//                tiles.  In a packed tile each warp handles its quarter's node alone (norms,
+//                D(x, .), thresholds, ranks, masks, walk, output) with warp-level sync only; a
+//                large node is handled by the group together (named barrier) and walked by one
+//                of its warps.
 //   warp 12      owns TMEM (4 x 128 columns); one thread issues the Gram MMAs
-//   warp 15      node info: reservoir slots (loaded two nodes ahead), compaction of the valid
-//                ids, BF16 keys
-//   warps 17-18  TMA gather4 of the rows of alternate nodes (ids from the node info)
-//   warps 13, 14, 16, 19  walkers: write adj / deg
-// Waits are bounded as in the other engines (DERR_TIMEOUT; TMEM is still released).
+//   warp 13      node info: reservoir slots loaded two nodes ahead, compaction of the valid ids,
+//                packing; writes the tile sequence, ended by one end marker per consumer
+//   warps 14-15  TMA gather4 of the rows of alternate tiles
+// A warp reaches TMEM lanes 32 (w % 4) .. +31 and runs on scheduler w % 4; the single-warp roles
+// sit one on each scheduler.  Waits are bounded as in the other engines (DERR_TIMEOUT; TMEM is
+// still released).
 #include "tc_common.cuh"
 
 namespace pipnn {
@@ -34,23 +44,18 @@ namespace {
 
 using namespace tc;
 
-// Warp roles.  A warp reaches TMEM lanes 32 (w % 4) .. +31 and runs on scheduler w % 4, so the
-// epilogue groups are warps 4g .. 4g + 3, and the other roles are placed so that each scheduler
-// carries a similar load (the rows of lane quarter 0, the nearest candidates, are always
-// occupied; quarter 3 is the lightest).
 constexpr int PT_GROUPS = 3;                 // epilogue groups of 4 warps: warps 0 .. 11
 constexpr int PT_EPI_WARPS = 4 * PT_GROUPS;
-constexpr int PT_MMA_WARP = 12;              // scheduler 0
-constexpr int PT_INFO_WARP = 15;             // scheduler 3
-constexpr int PT_WALKERS = 4;                // warps 13, 14, 16, 19
-constexpr int PT_GATHERERS = 2;              // warps 17, 18
-constexpr int PT_THREADS = 20 * 32;
-__host__ __device__ constexpr int walker_of(int warp) {
-    return warp == 13 ? 0 : warp == 14 ? 1 : warp == 16 ? 2 : warp == 19 ? 3 : -1;
-}
-__host__ __device__ constexpr int gatherer_of(int warp) { return warp == 17 ? 0 : warp == 18 ? 1 : -1; }
-constexpr uint32_t PT_MAXC = 127;                                 // candidates per node (+ the node)
-constexpr int W_MASK_OFF = 0, W_IDS_OFF = 2048, W_ORDER_OFF = 2560, W_MISC_OFF = 2688, W_SLOT_BYTES = 2704;
+constexpr int PT_MMA_WARP = 12;
+constexpr int PT_INFO_WARP = 13;
+constexpr int PT_GATHER_WARP0 = 14;          // and 15
+constexpr int PT_GATHERERS = 2;
+constexpr int PT_THREADS = 16 * 32;
+constexpr uint32_t PT_MAXC = 127;            // candidates per node (+ the node)
+constexpr uint32_t PT_SMALL = 31;            // packed nodes: at most this many valid candidates
+constexpr uint32_t PT_ENDS = PT_GROUPS > PT_GATHERERS ? PT_GROUPS : PT_GATHERERS;  // end markers
+
+enum : uint32_t { TK_PACK = 1, TK_LARGE = 2, TK_END = 3 };
 
 struct PtArgs {
     const uint64_t *res;   // n x l_max reservoir slots
@@ -63,33 +68,37 @@ struct PtArgs {
     unsigned *err;
 };
 
+// Tile info, info warp -> gathers, MMA, epilogue: row ids (a packed node's rows start at 32q; the
+// row after its candidates is the node itself), BF16 keys of the candidate rows, and
+// misc = {kind, nodes, (c_q, v_q, n_x q) for q < 4}.
+constexpr int I_IDS = 0, I_BKEY = 512, I_MISC = 768, I_BYTES = 832;
+constexpr int M_KIND = 0, M_NODES = 1, M_NODE = 2;  // node q: misc[2 + 3q + {0, 1, 2}] = c, v, n_x
+
 template <int KB>
 struct PtCfg {
     static constexpr int A = 4;            // gathered row tiles in flight
     static constexpr int T = 4;            // accumulator buffers
-    static constexpr int I = 8;            // node-info slots (info and gathers run ahead)
-    static constexpr int W = 2 * PT_WALKERS;  // walk slots (walker w alternates between w and w + PT_WALKERS)
-    // node info, producer -> epilogue: ids[128] u32, BF16 keys[128] u16, c, v, n_x
-    static constexpr int I_IDS = 0, I_BKEY = 512, I_MISC = 768, I_BYTES = 784;
-    // walk slot, epilogue -> walker: column masks[128] x 4 u32, ids[128], order[128] u8, c, v
-    static constexpr int W_MASK = W_MASK_OFF, W_IDS = W_IDS_OFF, W_ORDER = W_ORDER_OFF, W_MISC = W_MISC_OFF,
-                         W_BYTES = W_SLOT_BYTES;
+    static constexpr int I = 8;            // tile-info slots (info and gathers run ahead)
     static constexpr int OFF_A0 = 0;
     static constexpr int OFF_INFO = OFF_A0 + A * KB * REGION;
-    static constexpr int OFF_WS = OFF_INFO + I * I_BYTES;
-    // per group, two node buffers of: D(x, z_r) u32[128], n_r / 2 float[128]
-    static constexpr int OFF_DX = OFF_WS + W * W_BYTES;
-    static constexpr int OFF_BAR = OFF_DX + PT_GROUPS * 2 * 1024;
+    static constexpr int OFF_STAGE = OFF_INFO + I * I_BYTES;          // the info warp's packed tile
+    // per group (large nodes): column masks 128 x 4 u32, ids 128, order 128 u8, D(x, .) 128,
+    // n / 2 128 floats
+    static constexpr int G_MASK = 0, G_IDS = 2048, G_ORDER = 2560, G_DX = 2688, G_HN = 3200, G_BYTES = 3712;
+    static constexpr int OFF_GROUP = OFF_STAGE + I_BYTES;
+    // per epilogue warp (packed nodes): D(x, .) 32, n / 2 32 floats, order 32 u8
+    static constexpr int W_DX = 0, W_HN = 128, W_ORDER = 256, W_BYTES = 288;
+    static constexpr int OFF_WARP = OFF_GROUP + PT_GROUPS * G_BYTES;
+    static constexpr int OFF_BAR = OFF_WARP + PT_EPI_WARPS * W_BYTES;
     static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = A, BAR_CFULL = 2 * A, BAR_IEMPTY = 2 * A + I,
-                         BAR_TFULL = 2 * A + 2 * I, BAR_TEMPTY = 2 * A + 2 * I + T,
-                         BAR_WFULL = 2 * A + 2 * I + 2 * T, BAR_WEMPTY = 2 * A + 2 * I + 2 * T + W,
-                         NBAR = 2 * A + 2 * I + 2 * T + 2 * W;
-    static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;     // tmem base, abort flag
+                         BAR_TFULL = 2 * A + 2 * I, BAR_TEMPTY = 2 * A + 2 * I + T, NBAR = 2 * A + 2 * I + 2 * T;
+    static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;               // tmem base, abort flag
     static constexpr int BYTES = OFF_MISC + 16;
     static constexpr int SMEM = BYTES + 1024;
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(T * 128 <= (int)TMEM_COLS, "TMEM budget");
-    static_assert(I_BYTES % 16 == 0 && W_BYTES % 16 == 0, "slot alignment");
+    static_assert(I_BYTES % 16 == 0 && G_BYTES % 16 == 0 && W_BYTES % 16 == 0, "alignment");
+    static_assert(I >= (int)PT_ENDS, "end markers fit the ring");
 };
 
 // Register g[j] for a run-time j (five-level select tree).
@@ -126,6 +135,24 @@ __device__ __forceinline__ uint32_t bf16_key(float f) {
     return (b & 0x8000u) ? (~b & 0xFFFFu) : (b | 0x8000u);
 }
 
+// Rank of candidate r among c in (D(x, .), id, slot) order: the start of its run of equal BF16
+// keys plus its place inside the run, or (full) a count over all c.
+__device__ __forceinline__ uint32_t candidate_rank(uint32_t r, uint32_t c, uint32_t DX, uint32_t id,
+                                                   const uint32_t *dx, const uint32_t *ids, const uint16_t *bkey,
+                                                   bool full) {
+    uint32_t lo = 0;
+    if (!full) {
+        lo = r;
+        while (lo > 0 && bkey[lo - 1] == bkey[r]) lo--;
+    }
+    uint32_t rank = lo;
+    for (uint32_t s = lo; s < c && (full || bkey[s] == bkey[r]); s++) {
+        const uint32_t ds = dx[s], is = ids[s];
+        rank += (ds < DX || (ds == DX && (is < id || (is == id && s < r)))) ? 1u : 0u;
+    }
+    return rank;
+}
+
 template <int KB>
 __global__ void __launch_bounds__(PT_THREADS, 1)
     prune_tc_kernel(const __grid_constant__ CUtensorMap xmap, const PtArgs a) {
@@ -137,11 +164,11 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
     volatile uint32_t *tmem_slot = reinterpret_cast<volatile uint32_t *>(smem + C::OFF_MISC);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + C::OFF_MISC + 4);
     auto bar = [&](int i) { return sbase + C::OFF_BAR + 8 * i; };
-    auto info = [&](uint32_t tb) { return smem + C::OFF_INFO + tb * C::I_BYTES; };
-    auto wslot = [&](uint32_t ws) { return smem + C::OFF_WS + ws * C::W_BYTES; };
+    auto info = [&](uint32_t ib) { return smem + C::OFF_INFO + ib * I_BYTES; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t n = a.n;
+    const uint32_t R = a.R;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < C::A; i++) {
@@ -156,10 +183,6 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             mbar_init(bar(C::BAR_TFULL + i), 1);
             mbar_init(bar(C::BAR_TEMPTY + i), 128);
         }
-        for (int i = 0; i < C::W; i++) {
-            mbar_init(bar(C::BAR_WFULL + i), 128);
-            mbar_init(bar(C::BAR_WEMPTY + i), 32);
-        }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
@@ -171,9 +194,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == PT_INFO_WARP) {
-        // ------------------------------------------------------------ node info (one warp)
+        // ------------------------------------------------------------ tile info (one warp)
         // Software pipeline: the reservoir row, count and node norm of node j + 2 are requested
-        // while node j is compacted, so their latency is hidden behind two nodes of work.
+        // while node j is compacted.
         struct Pre {
             uint64_t key[4];
             int32_t nv;
@@ -193,66 +216,129 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 p.key[k] = s < a.l_max ? a.res[v * a.l_max + s] : 0ull;
             }
         };
+        unsigned char *stage = smem + C::OFF_STAGE;
+        uint32_t *stage_misc = reinterpret_cast<uint32_t *>(stage + I_MISC);
+        uint32_t tile = 0, packed = 0;  // tiles written; nodes in the staged packed tile
+        bool stop = false;
+        // the next tile slot; false if the kernel aborted
+        auto acquire = [&]() {
+            return __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_IEMPTY + tile % C::I), ((tile / C::I) & 1) ^ 1,
+                                                     abort, a.err));
+        };
+        auto publish = [&]() {
+            __syncwarp();
+            mbar_arrive(bar(C::BAR_CFULL + tile % C::I));
+            tile++;
+        };
+        auto flush_packed = [&]() {
+            if (lane == 0) {
+                stage_misc[M_KIND] = TK_PACK;
+                stage_misc[M_NODES] = packed;
+            }
+            __syncwarp();
+            if (!acquire()) return false;
+            const uint4 *srcv = reinterpret_cast<const uint4 *>(stage);
+            uint4 *dstv = reinterpret_cast<uint4 *>(info(tile % C::I));
+            for (int q = lane; q < I_BYTES / 16; q += 32) dstv[q] = srcv[q];
+            publish();
+            packed = 0;
+            return true;
+        };
         Pre p0, p1;
         load(blockIdx.x, p0);
         load(blockIdx.x + (uint64_t)gridDim.x, p1);
-        for (uint32_t j = 0;; j++) {
+        for (uint32_t j = 0; !stop; j++) {
             const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
             if (v >= n) break;
-            const uint32_t ib = j % C::I;
             Pre p2;
             load(v + 2 * (uint64_t)gridDim.x, p2);
-            const uint32_t c = p0.c;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_IEMPTY + ib), ((j / C::I) & 1) ^ 1, abort, a.err)))
-                break;
-            unsigned char *in = info(ib);
-            uint32_t *ids = reinterpret_cast<uint32_t *>(in + C::I_IDS);
-            uint16_t *bkey = reinterpret_cast<uint16_t *>(in + C::I_BKEY);
+            // valid candidates (id < n), in slot order
             uint32_t cc = 0;
+            bool in_range[4];
+            uint32_t pos[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const uint32_t s = 32 * k + lane;
                 const uint32_t id = (uint32_t)(p0.key[k] >> 16);
-                const bool in_range = s < c && (uint64_t)id < n;
-                if (s < c && !in_range) atomicOr(a.err, DERR_RANGE);
-                const unsigned m = __ballot_sync(0xffffffffu, in_range);
-                if (in_range) {
-                    const uint32_t pos = cc + __popc(m & ((1u << lane) - 1u));
-                    ids[pos] = id;
-                    bkey[pos] = (uint16_t)(p0.key[k] >> 48);
-                }
+                in_range[k] = s < p0.c && (uint64_t)id < n;
+                if (s < p0.c && !in_range[k]) atomicOr(a.err, DERR_RANGE);
+                const unsigned m = __ballot_sync(0xffffffffu, in_range[k]);
+                pos[k] = cc + __popc(m & ((1u << lane) - 1u));
                 cc += __popc(m);
             }
-            if (lane == 0) {
-                ids[cc] = (uint32_t)v;
-                uint32_t *misc = reinterpret_cast<uint32_t *>(in + C::I_MISC);
-                misc[0] = cc;
-                misc[1] = (uint32_t)v;
-                misc[2] = (uint32_t)p0.nv;
+            unsigned char *dst;
+            uint32_t row0;
+            if (cc <= PT_SMALL) {
+                dst = stage;
+                row0 = 32 * packed;
+            } else {
+                // a large node: its own tile, written straight into the ring
+                if (!acquire()) {
+                    stop = true;
+                    break;
+                }
+                dst = info(tile % C::I);
+                row0 = 0;
             }
-            __syncwarp();
-            mbar_arrive(bar(C::BAR_CFULL + ib));
+            uint32_t *ids = reinterpret_cast<uint32_t *>(dst + I_IDS);
+            uint16_t *bkey = reinterpret_cast<uint16_t *>(dst + I_BKEY);
+            uint32_t *misc = reinterpret_cast<uint32_t *>(dst + I_MISC);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (in_range[k]) {
+                    ids[row0 + pos[k]] = (uint32_t)(p0.key[k] >> 16);
+                    bkey[row0 + pos[k]] = (uint16_t)(p0.key[k] >> 48);
+                }
+            }
+            if (lane == 0) {
+                ids[row0 + cc] = (uint32_t)v;
+                const uint32_t q = cc <= PT_SMALL ? packed : 0;
+                misc[M_NODE + 3 * q + 0] = cc;
+                misc[M_NODE + 3 * q + 1] = (uint32_t)v;
+                misc[M_NODE + 3 * q + 2] = (uint32_t)p0.nv;
+                if (cc > PT_SMALL) {
+                    misc[M_KIND] = TK_LARGE;
+                    misc[M_NODES] = 1;
+                }
+            }
+            if (cc <= PT_SMALL) {
+                __syncwarp();
+                if (++packed == 4 && !flush_packed()) stop = true;
+            } else {
+                publish();
+            }
             p0 = p1;
             p1 = p2;
+        }
+        if (!stop && packed > 0 && !flush_packed()) stop = true;
+        // one end marker for every consumer that walks the tiles in a stride
+        for (uint32_t e = 0; e < PT_ENDS && !stop; e++) {
+            if (!acquire()) break;
+            if (lane == 0) reinterpret_cast<uint32_t *>(info(tile % C::I) + I_MISC)[M_KIND] = TK_END;
+            publish();
         }
     } else if (warp == PT_MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t issued_j = 0;
+            uint32_t issued = 0;
             bool any = false, stop = false;
-            for (uint32_t j = 0;; j++) {
-                const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
-                if (v >= n) break;
-                const uint32_t ua = j % C::A, tb = j % C::T, ib = j % C::I;
-                if (!mbar_wait(bar(C::BAR_CFULL + ib), (j / C::I) & 1, abort, a.err) ||
-                    !mbar_wait(bar(C::BAR_FULL_A + ua), (j / C::A) & 1, abort, a.err) ||
-                    !mbar_wait(bar(C::BAR_TEMPTY + tb), ((j / C::T) & 1) ^ 1, abort, a.err)) {
+            for (uint32_t k = 0;; k++) {
+                const uint32_t ua = k % C::A, tb = k % C::T, ib = k % C::I;
+                if (!mbar_wait(bar(C::BAR_CFULL + ib), (k / C::I) & 1, abort, a.err)) {
+                    stop = true;
+                    break;
+                }
+                const uint32_t *misc = reinterpret_cast<const uint32_t *>(info(ib) + I_MISC);
+                const uint32_t kind = misc[M_KIND];
+                if (kind == TK_END) break;
+                if (!mbar_wait(bar(C::BAR_FULL_A + ua), (k / C::A) & 1, abort, a.err) ||
+                    !mbar_wait(bar(C::BAR_TEMPTY + tb), ((k / C::T) & 1) ^ 1, abort, a.err)) {
                     stop = true;
                     break;
                 }
                 fence_after();
-                const uint32_t rows = reinterpret_cast<const uint32_t *>(info(ib) + C::I_MISC)[0] + 1;
-                const uint32_t idesc = idesc_bf16(128, (rows + 15) & ~15u);
+                const uint32_t ncol = kind == TK_PACK ? 128u : ((misc[M_NODE] + 1 + 15) & ~15u);
+                const uint32_t idesc = idesc_bf16(128, ncol);
                 const uint32_t aB = sbase + C::OFF_A0 + ua * KB * REGION;
                 const uint32_t d = tmem + tb * 128;
 #pragma unroll
@@ -263,201 +349,247 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 mma_commit(bar(C::BAR_EMPTY_A + ua));
                 mma_commit(bar(C::BAR_TFULL + tb));
                 any = true;
-                issued_j = j;
+                issued = k;
             }
-            if (stop && any)
-                mbar_wait(bar(C::BAR_TFULL + issued_j % C::T), (issued_j / C::T) & 1, abort, a.err);
+            if (stop && any) mbar_wait(bar(C::BAR_TFULL + issued % C::T), (issued / C::T) & 1, abort, a.err);
         }
         __syncwarp();
     } else if (warp < PT_EPI_WARPS) {
         // ------------------------------------------------------------ epilogue (groups of 4 warps)
-        const uint32_t grp = warp >> 2;                 // group: nodes j = grp, grp + PT_GROUPS, ...
+        const uint32_t grp = warp >> 2;                 // group: tiles k = grp, grp + PT_GROUPS, ...
         const int quarter = warp & 3;                   // TMEM lane quarter this warp may access
-        const uint32_t r = quarter * 32 + lane;         // row = candidate slot
+        const uint32_t r = quarter * 32 + lane;         // row of the tile
         const uint32_t bar_id = 1 + grp;
-        bool stop = false;
-        for (uint32_t k = 0;; k++) {
-            const uint32_t j = grp + k * PT_GROUPS;
-            const uint64_t vv = blockIdx.x + (uint64_t)j * gridDim.x;
-            if (vv >= n) break;
-            const uint32_t tb = j % C::T, ws = j % C::W, ib = j % C::I;
-            const bool ok = !stop && __all_sync(0xffffffffu,
-                                                 mbar_wait(bar(C::BAR_TFULL + tb), (j / C::T) & 1, abort, a.err) &&
-                                                     mbar_wait(bar(C::BAR_CFULL + ib), (j / C::I) & 1, abort, a.err) &&
-                                                     mbar_wait(bar(C::BAR_WEMPTY + ws), ((j / C::W) & 1) ^ 1, abort,
-                                                               a.err));
+        unsigned char *gs = smem + C::OFF_GROUP + grp * C::G_BYTES;
+        unsigned char *wsm = smem + C::OFF_WARP + warp * C::W_BYTES;
+        for (uint32_t k = grp;; k += PT_GROUPS) {
+            const uint32_t tb = k % C::T, ib = k % C::I;
+            // the tile kind first (an end marker is never followed by an accumulator), then one
+            // decision for the whole group, so that its warps always meet the same named barriers
+            bool ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_CFULL + ib), (k / C::I) & 1, abort, a.err));
             const unsigned char *in = info(ib);
-            const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + C::I_IDS);
-            const uint16_t *bkey = reinterpret_cast<const uint16_t *>(in + C::I_BKEY);
-            uint32_t *dx = reinterpret_cast<uint32_t *>(smem + C::OFF_DX + (grp * 2 + (k & 1)) * 1024);
-            float *hn = reinterpret_cast<float *>(dx + 128);
-            unsigned char *wsl = wslot(ws);
-            uint32_t c = 0, DX = 0;
+            const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + I_IDS);
+            const uint16_t *bkey = reinterpret_cast<const uint16_t *>(in + I_BKEY);
+            const uint32_t *misc = reinterpret_cast<const uint32_t *>(in + I_MISC);
+            const uint32_t kind = ok ? misc[M_KIND] : 0u;
+            if (ok && kind != TK_END)
+                ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_TFULL + tb), (k / C::T) & 1, abort, a.err));
+            if (named_barrier_or(bar_id, 128, !ok) || kind == TK_END) break;
+            fence_after();
+            const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + tb * 128;
+
+            if (kind == TK_PACK) {
+                // ---- this warp's node, alone: rows and columns 32q .. 32q + c
+                const uint32_t nodes = misc[M_NODES];
+                if ((uint32_t)quarter < nodes) {
+                    const uint32_t c = misc[M_NODE + 3 * quarter + 0];
+                    const uint64_t v = misc[M_NODE + 3 * quarter + 1];
+                    const float nx = (float)(int32_t)misc[M_NODE + 3 * quarter + 2];
+                    const uint32_t *nid = ids + 32 * quarter;
+                    const uint16_t *nkey = bkey + 32 * quarter;
+                    uint32_t *wdx = reinterpret_cast<uint32_t *>(wsm + C::W_DX);
+                    float *whn = reinterpret_cast<float *>(wsm + C::W_HN);
+                    unsigned char *word = wsm + C::W_ORDER;
+                    uint32_t g[32];
+                    tmem_ld32(trow + quarter * 32, g);
+                    const bool valid = (uint32_t)lane < c;
+                    const float nr = __uint_as_float(pick32(g, lane));  // diagonal: exact integer
+                    const float gx = __uint_as_float(pick32(g, c));
+                    const float dxf = __fmaf_rn(-2.0f, gx, nr + nx);   // exact integer < 2^24
+                    const uint32_t DX = valid ? (uint32_t)dxf : 0u;
+                    const uint32_t T = removal_threshold(DX, a.alpha2, a.inv_alpha2);
+                    const float theta = (nr - (float)T) * 0.5f;         // exact
+                    wdx[lane] = DX;
+                    whn[lane] = 0.5f * nr;
+                    const bool bad =
+                        valid && (bf16_key(dxf) != nkey[lane] || (lane > 0 && nkey[lane - 1] > nkey[lane]));
+                    const bool full = __any_sync(0xffffffffu, bad);
+                    __syncwarp();  // every lane's D(x, .) and n / 2 are visible
+                    if (valid) word[candidate_rank(lane, c, DX, nid[lane], wdx, nid, nkey, full)] = (unsigned char)lane;
+                    // column mask: candidates y < c (not itself) with G[r][y] - n_y / 2 > theta
+                    uint32_t m = 0;
+                    const float4 *h4 = reinterpret_cast<const float4 *>(whn);
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; j4++) {
+                        const float4 h = h4[j4];
+                        m |= __fsub_rn(__uint_as_float(g[4 * j4 + 0]), h.x) > theta ? (1u << (4 * j4 + 0)) : 0u;
+                        m |= __fsub_rn(__uint_as_float(g[4 * j4 + 1]), h.y) > theta ? (1u << (4 * j4 + 1)) : 0u;
+                        m |= __fsub_rn(__uint_as_float(g[4 * j4 + 2]), h.z) > theta ? (1u << (4 * j4 + 2)) : 0u;
+                        m |= __fsub_rn(__uint_as_float(g[4 * j4 + 3]), h.w) > theta ? (1u << (4 * j4 + 3)) : 0u;
+                    }
+                    m &= ((1u << c) - 1u) & ~(1u << lane);  // c <= 31
+                    __syncwarp();
+                    // walk: lane i holds the candidate of rank i and its mask
+                    const uint32_t tl = valid ? word[lane] : 0u;
+                    const uint32_t cm = __shfl_sync(0xffffffffu, m, tl);
+                    unsigned U = __ballot_sync(0xffffffffu, valid);
+                    uint32_t e = 0, out = 0xFFFFFFFFu;
+                    while (U != 0u && e < R) {
+                        const uint32_t u = __ffs(U) - 1;
+                        const uint32_t t = __shfl_sync(0xffffffffu, tl, u);
+                        if ((uint32_t)lane == e) out = nid[t];
+                        e++;
+                        U &= ~__ballot_sync(0xffffffffu, (cm >> t) & 1u) & ~(1u << u);
+                    }
+                    for (uint32_t p = lane; p < R; p += 32) a.adj[v * R + p] = p < e ? out : 0xFFFFFFFFu;
+                    if (lane == 0) a.deg[v] = e;
+                    __syncwarp();
+                }
+                fence_before();
+                mbar_arrive(bar(C::BAR_TEMPTY + tb));
+                mbar_arrive(bar(C::BAR_IEMPTY + ib));
+                continue;
+            }
+
+            // ---- a large node, by the group: rows 0 .. c
+            uint32_t *gmask = reinterpret_cast<uint32_t *>(gs + C::G_MASK);
+            uint32_t *gids = reinterpret_cast<uint32_t *>(gs + C::G_IDS);
+            unsigned char *gorder = gs + C::G_ORDER;
+            uint32_t *dx = reinterpret_cast<uint32_t *>(gs + C::G_DX);
+            float *hn = reinterpret_cast<float *>(gs + C::G_HN);
+            const uint32_t c = misc[M_NODE + 0];
+            const uint64_t v = misc[M_NODE + 1];
+            const float nx = (float)(int32_t)misc[M_NODE + 2];
+            uint32_t DX = 0;
             float theta = 0.0f;
             bool bad = false;
-            if (ok) {
-                fence_after();
-                c = reinterpret_cast<const uint32_t *>(in + C::I_MISC)[0];
-                const float nx = (float)reinterpret_cast<const int32_t *>(in + C::I_MISC)[2];
-                // E1: n_r from the diagonal (column r lies in chunk `quarter`), D(x, z_r) from
-                // column c, the removal threshold of z_r
-                const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + tb * 128;
+            {
                 uint32_t g[32];
                 tmem_ld32(trow + quarter * 32, g);
-                const float nr = __uint_as_float(pick32(g, lane));  // exact integer < 2^23
+                const float nr = __uint_as_float(pick32(g, lane));  // diagonal: exact integer
                 hn[r] = 0.5f * nr;
                 tmem_ld32(trow + (c & ~31u), g);
                 if (r < c) {
                     const float gx = __uint_as_float(pick32(g, c & 31u));
-                    const float dxf = __fmaf_rn(-2.0f, gx, nr + nx);    // exact integer < 2^24
+                    const float dxf = __fmaf_rn(-2.0f, gx, nr + nx);
                     DX = (uint32_t)dxf;
                     const uint32_t T = removal_threshold(DX, a.alpha2, a.inv_alpha2);
-                    theta = (nr - (float)T) * 0.5f;                    // exact (multiple of 1/2)
+                    theta = (nr - (float)T) * 0.5f;
                     dx[r] = DX;
                     bad = bf16_key(dxf) != bkey[r] || (r > 0 && bkey[r - 1] > bkey[r]);
                 }
             }
-            const bool full_count = named_barrier_or(bar_id, 128, ok && bad);
-            if (ok) {
-                // E2: rank of z_r in (D(x, z), id, slot) order
-                if (r < c) {
-                    const uint32_t id = ids[r];
-                    uint32_t lo = 0;
-                    if (!full_count) {
-                        lo = r;
-                        while (lo > 0 && bkey[lo - 1] == bkey[r]) lo--;
-                    }
-                    uint32_t rank = lo;
-                    for (uint32_t s = lo; s < c && (full_count || bkey[s] == bkey[r]); s++) {
-                        const uint32_t ds = dx[s], is = ids[s];
-                        rank += (ds < DX || (ds == DX && (is < id || (is == id && s < r)))) ? 1u : 0u;
-                    }
-                    wsl[C::W_ORDER + rank] = (unsigned char)r;
-                    reinterpret_cast<uint32_t *>(wsl + C::W_IDS)[r] = id;
-                }
-                if (r == 0) {
-                    reinterpret_cast<uint32_t *>(wsl + C::W_MISC)[0] = c;
-                    reinterpret_cast<uint32_t *>(wsl + C::W_MISC)[1] =
-                        reinterpret_cast<const uint32_t *>(in + C::I_MISC)[1];
-                }
-                mbar_arrive(bar(C::BAR_IEMPTY + ib));  // node info no longer read
-                // E3: column mask of z_r -- the candidates y with G[r][y] - n_y / 2 > theta_r
-                // (both sides multiples of 1/2 below 2^23: exact)
-                uint32_t mw[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-                for (uint32_t q = 0; q < 4; q++) {
-                    if (q * 32 < c) {
-                        uint32_t g[32];
-                        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * 128 + q * 32, g);
-                        const float4 *h4 = reinterpret_cast<const float4 *>(hn + q * 32);
-                        uint32_t m = 0;
-#pragma unroll
-                        for (int j4 = 0; j4 < 8; j4++) {
-                            const float4 h = h4[j4];
-                            m |= __fsub_rn(__uint_as_float(g[4 * j4 + 0]), h.x) > theta ? (1u << (4 * j4 + 0)) : 0u;
-                            m |= __fsub_rn(__uint_as_float(g[4 * j4 + 1]), h.y) > theta ? (1u << (4 * j4 + 1)) : 0u;
-                            m |= __fsub_rn(__uint_as_float(g[4 * j4 + 2]), h.z) > theta ? (1u << (4 * j4 + 2)) : 0u;
-                            m |= __fsub_rn(__uint_as_float(g[4 * j4 + 3]), h.w) > theta ? (1u << (4 * j4 + 3)) : 0u;
-                        }
-                        const uint32_t live = c - q * 32;
-                        if (live < 32) m &= (1u << live) - 1u;
-                        if (r / 32 == q) m &= ~(1u << (r & 31));
-                        mw[q] = m;
-                    }
-                }
-                if (r < c) reinterpret_cast<uint4 *>(wsl + C::W_MASK)[r] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
-                fence_before();
-                mbar_arrive(bar(C::BAR_TEMPTY + tb));
-                mbar_arrive(bar(C::BAR_WFULL + ws));
+            const bool full = named_barrier_or(bar_id, 128, bad);
+            if (r < c) {
+                gorder[candidate_rank(r, c, DX, ids[r], dx, ids, bkey, full)] = (unsigned char)r;
+                gids[r] = ids[r];
             }
-            stop = named_barrier_or(bar_id, 128, !ok || *abort);
-            if (stop) break;
+            uint32_t mw[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) {
+                if (q * 32 < c) {
+                    uint32_t g[32];
+                    tmem_ld32(trow + q * 32, g);
+                    const float4 *h4 = reinterpret_cast<const float4 *>(hn + q * 32);
+                    uint32_t m = 0;
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; j4++) {
+                        const float4 h = h4[j4];
+                        m |= __fsub_rn(__uint_as_float(g[4 * j4 + 0]), h.x) > theta ? (1u << (4 * j4 + 0)) : 0u;
+                        m |= __fsub_rn(__uint_as_float(g[4 * j4 + 1]), h.y) > theta ? (1u << (4 * j4 + 1)) : 0u;
+                        m |= __fsub_rn(__uint_as_float(g[4 * j4 + 2]), h.z) > theta ? (1u << (4 * j4 + 2)) : 0u;
+                        m |= __fsub_rn(__uint_as_float(g[4 * j4 + 3]), h.w) > theta ? (1u << (4 * j4 + 3)) : 0u;
+                    }
+                    const uint32_t live = c - q * 32;
+                    if (live < 32) m &= (1u << live) - 1u;
+                    if (r / 32 == q) m &= ~(1u << (r & 31));
+                    mw[q] = m;
+                }
+            }
+            if (r < c) reinterpret_cast<uint4 *>(gmask)[r] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+            fence_before();
+            mbar_arrive(bar(C::BAR_TEMPTY + tb));
+            mbar_arrive(bar(C::BAR_IEMPTY + ib));
+            named_barrier_or(bar_id, 128, false);  // masks, order and ids complete
+            if (quarter == 0) {
+                // the walk: per block of 32 ranks one vote drops every candidate removed by an
+                // earlier admission, then each admission removes, with one vote, the later lanes
+                // it prunes
+                const uint4 *mask = reinterpret_cast<const uint4 *>(gmask);
+                uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0, e = 0;
+                uint32_t out[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+                for (uint32_t b = 0; b * 32 < c && e < R; b++) {
+                    const uint32_t i = b * 32 + lane;
+                    const bool valid = i < c;
+                    const uint32_t tl = valid ? gorder[i] : 0u;
+                    const uint4 cm = valid ? mask[tl] : make_uint4(0, 0, 0, 0);
+                    unsigned U = __ballot_sync(0xffffffffu,
+                                               valid && ((cm.x & A0) | (cm.y & A1) | (cm.z & A2) | (cm.w & A3)) == 0u);
+                    while (U != 0u && e < R) {
+                        const uint32_t u = __ffs(U) - 1;
+                        const uint32_t t = __shfl_sync(0xffffffffu, tl, u);
+                        const uint32_t wd = t >> 5, bit = 1u << (t & 31);
+                        A0 |= wd == 0 ? bit : 0u;
+                        A1 |= wd == 1 ? bit : 0u;
+                        A2 |= wd == 2 ? bit : 0u;
+                        A3 |= wd == 3 ? bit : 0u;
+                        const uint32_t id = gids[t];
+                        const uint32_t o = e >> 5;
+                        const bool mine = (e & 31) == (uint32_t)lane;
+                        out[0] = (mine && o == 0) ? id : out[0];
+                        out[1] = (mine && o == 1) ? id : out[1];
+                        out[2] = (mine && o == 2) ? id : out[2];
+                        out[3] = (mine && o == 3) ? id : out[3];
+                        e++;
+                        const uint32_t mwd = wd == 0 ? cm.x : wd == 1 ? cm.y : wd == 2 ? cm.z : cm.w;
+                        U &= ~__ballot_sync(0xffffffffu, (mwd >> (t & 31)) & 1u) & ~(1u << u);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t p = lane + 32 * q;
+                    if (p < R) a.adj[v * R + p] = p < e ? out[q] : 0xFFFFFFFFu;
+                }
+                if (lane == 0) a.deg[v] = e;
+            }
+            // the group's walk data is rewritten by its next large tile only after this barrier
+            if (named_barrier_or(bar_id, 128, *abort != 0)) break;
         }
-    } else if (walker_of(warp) >= 0) {
-        // ------------------------------------------------------------ walkers
-        // Walker w takes nodes j = w, w + PT_WALKERS, ... and alternates between its two walk slots
-        // (w and w + PT_WALKERS).  Per block of 32 ranks the lanes drop, with one vote, every
-        // candidate removed by an earlier admission; then each admission (the first remaining
-        // lane) removes, with one vote, the later lanes whose column mask holds it.
-        const uint32_t w = walker_of(warp);
-        const uint32_t R = a.R;
-        for (uint32_t k = 0;; k++) {
-            const uint32_t j = w + k * PT_WALKERS;
-            if (blockIdx.x + (uint64_t)j * gridDim.x >= n) break;
-            const uint32_t sl = j % C::W;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_WFULL + sl), (j / C::W) & 1, abort, a.err))) break;
-            const unsigned char *wsl = wslot(sl);
-            const uint32_t c = reinterpret_cast<const uint32_t *>(wsl + C::W_MISC)[0];
-            const uint64_t v = reinterpret_cast<const uint32_t *>(wsl + C::W_MISC)[1];
-            const uint4 *mask = reinterpret_cast<const uint4 *>(wsl + C::W_MASK);
-            const uint32_t *ids = reinterpret_cast<const uint32_t *>(wsl + C::W_IDS);
-            const unsigned char *order = wsl + C::W_ORDER;
-            uint32_t A0 = 0, A1 = 0, A2 = 0, A3 = 0;  // admitted slots
-            uint32_t e = 0;
-            uint32_t out[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-            for (uint32_t b = 0; b * 32 < c && e < R; b++) {
-                const uint32_t i = b * 32 + lane;
-                const bool valid = i < c;
-                const uint32_t tl = valid ? order[i] : 0u;
-                const uint4 cm = valid ? mask[tl] : make_uint4(0, 0, 0, 0);
-                unsigned U = __ballot_sync(0xffffffffu,
-                                           valid && ((cm.x & A0) | (cm.y & A1) | (cm.z & A2) | (cm.w & A3)) == 0u);
-                while (U != 0u && e < R) {
-                    const uint32_t u = __ffs(U) - 1;
-                    const uint32_t t = __shfl_sync(0xffffffffu, tl, u);
-                    const uint32_t wd = t >> 5, bit = 1u << (t & 31);
-                    A0 |= wd == 0 ? bit : 0u;
-                    A1 |= wd == 1 ? bit : 0u;
-                    A2 |= wd == 2 ? bit : 0u;
-                    A3 |= wd == 3 ? bit : 0u;
-                    const uint32_t id = ids[t];
-                    const uint32_t o = e >> 5;
-                    const bool mine = (e & 31) == (uint32_t)lane;
-                    out[0] = (mine && o == 0) ? id : out[0];
-                    out[1] = (mine && o == 1) ? id : out[1];
-                    out[2] = (mine && o == 2) ? id : out[2];
-                    out[3] = (mine && o == 3) ? id : out[3];
-                    e++;
-                    const uint32_t mw = wd == 0 ? cm.x : wd == 1 ? cm.y : wd == 2 ? cm.z : cm.w;
-                    U &= ~__ballot_sync(0xffffffffu, (mw >> (t & 31)) & 1u) & ~(1u << u);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const uint32_t p = lane + 32 * q;
-                if (p < R) a.adj[v * R + p] = p < e ? out[q] : 0xFFFFFFFFu;
-            }
-            if (lane == 0) a.deg[v] = e;
-            __syncwarp();
-            mbar_arrive(bar(C::BAR_WEMPTY + sl));
-        }
-    } else if (gatherer_of(warp) >= 0) {
+    } else {
         // ------------------------------------------------------------ row gathers (two warps)
-        for (uint32_t j = gatherer_of(warp);; j += PT_GATHERERS) {
-            const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
-            if (v >= n) break;
-            const uint32_t ua = j % C::A, ib = j % C::I;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_CFULL + ib), (j / C::I) & 1, abort, a.err) &&
-                                             mbar_wait(bar(C::BAR_EMPTY_A + ua), ((j / C::A) & 1) ^ 1, abort,
-                                                       a.err)))
-                break;
+        for (uint32_t k = warp - PT_GATHER_WARP0;; k += PT_GATHERERS) {
+            const uint32_t ua = k % C::A, ib = k % C::I;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_CFULL + ib), (k / C::I) & 1, abort, a.err))) break;
             const unsigned char *in = info(ib);
-            const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + C::I_IDS);
-            const uint32_t rows = reinterpret_cast<const uint32_t *>(in + C::I_MISC)[0] + 1;
-            const uint32_t ng = (rows + 3) / 4;  // gathers of four rows
-            const uint32_t fb = bar(C::BAR_FULL_A + ua);
-            if (lane == 0) mbar_arrive_tx(fb, ng * 512u * KB);
-            __syncwarp();
-            if ((uint32_t)lane < ng) {
-                int32_t y[4];
+            const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + I_IDS);
+            const uint32_t *misc = reinterpret_cast<const uint32_t *>(in + I_MISC);
+            const uint32_t kind = misc[M_KIND];
+            if (kind == TK_END) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + ua), ((k / C::A) & 1) ^ 1, abort, a.err)))
+                break;
+            // lane L gathers rows 4L .. 4L + 3 if any of them is in use
+            uint32_t y[4];
+            bool use;
+            if (kind == TK_PACK) {
+                const uint32_t q = (uint32_t)lane >> 3;
+                const uint32_t nodes = misc[M_NODES];
+                const uint32_t c = q < nodes ? misc[M_NODE + 3 * q] : 0u;
+                const uint32_t node_row = 32 * q + c;  // the node itself
+                use = q < nodes && 4 * ((uint32_t)lane & 7) <= c;
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    const uint32_t r = 4 * lane + e;
-                    y[e] = (int32_t)(r < rows ? ids[r] : ids[rows - 1]);
+                    const uint32_t row = 4 * lane + e;
+                    y[e] = use ? ids[(row & 31) <= c ? row : node_row] : 0u;
                 }
+            } else {
+                const uint32_t rows = misc[M_NODE] + 1;
+                use = 4u * lane < rows;
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const uint32_t row = 4 * lane + e;
+                    y[e] = use ? ids[row < rows ? row : rows - 1] : 0u;
+                }
+            }
+            const unsigned um = __ballot_sync(0xffffffffu, use);
+            const uint32_t fb = bar(C::BAR_FULL_A + ua);
+            if (lane == 0) mbar_arrive_tx(fb, __popc(um) * 512u * KB);
+            __syncwarp();
+            if (use) {
                 const uint32_t dst = sbase + C::OFF_A0 + ua * KB * REGION + lane * 4 * 128;
 #pragma unroll
-                for (int kb = 0; kb < KB; kb++) tma_gather4(dst + kb * REGION, &xmap, kb * 64, y[0], y[1], y[2], y[3], fb);
+                for (int kb = 0; kb < KB; kb++)
+                    tma_gather4(dst + kb * REGION, &xmap, kb * 64, (int32_t)y[0], (int32_t)y[1], (int32_t)y[2],
+                                (int32_t)y[3], fb);
             }
             if (lane != 0) mbar_arrive(fb);
         }
