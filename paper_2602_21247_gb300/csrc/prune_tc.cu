@@ -30,8 +30,9 @@
 //                large node is handled by the group together (named barrier) and walked by one
 //                of its warps.
 //   warp 12      owns TMEM (4 x 128 columns); one thread issues the Gram MMAs
-//   warp 13      node info: reservoir slots loaded two nodes ahead, compaction of the valid ids,
-//                packing; writes the tile sequence, ended by one end marker per consumer
+//   warp 13      node info: reservoir rows copied eight nodes ahead (cp.async ring), compaction
+//                of the valid ids, packing; writes the tile sequence, ended by one end marker per
+//                consumer
 //   warps 14-15  TMA gather4 of the rows of alternate tiles
 // A warp reaches TMEM lanes 32 (w % 4) .. +31 and runs on scheduler w % 4; the single-warp roles
 // sit one on each scheduler.  Waits are bounded as in the other engines (DERR_TIMEOUT; TMEM is
@@ -89,7 +90,11 @@ struct PtCfg {
     // per epilogue warp (packed nodes): D(x, .) 32, n / 2 32 floats, order 32 u8
     static constexpr int W_DX = 0, W_HN = 128, W_ORDER = 256, W_BYTES = 288;
     static constexpr int OFF_WARP = OFF_GROUP + PT_GROUPS * G_BYTES;
-    static constexpr int OFF_BAR = OFF_WARP + PT_EPI_WARPS * W_BYTES;
+    // the info warp's prefetch ring: per node its reservoir row (up to 128 slots), count and norm
+    static constexpr int P = 8;                                       // nodes in flight
+    static constexpr int P_KEYS = 0, P_CNT = 1024, P_NRM = 1028, P_BYTES = 1040;
+    static constexpr int OFF_PRE = OFF_WARP + PT_EPI_WARPS * W_BYTES;
+    static constexpr int OFF_BAR = OFF_PRE + P * P_BYTES;
     static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = A, BAR_CFULL = 2 * A, BAR_IEMPTY = 2 * A + I,
                          BAR_TFULL = 2 * A + 2 * I, BAR_TEMPTY = 2 * A + 2 * I + T, NBAR = 2 * A + 2 * I + 2 * T;
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;               // tmem base, abort flag
@@ -97,7 +102,7 @@ struct PtCfg {
     static constexpr int SMEM = BYTES + 1024;
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(T * 128 <= (int)TMEM_COLS, "TMEM budget");
-    static_assert(I_BYTES % 16 == 0 && G_BYTES % 16 == 0 && W_BYTES % 16 == 0, "alignment");
+    static_assert(I_BYTES % 16 == 0 && G_BYTES % 16 == 0 && W_BYTES % 16 == 0 && P_BYTES % 16 == 0, "alignment");
     static_assert(I >= (int)PT_ENDS, "end markers fit the ring");
 };
 
@@ -195,26 +200,23 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 
     if (warp == PT_INFO_WARP) {
         // ------------------------------------------------------------ tile info (one warp)
-        // Software pipeline: the reservoir row, count and node norm of node j + 2 are requested
-        // while node j is compacted.
-        struct Pre {
-            uint64_t key[4];
-            int32_t nv;
-            uint32_t c;
-        };
-        auto load = [&](uint64_t v, Pre &p) {
-            p.c = 0;
-            p.nv = 0;
-            if (v >= n) return;
-            p.nv = a.sqn[v];
-            const uint32_t c = a.cnt[v];
-            p.c = c < a.l_max ? c : a.l_max;
-            // every slot of the row is read, so these loads do not wait for the count
+        // Prefetch: the reservoir row, count and norm of node j + P are copied (cp.async, no
+        // registers in flight) into ring slot (j + P) % P while node j is compacted.
+        auto fetch = [&](uint32_t j) {
+            const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
+            if (v < n) {
+                const uint32_t slot = sbase + C::OFF_PRE + (j % C::P) * C::P_BYTES;
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const uint32_t s = 32 * k + lane;
-                p.key[k] = s < a.l_max ? a.res[v * a.l_max + s] : 0ull;
+                for (int k = 0; k < 4; k++) {
+                    const uint32_t s_ = 32 * k + lane;
+                    if (s_ < a.l_max) cp_async8(slot + C::P_KEYS + 8 * s_, a.res + v * a.l_max + s_);
+                }
+                if (lane == 0) {
+                    cp_async4(slot + C::P_CNT, a.cnt + v);
+                    cp_async4(slot + C::P_NRM, a.sqn + v);
+                }
             }
+            cp_async_commit();  // one group per node, empty past the end
         };
         unsigned char *stage = smem + C::OFF_STAGE;
         uint32_t *stage_misc = reinterpret_cast<uint32_t *>(stage + I_MISC);
@@ -244,24 +246,35 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             packed = 0;
             return true;
         };
-        Pre p0, p1;
-        load(blockIdx.x, p0);
-        load(blockIdx.x + (uint64_t)gridDim.x, p1);
+        for (uint32_t j = 0; j < (uint32_t)C::P; j++) fetch(j);
         for (uint32_t j = 0; !stop; j++) {
             const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
             if (v >= n) break;
-            Pre p2;
-            load(v + 2 * (uint64_t)gridDim.x, p2);
-            // valid candidates (id < n), in slot order
-            uint32_t cc = 0;
-            bool in_range[4];
-            uint32_t pos[4];
+            cp_async_wait<C::P - 1>();  // node j's group (every later one may still be in flight)
+            __syncwarp();
+            const unsigned char *pre = smem + C::OFF_PRE + (j % C::P) * C::P_BYTES;
+            const uint32_t c0 = *reinterpret_cast<const uint32_t *>(pre + C::P_CNT);
+            const uint32_t pc = c0 < a.l_max ? c0 : a.l_max;
+            const int32_t pnv = *reinterpret_cast<const int32_t *>(pre + C::P_NRM);
+            uint64_t key[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const uint32_t s = 32 * k + lane;
-                const uint32_t id = (uint32_t)(p0.key[k] >> 16);
-                in_range[k] = s < p0.c && (uint64_t)id < n;
-                if (s < p0.c && !in_range[k]) atomicOr(a.err, DERR_RANGE);
+                key[k] = s < pc ? reinterpret_cast<const uint64_t *>(pre + C::P_KEYS)[s] : 0ull;
+            }
+            __syncwarp();
+            fetch(j + C::P);  // the slot is free again
+            // valid candidates (id < n), in slot order
+            uint32_t cc = 0;
+            bool in_range[4] = {false, false, false, false};
+            uint32_t pos[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (32u * k >= pc) break;  // uniform: most reservoirs need one round
+                const uint32_t s = 32 * k + lane;
+                const uint32_t id = (uint32_t)(key[k] >> 16);
+                in_range[k] = s < pc && (uint64_t)id < n;
+                if (s < pc && !in_range[k]) atomicOr(a.err, DERR_RANGE);
                 const unsigned m = __ballot_sync(0xffffffffu, in_range[k]);
                 pos[k] = cc + __popc(m & ((1u << lane) - 1u));
                 cc += __popc(m);
@@ -286,8 +299,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 if (in_range[k]) {
-                    ids[row0 + pos[k]] = (uint32_t)(p0.key[k] >> 16);
-                    bkey[row0 + pos[k]] = (uint16_t)(p0.key[k] >> 48);
+                    ids[row0 + pos[k]] = (uint32_t)(key[k] >> 16);
+                    bkey[row0 + pos[k]] = (uint16_t)(key[k] >> 48);
                 }
             }
             if (lane == 0) {
@@ -295,7 +308,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 const uint32_t q = cc <= PT_SMALL ? packed : 0;
                 misc[M_NODE + 3 * q + 0] = cc;
                 misc[M_NODE + 3 * q + 1] = (uint32_t)v;
-                misc[M_NODE + 3 * q + 2] = (uint32_t)p0.nv;
+                misc[M_NODE + 3 * q + 2] = (uint32_t)pnv;
                 if (cc > PT_SMALL) {
                     misc[M_KIND] = TK_LARGE;
                     misc[M_NODES] = 1;
@@ -307,9 +320,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             } else {
                 publish();
             }
-            p0 = p1;
-            p1 = p2;
         }
+        cp_async_wait<0>();  // no copy outlives the warp's loop
         if (!stop && packed > 0 && !flush_packed()) stop = true;
         // one end marker for every consumer that walks the tiles in a stride
         for (uint32_t e = 0; e < PT_ENDS && !stop; e++) {

@@ -179,6 +179,21 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Asynchronous global -> shared copies (no registers hold the data in flight): committed in
+// groups, waited for with "at most N groups still pending".  Completion is visible to the copying
+// thread only; a __syncwarp after the wait publishes a warp's copies to all its lanes.
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // TMA tiled load of a 128-row x 64-column BF16 box at (x, y) into 16 KB of shared memory,
 // 128-byte swizzled -- the layout the MMA descriptors read.  Rows past the tensor read as zero.
 __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap *map, int32_t x, int32_t y,
