@@ -1,26 +1,28 @@
 // leaf_tc.cu -- A2..A4 on the 5th-generation tensor cores (tcgen05 + TMEM), byte data.
 //
 // For every leaf b and every 128-row tile of it, the kernel forms, for all |b| members j,
-//     v_ij = n_j - 2 <x_i, x_j>         (D_ij = n_i + v_ij, squared L2; n = squared norm)
+//     -D_ij / 2 = <x_i, x_j> - n_i / 2 - n_j / 2      (D = squared L2, n = squared norm)
 // directly in the tensor-core accumulator, and keeps per row the k nearest other members by
 // (D, id) (Sec. 4.2: the all-pairs distance matrix of a leaf; App. A.3: bi-directed k-NN pick).
 // The distance matrix never leaves TMEM / registers.
 //
-// The MMA operands come from one leaf-ordered BF16 copy of the members' rows: A_i = [x_i, 1,1,1,1]
-// and B_j = [x_j, -b1, -b2, -b3, -h] with n_j / 2 = b1 + b2 + b3 + h split into byte-wide pieces and
-// h = (n_j mod 2) / 2, so the accumulator is  x_i . x_j - n_j / 2 = -v_ij / 2.  Exactness: u8 / i8
-// values and the pieces are exact in BF16, every product is an integer, and for d <= 128 every
-// partial sum is a multiple of 1/2 below 2^23 in magnitude, so FP32 accumulation in any order is
-// exact and the picks equal those of the defining integer arithmetic.
+// The MMA operands come from one leaf-ordered BF16 copy of the members' rows, extended by one
+// K = 16 norm step: A_i = [x_i | 1,1,1,1, -a1,-a2,-a3,-ha] and B_j = [x_j | -b1,-b2,-b3,-hb, 1,1,1,1]
+// where n / 2 = p1 + p2 + p3 + h is split into byte-wide pieces and h = (n mod 2) / 2 (the B row's
+// pieces b, the A row's a).  Exactness: u8 / i8 values and the pieces are exact in BF16, every
+// product is an integer or a half, and for d <= 128 every partial sum is a multiple of 1/2 below
+// 2^23 in magnitude, so FP32 accumulation in any order is exact and the picks equal those of the
+// defining integer arithmetic.
 //
 // Persistent CTA (one per SM, 10 warps) over units (leaf, 128-row tile):
 //   warp 0     producer: TMA tiled loads (128 rows x 64 columns, 128-byte swizzle) of the A and B
-//              tiles from the leaf-ordered copy; B tiles also get the norm pieces (a 32-byte slice
-//              per stage) and a column-id list
+//              tiles from the leaf-ordered copy; both also get their norm pieces (a 32-byte slice
+//              per buffer / stage) and B tiles a column-id list
 //   warp 1     owns TMEM; one thread issues tcgen05.mma M=128, N<=128, K=16 steps into one of four
 //              accumulator buffers and commits to the stage / accumulator barriers
-//   warps 2-9  epilogue: tcgen05.ld 32 columns at a time, two smallest per row (k = 2) or exact
-//              (v, id) insertion (k > 2); two warps share each TMEM lane quarter
+//   warps 2-9  epilogue: tcgen05.ld 32 columns at a time, two smallest per row (k <= 2; the next
+//              chunk's load always in flight) or exact (D, id) insertion (k > 2); two warps share
+//              each TMEM lane quarter
 // Every mbarrier wait is bounded by %globaltimer (2 s); on expiry the CTA records DERR_TIMEOUT,
 // every role stops at the same points, and the TMEM is still released.
 #include "tc_common.cuh"
@@ -34,6 +36,7 @@ using namespace tc;
 // ------------------------------------------------------------------ kernel
 struct TcUnit {
     uint64_t off;   // first member of the leaf
+    uint64_t out;   // first output slot of the tile's first row
     uint32_t s;     // leaf size
     uint32_t row0;  // first row of the tile
 };
@@ -41,10 +44,7 @@ struct TcUnit {
 struct TcArgs {
     const TcUnit *units;
     const uint32_t *members;     // leaf members, ascending ids inside every leaf
-    const int32_t *member_norm;  // squared norm of every leaf member, in member order
     const uint2 *member_pieces;  // -(n / 2) of every leaf member as four BF16 pieces
-    const uint64_t *cand_off;    // per unit: first output slot of the unit's leaf
-    const uint32_t *unit_leaf;   // per unit: leaf index (for cand_off)
     uint32_t k;
     uint32_t *out_dst, *out_src;
     float *out_dist;
@@ -58,12 +58,13 @@ struct TcCfg {
     static constexpr int T = 4;                                          // accumulator buffers
     static constexpr int REGION = tc::REGION;
     static constexpr int OFF_A0 = 0;                                     // A data, 2 buffers
-    static constexpr int OFF_AN = OFF_A0 + 2 * KB * REGION;              // A norm block (constant)
+    static constexpr int OFF_AN = OFF_A0 + 2 * KB * REGION;              // A norm blocks (a 32-byte slice per buffer)
     static constexpr int OFF_B0 = OFF_AN + REGION;                       // B data, S stages
     static constexpr int OFF_BN = OFF_B0 + S * KB * REGION;              // B norm blocks (32-byte slice per stage)
     static constexpr int OFF_CI = OFF_BN + REGION;                       // T x NMAX column ids
-    static constexpr int OFF_MV = OFF_CI + T * NMAX * 4;                 // 128 rows x KMAX (v, id)
-    static constexpr int OFF_BAR = OFF_MV + ROWS * KMAX * 8;
+    static constexpr int MVBUF = KMAX == 2 ? 2 : 1;                      // k <= 2: one per unit parity
+    static constexpr int OFF_MV = OFF_CI + T * NMAX * 4;                 // MVBUF x 128 rows x KMAX (D, id)
+    static constexpr int OFF_BAR = OFF_MV + MVBUF * ROWS * KMAX * 8;
     static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = 2, BAR_FULL = 4, BAR_EMPTY = BAR_FULL + S,
                          BAR_TFULL = BAR_EMPTY + S, BAR_TEMPTY = BAR_TFULL + T, BAR_CFULL = BAR_TEMPTY + T,
                          NBAR = BAR_CFULL + T;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; i++) {
-            mbar_init(bar(C::BAR_FULL_A + i), 1);
+            mbar_init(bar(C::BAR_FULL_A + i), 32);
             mbar_init(bar(C::BAR_EMPTY_A + i), 1);
         }
         for (int i = 0; i < C::S; i++) {
@@ -138,22 +139,25 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == PRODUCER_WARP) {
         // ------------------------------------------------------------ producer (one warp)
-        // A's norm block: [1, 1, 1, 1, 0, ...] in logical chunk 0 of every row, zeros in chunk 1
+        // norm slices (K = 16 BF16 = 32 bytes = logical chunks 2 x, 2 x + 1 of a 128-byte row):
+        // A buffer x: [1,1,1,1, a-pieces, 0 x 8], B stage x: [b-pieces, 1,1,1,1, 0 x 8]; the A and B
+        // jobs rewrite only the pieces
         for (uint32_t r = lane; r < (uint32_t)ROWS; r += 32) {
-            const uint32_t one = 0x3F80u;  // bf16 1.0
-            const uint32_t base = sbase + C::OFF_AN + r * 128;
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((0u ^ (r & 7)) << 4)),
-                         "r"(one | (one << 16)), "r"(one | (one << 16)), "r"(0u), "r"(0u)
-                         : "memory");
-            asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(base + ((1u ^ (r & 7)) << 4)), "r"(0u),
-                         "r"(0u), "r"(0u), "r"(0u)
-                         : "memory");
-            // every stage's 32-byte norm slice starts zero; a B job rewrites only its first 8 bytes
-            for (uint32_t q = 0; q < 2u * C::S; q++)
+            const uint32_t one2 = 0x3F803F80u;  // two bf16 1.0
+            for (uint32_t q = 0; q < 4; q++) {
+                const bool lo = (q & 1) == 0;
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + C::OFF_AN + r * 128 +
+                                                                              ((q ^ (r & 7)) << 4)),
+                             "r"(lo ? one2 : 0u), "r"(lo ? one2 : 0u), "r"(0u), "r"(0u)
+                             : "memory");
+            }
+            for (uint32_t q = 0; q < 2u * C::S; q++) {
+                const bool lo = (q & 1) == 0;
                 asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + C::OFF_BN + r * 128 +
                                                                               ((q ^ (r & 7)) << 4)),
-                             "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+                             "r"(0u), "r"(0u), "r"(lo ? one2 : 0u), "r"(lo ? one2 : 0u)
                              : "memory");
+            }
         }
         fence_proxy_async();
         // job stream: per unit one A job, then one B job per 128-column tile.  The member ids
@@ -195,13 +199,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             return unit_job(c.i + 1, c.u + gridDim.x);
         };
-        // column ids are only needed by the general-k epilogue
+        // an A job's rows need their norm pieces, a B job's columns pieces and ids
         auto load_ids = [&](const Job &q, uint32_t (&id)[4], uint2 (&nr)[4]) {
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 const uint32_t r = q.first + 4 * lane + e;
-                const bool in = q.kind == 1 && r < q.s;
-                id[e] = (KMAX > 2 && in) ? a.members[q.off + r] : 0u;
+                const bool in = q.kind <= 1 && r < q.s;
+                id[e] = (in && q.kind == 1) ? a.members[q.off + r] : 0u;
                 nr[e] = in ? a.member_pieces[q.off + r] : make_uint2(0u, 0u);
             }
         };
@@ -220,13 +224,28 @@ __global__ void __launch_bounds__(THREADS, 1)
                 ok = mbar_wait(bar(C::BAR_EMPTY_A + ua), ((cur.i >> 1) & 1) ^ 1, abort, a.err);
                 // the next job's ids and norm pieces: requested here, consumed next iteration
                 load_ids(nxt, nid, nnr);
-                if (ok && lane == 0) {
-                    const uint32_t fb = bar(C::BAR_FULL_A + ua);
-                    mbar_arrive_tx(fb, KB * C::REGION);
-                    const uint32_t dst = sbase + C::OFF_A0 + ua * KB * C::REGION;
+                if (ok) {
+                    // -(n_i / 2) of the tile's rows (zero past the leaf): bytes 8..15 of logical
+                    // chunk 2 ua
 #pragma unroll
-                    for (int kb = 0; kb < KB; kb++)
-                        tma_load_tile(dst + kb * C::REGION, &map, kb * 64, (int32_t)(cur.off + cur.first), fb);
+                    for (int e = 0; e < 4; e++) {
+                        const uint32_t r = 4 * lane + e;
+                        asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(sbase + C::OFF_AN + r * 128 +
+                                                                             (((2 * ua) ^ (r & 7)) << 4) + 8),
+                                     "r"(nr[e].x), "r"(nr[e].y)
+                                     : "memory");
+                    }
+                    fence_proxy_async();
+                    const uint32_t fb = bar(C::BAR_FULL_A + ua);
+                    if (lane == 0) {
+                        mbar_arrive_tx(fb, KB * C::REGION);
+                        const uint32_t dst = sbase + C::OFF_A0 + ua * KB * C::REGION;
+#pragma unroll
+                        for (int kb = 0; kb < KB; kb++)
+                            tma_load_tile(dst + kb * C::REGION, &map, kb * 64, (int32_t)(cur.off + cur.first), fb);
+                    } else {
+                        mbar_arrive(fb);
+                    }
                 }
             } else {
                 const uint32_t st = j % C::S, tb = j % C::T;
@@ -237,7 +256,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const uint32_t r = 4 * lane + e;
-                        if (KMAX > 2) ci[r] = cur.first + r < cur.s ? id[e] : 0xFFFFFFFFu;
+                        ci[r] = cur.first + r < cur.s ? id[e] : 0xFFFFFFFFu;
                         // -(n_j / 2) as four BF16-exact pieces (zero past the leaf) in the first 8
                         // bytes of this stage's 32-byte slice (logical chunk 2 st)
                         asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(sbase + C::OFF_BN + r * 128 +
@@ -302,9 +321,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                         const uint64_t bd = smem_desc_sw128(bB + (kk >> 2) * C::REGION + (kk & 3) * 32);
                         mma_bf16(d, ad, bd, idesc, kk > 0 ? 1u : 0u);
                     }
-                    // + n_j: ones x norm pieces (this stage's 32-byte slice)
-                    mma_bf16(d, smem_desc_sw128(sbase + C::OFF_AN), smem_desc_sw128(sbase + C::OFF_BN + st * 32),
-                             idesc, 1u);
+                    // - n_i / 2 - n_j / 2: the norm slices of this A buffer and this B stage
+                    mma_bf16(d, smem_desc_sw128(sbase + C::OFF_AN + ua * 32),
+                             smem_desc_sw128(sbase + C::OFF_BN + st * 32), idesc, 1u);
                     mma_commit(bar(C::BAR_EMPTY + st));
                     mma_commit(bar(C::BAR_TFULL + tb));
                     any = true;
@@ -317,8 +336,163 @@ __global__ void __launch_bounds__(THREADS, 1)
                 mbar_wait(bar(C::BAR_TFULL + issued_j % C::T), (issued_j / C::T) & 1, abort, a.err);
         }
         __syncwarp();
+    } else if constexpr (KMAX == 2) {
+        // ------------------------------------------------------------ epilogue, k <= 2
+        // D_ij = -2 acc is an integer below 2^23 (d <= 128 bytes), so fma(-2, acc, 2^23) = D + 2^23
+        // exactly and its bit pattern is 0x4B000000 + D: times 128 plus the column in the tile it is
+        // a 32-bit key ordered by (D, column), i.e. by (D, id) -- the leaf's members are in ascending
+        // id order.  Two smallest per chain: k2 = min(k2, max(k1, key)), k1 = min(k1, key).  Warp
+        // (quarter, half) takes chunks half and half + 2 of every tile; one chunk's TMEM load is
+        // always in flight while the other is ranked, across tiles and units.
+        const int ew = warp - EPI_WARP0;
+        const int half = ew >> 2;
+        const int quarter = warp & 3;
+        const uint32_t r = quarter * 32 + lane;
+        const uint32_t tq = tmem + ((uint32_t)(quarter * 32) << 16);
+        uint64_t *mv = reinterpret_cast<uint64_t *>(smem + C::OFF_MV);
+        // warp-uniform: tcgen05.ld is a warp-collective instruction
+        auto open_tile = [&](uint32_t jj) {
+            const uint32_t tb = jj % C::T, ph = (jj / C::T) & 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_TFULL + tb), ph, abort, a.err) &&
+                                                        mbar_wait(bar(C::BAR_CFULL + tb), ph, abort, a.err));
+            fence_after();
+            return ok;
+        };
+        // two smallest keys of chunk q (columns base .. base + 31 of the leaf) folded into T1 <= T2
+        auto rank_chunk = [&](uint32_t (&g)[32], uint32_t q, uint32_t base, uint32_t s, uint32_t self_col,
+                              uint32_t &T1, uint32_t &T2) {
+            uint32_t key[32];
+#pragma unroll
+            for (int jj = 0; jj < 32; jj++)
+                key[jj] = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(g[jj]), 8388608.0f)) * 128u +
+                          (q * 32 + jj);
+            // the row's own column and columns past the leaf never qualify (both tests are uniform
+            // over the warp: a warp's rows are 32 consecutive columns)
+            if (self_col - base < 32u || base + 32 > s) {
+#pragma unroll
+                for (int jj = 0; jj < 32; jj++)
+                    if (base + jj == self_col || base + jj >= s) key[jj] = ~0u;
+            }
+            uint32_t k1[4], k2[4];
+#pragma unroll
+            for (int ch = 0; ch < 4; ch++) {
+                k1[ch] = key[ch];
+                k2[ch] = ~0u;
+            }
+#pragma unroll
+            for (int jj = 4; jj < 32; jj++) {
+                const int ch = jj & 3;
+                k2[ch] = min(k2[ch], max(k1[ch], key[jj]));
+                k1[ch] = min(k1[ch], key[jj]);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 4; ch++) {
+                const uint32_t m2 = min(max(T1, k1[ch]), min(T2, k2[ch]));
+                T1 = min(T1, k1[ch]);
+                T2 = m2;
+            }
+        };
+        uint32_t u = blockIdx.x, i = 0, j = 0, t = 0;
+        TcUnit un = a.units[u];
+        TcUnit unx = a.units[u + gridDim.x < nunits ? u + gridDim.x : u];
+        uint32_t my_id = un.row0 + r < un.s ? a.members[un.off + un.row0 + r] : 0xFFFFFFFFu;
+        uint64_t RK1 = ~0ull, RK2 = ~0ull;  // running two smallest (D << 32 | id) of this half
+        uint32_t gA[32], gB[32];
+#pragma unroll
+        for (int jj = 0; jj < 32; jj++) gA[jj] = gB[jj] = 0u;
+        bool failed = !open_tile(0);
+        bool cur_ok = !failed;  // tile j is open (its accumulator and column ids are ready)
+        if (!failed && half * 32 < (un.s < (uint32_t)C::NMAX ? un.s : (uint32_t)C::NMAX))
+            tmem_ld32_async(tq + half * 32, gA);
+        for (;;) {
+            const uint32_t tb = j % C::T;
+            const uint32_t c0 = t * C::NMAX;
+            const uint32_t ncols = un.s - c0 < (uint32_t)C::NMAX ? un.s - c0 : C::NMAX;
+            const uint32_t nct = (un.s + C::NMAX - 1) / C::NMAX;
+            const uint32_t self_col = un.row0 + r;
+            const bool v0 = cur_ok && half * 32 < ncols;
+            const bool v1 = cur_ok && (half + 2) * 32 < ncols;
+            tmem_wait_ld_regs(gA);
+            if (v1) tmem_ld32_async(tq + tb * C::NMAX + (half + 2) * 32, gB);
+            uint32_t T1 = ~0u, T2 = ~0u;
+            if (v0) rank_chunk(gA, half, c0 + half * 32, un.s, self_col, T1, T2);
+            tmem_wait_ld_regs(gB);
+            // open the next tile -- the rest of this unit, else the next unit's first -- and start
+            // its first chunk's load before ranking this tile's second chunk
+            const bool last = t + 1 == nct;
+            bool nxt_ok = false;
+            if (!failed && (!last || u + gridDim.x < nunits)) {
+                nxt_ok = open_tile(j + 1);
+                failed = !nxt_ok;
+                const uint32_t nrem = last ? unx.s : un.s - c0 - C::NMAX;
+                if (nxt_ok && half * 32 < nrem) tmem_ld32_async(tq + ((j + 1) % C::T) * C::NMAX + half * 32, gA);
+            }
+            if (v1) rank_chunk(gB, half + 2, c0 + (half + 2) * 32, un.s, self_col, T1, T2);
+            if (cur_ok) {
+                // the tile's pair as (D << 32 | id), merged into the running pair
+                const uint32_t *ci = colid + tb * C::NMAX;
+                const uint64_t K1 =
+                    T1 == ~0u ? ~0ull : ((uint64_t)((T1 & 0x7FFFFFFFu) >> 7) << 32) | ci[T1 & 127u];
+                const uint64_t K2 =
+                    T2 == ~0u ? ~0ull : ((uint64_t)((T2 & 0x7FFFFFFFu) >> 7) << 32) | ci[T2 & 127u];
+                const uint64_t m2 = min(max(RK1, K1), min(RK2, K2));
+                RK1 = min(RK1, K1);
+                RK2 = m2;
+                // the accumulator buffer and the column ids of tile j are free again
+                fence_before();
+                mbar_arrive(bar(C::BAR_TEMPTY + tb));
+            }
+            cur_ok = nxt_ok;
+            j++;
+            if (!last) {
+                t++;
+                continue;
+            }
+            // unit done: merge the two halves of each row (one buffer per unit parity, so the next
+            // unit's writes cannot meet this unit's reads) and emit
+            uint64_t *m = mv + ((i & 1) * ROWS + r) * 2;
+            if (half == 1) {
+                m[0] = RK1;
+                m[1] = RK2;
+            }
+            failed = named_barrier_or(1, EPI_WARPS * 32, failed || *abort);
+            if (half == 0 && un.row0 + r < un.s && !failed) {
+                const uint64_t P1 = m[0], P2 = m[1];
+                const uint64_t R2 = min(max(RK1, P1), min(RK2, P2));
+                const uint64_t R1 = min(RK1, P1);
+                const uint32_t kk = un.s - 1 < a.k ? un.s - 1 : a.k;
+                uint64_t w = un.out + (uint64_t)r * 2 * kk;
+#pragma unroll
+                for (int p = 0; p < 2; p++) {
+                    if ((uint32_t)p < kk) {
+                        const uint64_t R = p == 0 ? R1 : R2;
+                        const bool none = R == ~0ull;
+                        const uint32_t src = none ? my_id : (uint32_t)R;
+                        const float D = none ? __int_as_float(0x7f800000) : (float)(uint32_t)(R >> 32);
+                        a.out_dst[w] = my_id;
+                        a.out_src[w] = src;
+                        a.out_dist[w] = D;
+                        a.out_dst[w + 1] = src;
+                        a.out_src[w + 1] = my_id;
+                        a.out_dist[w + 1] = D;
+                        w += 2;
+                    }
+                }
+            }
+            u += gridDim.x;
+            i++;
+            if (failed || u >= nunits) break;
+            un = unx;
+            unx = a.units[u + gridDim.x < nunits ? u + gridDim.x : u];
+            my_id = un.row0 + r < un.s ? a.members[un.off + un.row0 + r] : 0xFFFFFFFFu;
+            t = 0;
+            RK1 = ~0ull;
+            RK2 = ~0ull;
+        }
+        // a load started for a tile that a failure left unused completes before TMEM is released
+        tmem_wait_ld();
     } else {
-        // ------------------------------------------------------------ epilogue
+        // ------------------------------------------------------------ epilogue, k > 2
         const int ew = warp - EPI_WARP0;          // 0..7
         const int half = ew >> 2;                    // which column chunks
         const int quarter = warp & 3;                // TMEM lane quarter this warp may access
@@ -340,12 +514,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                 ki[p] = 0xFFFFFFFFu;
             }
             const uint32_t nct = (s + C::NMAX - 1) / C::NMAX;
-            const uint32_t self_col = row0 + r;      // this row's own column inside the leaf
-            // k = 2: running two smallest (D << 32 | column) of this half, and per tile the two
-            // smallest 32-bit keys (D << 7 | column in the tile) -- see the tile loop below
-            uint64_t RK1 = ~0ull, RK2 = ~0ull;
-            const int32_t n_i = row_ok ? a.member_norm[off + row0 + r] : 0;
-            const float nb23 = (float)n_i + 8388608.0f;  // n_i + 2^23, exact
             for (uint32_t t = 0; t < nct; t++, j++) {
                 const uint32_t tb = j % C::T, ph = (j / C::T) & 1;
                 if (failed) continue;
@@ -360,71 +528,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t c0 = t * C::NMAX;
                 const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
                 const uint32_t *info = colid + tb * C::NMAX;
-                if constexpr (KMAX == 2) {
-                    // D_ij = n_i - 2 acc is an integer below 2^23 (d <= 128 bytes), so
-                    // fma(-2, acc, n_i + 2^23) = D + 2^23 exactly and its bit pattern is
-                    // 0x4B000000 + D: times 128 plus the column in the tile it is a 32-bit key whose
-                    // order is (D, column) -- ties to the smaller column, i.e. the smaller id.
-                    // Two smallest per chain: k2 = min(k2, max(k1, key)), k1 = min(k1, key).
-                    uint32_t T1 = ~0u, T2 = ~0u;
-                    // this half's chunks of the tile (q = half, half + 2): both loads in flight
-                    // before one wait
-                    uint32_t gv[2][32];
-                    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX;
-                    const bool two = (half + 2) * 32 < ncols;
-                    if (half * 32 < ncols) tmem_ld32_async(tbase + half * 32, gv[0]);
-                    if (two) tmem_ld32_async(tbase + (half + 2) * 32, gv[1]);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const uint32_t q = half + 2 * h;
-                        if (q * 32 >= ncols) break;
-                        uint32_t key[32];
-#pragma unroll
-                        for (int jj = 0; jj < 32; jj++)
-                            key[jj] = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(gv[h][jj]), nb23)) * 128u +
-                                      (q * 32 + jj);
-                        const uint32_t base = c0 + q * 32;
-                        // the row's own column and columns past the leaf never qualify (both tests
-                        // are uniform over the warp: a warp's rows are 32 consecutive columns)
-                        if (self_col - base < 32u || base + 32 > s) {
-#pragma unroll
-                            for (int jj = 0; jj < 32; jj++)
-                                if (base + jj == self_col || base + jj >= s) key[jj] = ~0u;
-                        }
-                        uint32_t k1[4], k2[4];
-#pragma unroll
-                        for (int ch = 0; ch < 4; ch++) {
-                            k1[ch] = key[ch];
-                            k2[ch] = ~0u;
-                        }
-#pragma unroll
-                        for (int jj = 4; jj < 32; jj++) {
-                            const int ch = jj & 3;
-                            k2[ch] = min(k2[ch], max(k1[ch], key[jj]));
-                            k1[ch] = min(k1[ch], key[jj]);
-                        }
-#pragma unroll
-                        for (int ch = 0; ch < 4; ch++) {
-                            const uint32_t m2 = min(max(T1, k1[ch]), min(T2, k2[ch]));
-                            T1 = min(T1, k1[ch]);
-                            T2 = m2;
-                        }
-                    }
-                    // the tile's pair as (D << 32 | column in the leaf), merged into the running pair
-                    const uint64_t K1 = T1 == ~0u ? ~0ull
-                                                  : ((uint64_t)((T1 & 0x7FFFFFFFu) >> 7) << 32) | (c0 + (T1 & 127u));
-                    const uint64_t K2 = T2 == ~0u ? ~0ull
-                                                  : ((uint64_t)((T2 & 0x7FFFFFFFu) >> 7) << 32) | (c0 + (T2 & 127u));
-                    const uint64_t m2 = min(max(RK1, K1), min(RK2, K2));
-                    RK1 = min(RK1, K1);
-                    RK2 = m2;
-                } else {
                 for (uint32_t q = half; q * 32 < ncols; q += 2) {
                     uint32_t gv[32];
                     tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX + q * 32, gv);
                     if (!row_ok) continue;
-                    // the accumulator holds -v/2; rank by v/2 (same order, exact)
+                    // the accumulator holds -D/2; rank by D/2 (same order, exact)
                     float v[32];
 #pragma unroll
                     for (int jj = 0; jj < 32; jj++) v[jj] = -__uint_as_float(gv[jj]);
@@ -447,20 +555,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                         }
                     }
                 }
-                }
                 fence_before();
                 mbar_arrive(bar(C::BAR_TEMPTY + tb));
-            }
-            if constexpr (KMAX == 2) {
-                // columns -> member ids (the leaf's members are in ascending id order); kv holds
-                // v / 2 = (D - n_i) / 2, exact
-                const uint32_t C1 = (uint32_t)RK1, C2 = (uint32_t)RK2;
-                ki[0] = RK1 != ~0ull && C1 < s ? a.members[off + C1] : 0xFFFFFFFFu;
-                ki[1] = RK2 != ~0ull && C2 < s ? a.members[off + C2] : 0xFFFFFFFFu;
-                kv[0] = ki[0] == 0xFFFFFFFFu ? __int_as_float(0x7f800000)
-                                             : ((float)(uint32_t)(RK1 >> 32) - (float)n_i) * 0.5f;
-                kv[1] = ki[1] == 0xFFFFFFFFu ? __int_as_float(0x7f800000)
-                                             : ((float)(uint32_t)(RK2 >> 32) - (float)n_i) * 0.5f;
             }
             // merge the two halves of each row, then emit
             if (half == 1) {
@@ -476,13 +572,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (id != 0xFFFFFFFFu) topk_insert<KMAX>(kv, ki, e.x, id);
                 }
                 const uint32_t kk = s - 1 < a.k ? s - 1 : a.k;
-                const float ni = (float)a.member_norm[off + row0 + r];
-                uint64_t w = a.cand_off[a.unit_leaf[u]] + (uint64_t)(row0 + r) * 2 * kk;
+                uint64_t w = un.out + (uint64_t)r * 2 * kk;
 #pragma unroll
                 for (int p = 0; p < KMAX; p++) {
                     if ((uint32_t)p < kk) {
                         const uint32_t src = ki[p] == 0xFFFFFFFFu ? my_id : ki[p];
-                        const float D = __fadd_rn(ni, __fmul_rn(2.0f, kv[p]));
+                        const float D = __fmul_rn(2.0f, kv[p]);
                         a.out_dst[w] = my_id;
                         a.out_src[w] = src;
                         a.out_dist[w] = D;
@@ -508,13 +603,16 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 __global__ void build_units(const uint32_t *tile_grp, const uint32_t *tile_row0, uint64_t nunits,
-                            const uint64_t *leaf_off, TcUnit *units) {
+                            const uint64_t *leaf_off, const uint64_t *cand_off, uint32_t k, TcUnit *units) {
     for (uint64_t u = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; u < nunits; u += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t g = tile_grp[u];
         TcUnit x;
         x.off = leaf_off[g];
         x.s = (uint32_t)(leaf_off[g + 1] - x.off);
         x.row0 = tile_row0[u];
+        // row r of a leaf of s members writes 2 min(s - 1, k) slots from cand_off + r 2 min(s - 1, k)
+        const uint32_t kk = x.s - 1 < k ? x.s - 1 : k;
+        x.out = cand_off[g] + (uint64_t)x.row0 * 2 * kk;
         units[u] = x;
     }
 }
@@ -634,13 +732,9 @@ __global__ void max_leaf_size(const uint32_t *size, uint64_t L, unsigned *out) {
     atomicMax(out, m);
 }
 
-__global__ void member_norms(const uint32_t *members, uint64_t M, const int32_t *sqnorm, int32_t *out,
-                             uint2 *pieces) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < M; i += (uint64_t)gridDim.x * blockDim.x) {
-        const int32_t nrm = sqnorm[members[i]];
-        out[i] = nrm;
-        pieces[i] = neg_half_norm_pieces((uint32_t)nrm);
-    }
+__global__ void member_pieces(const uint32_t *members, uint64_t M, const int32_t *sqnorm, uint2 *pieces) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < M; i += (uint64_t)gridDim.x * blockDim.x)
+        pieces[i] = neg_half_norm_pieces((uint32_t)sqnorm[members[i]]);
 }
 
 template <int KB, int KMAX>
@@ -655,7 +749,6 @@ int launch_tc(const CUtensorMap &map, const TcArgs &args, uint64_t ntiles) {
         const uint64_t cnt = ntiles - t0 < 0xFFFFFFFFull ? ntiles - t0 : 0xFFFFFFFFull;
         TcArgs a = args;
         a.units += t0;
-        a.unit_leaf += t0;
         const unsigned grid = (unsigned)(cnt < (uint64_t)sms ? cnt : (uint64_t)sms);
         kern<<<grid, THREADS, C::SMEM, stream()>>>(map, a, (uint32_t)cnt);
         PIPNN_LAUNCH_CHECK();
@@ -699,9 +792,7 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
     // which is the tie order of (D, id)
     uint32_t *smem_members = nullptr;
     PIPNN_TRY(ws.alloc(&smem_members, M));
-    int32_t *mnorm = nullptr;
     uint2 *mpieces = nullptr;
-    PIPNN_TRY(ws.alloc(&mnorm, M));
     PIPNN_TRY(ws.alloc(&mpieces, M));
     if (M) {
         PIPNN_CUDA(cudaMemcpyAsync(smem_members, mem, M * 4, cudaMemcpyDeviceToDevice, stream()));
@@ -710,7 +801,7 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
         sort_leaf_members<<<grid_for(L, 1, 152u * 16u), 1024, 0, stream()>>>(off, L, smem_members);
         PIPNN_LAUNCH_CHECK();
         mem = smem_members;
-        member_norms<<<grid_for(M, 256), 256, 0, stream()>>>(mem, M, sqnorm, mnorm, mpieces);
+        member_pieces<<<grid_for(M, 256), 256, 0, stream()>>>(mem, M, sqnorm, mpieces);
         PIPNN_LAUNCH_CHECK();
     }
     if (M >= 0x7FFFFF00ull) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes < 2^31 leaf members");
@@ -725,18 +816,16 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
     TcUnit *units = nullptr;
     PIPNN_TRY(ws.alloc(&units, ntiles));
     if (ntiles) {
-        build_units<<<grid_for(ntiles, 256), 256, 0, stream()>>>(tile_grp, tile_row0, ntiles, off, units);
+        build_units<<<grid_for(ntiles, 256), 256, 0, stream()>>>(tile_grp, tile_row0, ntiles, off, cand_off, k,
+                                                                 units);
         PIPNN_LAUNCH_CHECK();
     }
     CUtensorMap map;
     PIPNN_TRY(encode_rows_map(&map, staged, M ? M : 1, kp, false));
     TcArgs a{};
     a.units = units;
-    a.unit_leaf = tile_grp;
     a.members = mem;
-    a.member_norm = mnorm;
     a.member_pieces = mpieces;
-    a.cand_off = cand_off;
     a.k = k;
     a.out_dst = out_dst;
     a.out_src = out_src;

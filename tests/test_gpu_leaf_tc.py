@@ -1,10 +1,11 @@
 """The tcgen05 tensor-core leaf engine (byte data) against the oracle: identical candidate edges.
 
-BF16 holds every u8 / i8 value, -2x and the byte-wide pieces of a squared norm exactly and, for
-d <= 128, every partial sum of the accumulated n_j - 2<x_i, x_j> is an integer below 2^24, so the
-tensor-core result is exact and the picks must equal the oracle's integer picks bit for bit --
-including extreme values (all 255, int8 -128) and leaves whose size is not a multiple of the
-128-row / 128-column tiles."""
+BF16 holds every u8 / i8 value and the byte-wide pieces of the halved squared norms exactly and,
+for d <= 128, every partial sum of the accumulated <x_i, x_j> - n_i / 2 - n_j / 2 (= -D_ij / 2) is a
+multiple of 1/2 below 2^23 in magnitude, so the tensor-core result is exact and the picks must
+equal the oracle's integer picks bit for bit -- including extreme values (all 255, int8 -128),
+leaves whose size is not a multiple of the 128-row / 128-column tiles, and many leaves per CTA
+(the engine carries loads across consecutive tiles and units)."""
 import numpy as np
 import pytest
 
@@ -60,6 +61,19 @@ SIZES = [1, 2, 3, 15, 16, 17, 127, 128, 129, 255, 256, 257, 383, 511, 600, 1024,
 def test_tc_pick_ragged_leaves_u8(k):
     X = synth.mixture(12000, 128, synth.U8, 50, 10.0, seed=51)
     off, mem = random_leaves(12000, SIZES, seed=k)
+    check(X, off, mem, k)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_tc_pick_many_leaves_per_cta(k):
+    # ~1,700 row tiles over ~600 leaves of 1 .. 700 members: every persistent CTA walks a dozen
+    # units of mixed sizes (one-tile leaves, leaves of <= 32 members, ragged last tiles)
+    rng = np.random.default_rng(57)
+    sizes = np.concatenate([rng.integers(1, 33, 150), rng.integers(33, 700, 450)])
+    rng.shuffle(sizes)
+    n = 30000
+    X = synth.mixture(n, 128, synth.U8, 80, 10.0, seed=58)
+    off, mem = random_leaves(n, sizes.tolist(), seed=k + 10)
     check(X, off, mem, k)
 
 
