@@ -71,35 +71,89 @@ __device__ __forceinline__ void hash_pair(const float *S, uint32_t m, uint32_t v
     }
 }
 
-// Two consecutive candidates per thread.  The leaf pick emits every pair in both directions next
-// to each other, (v, c) then (c, v): such a mirrored pair needs the two sketch rows only once.
+// Residualised hashes of node v against c1 and c2 and back, with v's sketch row loaded once.
+__device__ __forceinline__ void hash_fan(const float *S, uint32_t m, uint32_t v, uint32_t c1, uint32_t c2,
+                                         uint32_t &h_v1, uint32_t &h_1v, uint32_t &h_v2, uint32_t &h_2v) {
+    h_v1 = h_1v = h_v2 = h_2v = 0;
+    const float *sv = S + (uint64_t)v * m, *s1 = S + (uint64_t)c1 * m, *s2 = S + (uint64_t)c2 * m;
+    if ((m & 3u) == 0) {
+        const float4 *v4 = reinterpret_cast<const float4 *>(sv), *a4 = reinterpret_cast<const float4 *>(s1),
+                     *b4 = reinterpret_cast<const float4 *>(s2);
+        for (uint32_t i = 0; i < m / 4; i++) {
+            const float4 x = __ldg(v4 + i), a = __ldg(a4 + i), b = __ldg(b4 + i);
+            h_v1 |= ((a.x >= x.x ? 1u : 0u) | (a.y >= x.y ? 2u : 0u) | (a.z >= x.z ? 4u : 0u) |
+                     (a.w >= x.w ? 8u : 0u)) << (4 * i);
+            h_1v |= ((x.x >= a.x ? 1u : 0u) | (x.y >= a.y ? 2u : 0u) | (x.z >= a.z ? 4u : 0u) |
+                     (x.w >= a.w ? 8u : 0u)) << (4 * i);
+            h_v2 |= ((b.x >= x.x ? 1u : 0u) | (b.y >= x.y ? 2u : 0u) | (b.z >= x.z ? 4u : 0u) |
+                     (b.w >= x.w ? 8u : 0u)) << (4 * i);
+            h_2v |= ((x.x >= b.x ? 1u : 0u) | (x.y >= b.y ? 2u : 0u) | (x.z >= b.z ? 4u : 0u) |
+                     (x.w >= b.w ? 8u : 0u)) << (4 * i);
+        }
+    } else {
+        for (uint32_t i = 0; i < m; i++) {
+            const float x = __ldg(sv + i), a = __ldg(s1 + i), b = __ldg(s2 + i);
+            h_v1 |= (a >= x ? 1u : 0u) << i;
+            h_1v |= (x >= a ? 1u : 0u) << i;
+            h_v2 |= (b >= x ? 1u : 0u) << i;
+            h_2v |= (x >= b ? 1u : 0u) << i;
+        }
+    }
+}
+
+// Four consecutive candidates per thread.  The leaf pick emits every pair in both directions next
+// to each other, (v, c) then (c, v), and a node's picks one after another: for k = 2 a group of
+// four is (v, c1), (c1, v), (v, c2), (c2, v), which needs three sketch rows and three cursor
+// updates instead of six and four.  Any other group is taken as two pairs (mirrored pairs load
+// their two rows once) or one candidate at a time.
 // cursor[v] starts at v's first slot (the exclusive prefix sum) and is advanced atomically, so
 // afterwards it holds the first slot of v + 1 and v's run is [cursor[v - 1], cursor[v]).
 __global__ void hp_scatter(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, uint64_t n,
                            const float *S, uint32_t m, unsigned long long *cursor, uint64_t *slots) {
-    const uint64_t npairs = (count + 1) / 2;
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < npairs; p += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t e0 = 2 * p, e1 = e0 + 1;
-        const bool has1 = e1 < count;
-        const uint32_t v0 = dst[e0], c0 = src[e0];
-        const uint32_t v1 = has1 ? dst[e1] : 0u, c1 = has1 ? src[e1] : 0u;
-        const float w0 = dist[e0], w1 = has1 ? dist[e1] : 0.0f;
-        const bool ok0 = v0 < n && c0 < n && v0 != c0;
-        const bool ok1 = has1 && v1 < n && c1 < n && v1 != c1;
-        uint32_t h0 = 0, h1 = 0;
-        if (ok0) {
-            uint32_t back;
-            hash_pair(S, m, v0, c0, h0, back);
-            if (ok1) {
-                if (v1 == c0 && c1 == v0) h1 = back;
-                else hash_pair(S, m, v1, c1, h1, back);
-            }
-        } else if (ok1) {
-            uint32_t back;
-            hash_pair(S, m, v1, c1, h1, back);
+    const uint64_t ngroups = (count + 3) / 4;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < ngroups; g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = 4 * g;
+        uint32_t v[4], c[4];
+        float w[4];
+        bool ok[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const bool in = e + q < count;
+            v[q] = in ? dst[e + q] : 0u;
+            c[q] = in ? src[e + q] : 0u;
+            w[q] = in ? dist[e + q] : 0.0f;
+            ok[q] = in && v[q] < n && c[q] < n && v[q] != c[q];
         }
-        if (ok0) slots[atomicAdd(&cursor[v0], 1ull)] = reservoir_slot(w0, c0, h0);
-        if (ok1) slots[atomicAdd(&cursor[v1], 1ull)] = reservoir_slot(w1, c1, h1);
+        const bool mirror01 = ok[0] && ok[1] && v[1] == c[0] && c[1] == v[0];
+        const bool mirror23 = ok[2] && ok[3] && v[3] == c[2] && c[3] == v[2];
+        if (mirror01 && mirror23 && v[2] == v[0]) {
+            uint32_t h01, h10, h02, h20;
+            hash_fan(S, m, v[0], c[0], c[2], h01, h10, h02, h20);
+            const unsigned long long p = atomicAdd(&cursor[v[0]], 2ull);
+            slots[p] = reservoir_slot(w[0], c[0], h01);
+            slots[p + 1] = reservoir_slot(w[2], c[2], h02);
+            slots[atomicAdd(&cursor[v[1]], 1ull)] = reservoir_slot(w[1], c[1], h10);
+            slots[atomicAdd(&cursor[v[3]], 1ull)] = reservoir_slot(w[3], c[3], h20);
+            continue;
+        }
+#pragma unroll
+        for (int pr = 0; pr < 2; pr++) {
+            const int q0 = 2 * pr, q1 = q0 + 1;
+            uint32_t h0 = 0, h1 = 0;
+            if (ok[q0]) {
+                uint32_t back;
+                hash_pair(S, m, v[q0], c[q0], h0, back);
+                if (ok[q1]) {
+                    if (v[q1] == c[q0] && c[q1] == v[q0]) h1 = back;
+                    else hash_pair(S, m, v[q1], c[q1], h1, back);
+                }
+            } else if (ok[q1]) {
+                uint32_t back;
+                hash_pair(S, m, v[q1], c[q1], h1, back);
+            }
+            if (ok[q0]) slots[atomicAdd(&cursor[v[q0]], 1ull)] = reservoir_slot(w[q0], c[q0], h0);
+            if (ok[q1]) slots[atomicAdd(&cursor[v[q1]], 1ull)] = reservoir_slot(w[q1], c[q1], h1);
+        }
     }
 }
 
@@ -170,12 +224,27 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
     for (uint32_t w = lane; w < HP_HT; w += 32) ht[w] = ~0ull;
     __syncwarp();
 
-    for (uint64_t v = (uint64_t)blockIdx.x * HP_WARPS + warp; v < n; v += (uint64_t)gridDim.x * HP_WARPS) {
-        uint32_t cur = cnt[v];
+    // start[] is the scatter's advanced cursor: v's run is [start[v - 1], start[v]); a node's
+    // count and run bounds are requested one node ahead
+    const uint64_t stride = (uint64_t)gridDim.x * HP_WARPS;
+    uint64_t v = (uint64_t)blockIdx.x * HP_WARPS + warp;
+    uint32_t n_cur = 0;
+    uint64_t n_a = 0, n_b = 0;
+    if (v < n) {
+        n_cur = cnt[v];
+        n_a = v ? start[v - 1] : 0ull;
+        n_b = start[v];
+    }
+    for (; v < n; v += stride) {
+        uint32_t cur = n_cur;
         if (cur > l_max) cur = l_max;
-        // start[] is the scatter's advanced cursor: v's run is [start[v - 1], start[v])
-        uint64_t a = v ? start[v - 1] : 0ull;
-        const uint64_t b = start[v];
+        uint64_t a = n_a;
+        const uint64_t b = n_b;
+        if (v + stride < n) {
+            n_cur = cnt[v + stride];
+            n_a = start[v + stride - 1];
+            n_b = start[v + stride];
+        }
         if (a == b) {
             // no new candidates: the reservoir is unchanged (normalise the padding)
             for (uint32_t t = cur + lane; t < l_max; t += 32) res[v * l_max + t] = ~0ull;
@@ -213,10 +282,21 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
         const uint64_t total = (uint64_t)cur + (b - a);
         uint32_t u = 0;
         bool fast = true;
-        for (uint64_t base = 0; base < total; base += 32) {
+        for (uint64_t base0 = 0; base0 < total && fast; base0 += 128) {
+            // up to 128 slots requested at once, then inserted 32 at a time
+            uint64_t kq[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint64_t t = base0 + 32 * q + lane;
+                kq[q] = t < total ? (t < cur ? res[v * l_max + t] : slots[a + (t - cur)]) : ~0ull;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+            const uint64_t base = base0 + 32 * q;
+            if (base >= total) break;
             const uint64_t t = base + lane;
             const bool valid = t < total;
-            const uint64_t key = valid ? (t < cur ? res[v * l_max + t] : slots[a + (t - cur)]) : ~0ull;
+            const uint64_t key = kq[q];
             bool fresh = false;
             if (valid) {
                 uint32_t h = (uint32_t)(((key ^ (key >> 31)) * 0x9E3779B97F4A7C15ull) >> 56);
@@ -237,6 +317,7 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
             if (u > HP_DISTINCT) {  // uniform: the table then holds at most HP_DISTINCT + 32 < HP_HT
                 fast = false;
                 break;
+            }
             }
         }
         for (uint32_t w = lane; w < HP_HT; w += 32) ht[w] = ~0ull;
@@ -366,7 +447,7 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
     PIPNN_TRY(read_u64(tot, &E));
     PIPNN_TRY(ws.alloc(&slots, E));
     if (count) {
-        hp_scatter<<<grid_for((count + 1) / 2, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m,
+        hp_scatter<<<grid_for((count + 3) / 4, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m,
                                                                           reinterpret_cast<unsigned long long *>(start),
                                                                           slots);
         PIPNN_LAUNCH_CHECK();
@@ -480,7 +561,7 @@ int hashprune_noalloc_impl(const uint32_t *dst, const uint32_t *src, const float
     PIPNN_TRY(exclusive_scan_u64_scratch(start, start, n, total, scan));
     PIPNN_CUDA(cudaMemcpyAsync(start + n, total, 8, cudaMemcpyDeviceToDevice, stream()));
     if (count) {
-        hp_scatter<<<grid_for((count + 1) / 2, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m,
+        hp_scatter<<<grid_for((count + 3) / 4, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m,
                                                                           reinterpret_cast<unsigned long long *>(start),
                                                                           slots);
         PIPNN_LAUNCH_CHECK();

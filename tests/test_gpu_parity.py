@@ -134,6 +134,22 @@ def test_hashprune_parity_and_associativity(case):
     assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
 
 
+def test_hashprune_grouped_pick_stream_odd_sketch_width():
+    # the leaf pick's k = 2 stream, (v, c1), (c1, v), (v, c2), (c2, v) per member, with a sketch
+    # width that is not a multiple of four, a count that is not a multiple of four, and a prefix
+    # shifted by one so the groups straddle members
+    rng = np.random.default_rng(5)
+    X = synth.mixture(4000, 24, synth.U8, 20, 10.0, seed=36)
+    off_o, mem_o, _ = oracle.partition(X, oracle.params(**KW), seed=15)
+    dst, src, dist = oracle.leaf_pick(X, off_o, mem_o, k=2)
+    n, m = X.shape[0], 10
+    S = rng.standard_normal((n, m)).astype(np.float32)
+    for a, b in ((0, len(dst) - 3), (1, len(dst))):
+        res_o, cnt_o = oracle.hashprune_closed(dst[a:b], src[a:b], dist[a:b], S, n, 32)
+        res, cnt = pk.pipnn_hashprune(dev(dst[a:b]), dev(src[a:b]), dev(dist[a:b]), dev(S), n, 32)
+        assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
+
+
 def test_hashprune_hub_node_many_candidates():
     # one node receives far more candidates than a warp buffer holds
     rng = np.random.default_rng(4)
