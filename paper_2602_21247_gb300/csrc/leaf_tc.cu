@@ -43,7 +43,7 @@ struct TcUnit {
 
 struct TcArgs {
     const TcUnit *units;
-    const uint32_t *members;     // leaf members, ascending ids inside every leaf
+    const uint32_t *members;     // leaf members, ascending ids inside every 128-member tile
     const uint2 *member_pieces;  // -(n / 2) of every leaf member as four BF16 pieces
     uint32_t k;
     uint32_t *out_dst, *out_src;
@@ -340,8 +340,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         // ------------------------------------------------------------ epilogue, k <= 2
         // D_ij = -2 acc is an integer below 2^23 (d <= 128 bytes), so fma(-2, acc, 2^23) = D + 2^23
         // exactly and its bit pattern is 0x4B000000 + D: times 128 plus the column in the tile it is
-        // a 32-bit key ordered by (D, column), i.e. by (D, id) -- the leaf's members are in ascending
-        // id order.  Two smallest per chain: k2 = min(k2, max(k1, key)), k1 = min(k1, key).  Warp
+        // a 32-bit key ordered by (D, column), i.e. by (D, id) -- every 128-member tile of a leaf is
+        // in ascending id order.  Two smallest per chain: k2 = min(k2, max(k1, key)), k1 = min(k1, key).  Warp
         // (quarter, half) takes chunks half and half + 2 of every tile; one chunk's TMEM load is
         // always in flight while the other is ranked, across tiles and units.
         const int ew = warp - EPI_WARP0;
@@ -617,45 +617,6 @@ __global__ void build_units(const uint32_t *tile_grp, const uint32_t *tile_row0,
     }
 }
 
-// Sorts every leaf's members ascending, one block per leaf in shared memory (leaves of up to
-// TC_MAX_LEAF members; the host rejects larger ones).
-constexpr uint32_t TC_MAX_LEAF = 4096;
-
-// Leaves of up to WS_MAX members are sorted by one warp each in registers (sort_leaf_members_warp);
-// the block-wide sort takes the larger ones.
-constexpr uint32_t WS_MAX = 1024;
-
-__global__ void __launch_bounds__(1024) sort_leaf_members(const uint64_t *off, uint64_t L, uint32_t *mem) {
-    __shared__ uint32_t sh[TC_MAX_LEAF];
-    for (uint64_t b = blockIdx.x; b < L; b += gridDim.x) {
-        const uint64_t o = off[b];
-        const uint32_t n = (uint32_t)(off[b + 1] - o);
-        if (n <= WS_MAX || n > TC_MAX_LEAF) continue;
-        uint32_t P = 1;
-        while (P < n) P <<= 1;
-        for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) sh[i] = i < n ? mem[o + i] : 0xFFFFFFFFu;
-        __syncthreads();
-        for (uint32_t k = 2; k <= P; k <<= 1) {
-            for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
-                for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                    const uint32_t ixj = i ^ jj;
-                    if (ixj > i) {
-                        const uint32_t x = sh[i], y = sh[ixj];
-                        const bool asc = (i & k) == 0;
-                        if ((x > y) == asc) {
-                            sh[i] = y;
-                            sh[ixj] = x;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) mem[o + i] = sh[i];
-        __syncthreads();
-    }
-}
-
 // Ascending bitonic sort of 32 * E keys held E per lane (element E * lane + q in K[q]): exchanges
 // within a lane for distances below E, shuffles across lanes for the rest.
 template <int E>
@@ -688,48 +649,33 @@ __device__ __forceinline__ void warp_sort_u32(uint32_t (&K)[E], int lane) {
     }
 }
 
-// One leaf of 2..32E members by one warp: coalesced loads into a skewed shared buffer, E
-// consecutive elements per lane, register sort, and back.
-template <int E>
-__device__ __forceinline__ void warp_sort_leaf(uint32_t *mem, uint64_t o, uint32_t n, uint32_t *buf, int lane) {
-    constexpr uint32_t P = 32u * E;
-    auto at = [](uint32_t i) { return i + (i >> 5); };  // skew: lane l's run starts in bank l
-    for (uint32_t i = lane; i < P; i += 32) buf[at(i)] = i < n ? mem[o + i] : 0xFFFFFFFFu;
-    __syncwarp();
-    uint32_t K[E];
+// Sorts the members of every 128-member tile of every leaf ascending, one warp per tile in
+// registers.  Column order inside a B tile is then id order, which is all the packed (D, column)
+// keys of the k <= 2 epilogue need to break ties by id; across tiles (and halves) the epilogue
+// compares (D, id) itself, and the general-k epilogue compares (D, id) throughout.
+__global__ void __launch_bounds__(256) sort_tile_members(const uint32_t *tile_grp, const uint32_t *tile_row0,
+                                                         uint64_t ntiles, const uint64_t *off, uint32_t *mem) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t t = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles; t += nw) {
+        const uint32_t g = tile_grp[t], row0 = tile_row0[t];
+        const uint64_t o = off[g] + row0;
+        const uint64_t rest = off[g + 1] - o;
+        const uint32_t nn = rest < (uint64_t)ROWS ? (uint32_t)rest : (uint32_t)ROWS;
+        if (nn < 2) continue;
+        uint32_t K[4];
 #pragma unroll
-    for (int q = 0; q < E; q++) K[q] = buf[at(E * lane + q)];
-    __syncwarp();
-    warp_sort_u32<E>(K, lane);
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = 4 * lane + q;
+            K[q] = i < nn ? mem[o + i] : 0xFFFFFFFFu;
+        }
+        warp_sort_u32<4>(K, lane);
 #pragma unroll
-    for (int q = 0; q < E; q++) buf[at(E * lane + q)] = K[q];
-    __syncwarp();
-    for (uint32_t i = lane; i < n; i += 32) mem[o + i] = buf[at(i)];
-    __syncwarp();
-}
-
-__global__ void __launch_bounds__(256, 2) sort_leaf_members_warp(const uint64_t *off, uint64_t L, uint32_t *mem) {
-    __shared__ uint32_t sbuf[8][WS_MAX + WS_MAX / 32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *buf = sbuf[warp];
-    for (uint64_t b = blockIdx.x * 8ull + warp; b < L; b += gridDim.x * 8ull) {
-        const uint64_t o = off[b];
-        const uint32_t n = (uint32_t)(off[b + 1] - o);
-        if (n < 2 || n > WS_MAX) continue;
-        if (n <= 32) warp_sort_leaf<1>(mem, o, n, buf, lane);
-        else if (n <= 64) warp_sort_leaf<2>(mem, o, n, buf, lane);
-        else if (n <= 128) warp_sort_leaf<4>(mem, o, n, buf, lane);
-        else if (n <= 256) warp_sort_leaf<8>(mem, o, n, buf, lane);
-        else if (n <= 512) warp_sort_leaf<16>(mem, o, n, buf, lane);
-        else warp_sort_leaf<32>(mem, o, n, buf, lane);
+        for (int q = 0; q < 4; q++) {
+            const uint32_t i = 4 * lane + q;
+            if (i < nn) mem[o + i] = K[q];
+        }
     }
-}
-
-__global__ void max_leaf_size(const uint32_t *size, uint64_t L, unsigned *out) {
-    unsigned m = 0;
-    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < L; b += (uint64_t)gridDim.x * blockDim.x)
-        m = size[b] > m ? size[b] : m;
-    atomicMax(out, m);
 }
 
 __global__ void member_pieces(const uint32_t *members, uint64_t M, const int32_t *sqnorm, uint2 *pieces) {
@@ -777,42 +723,29 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
     const uint32_t kp = kb * 64;
     uint64_t M = 0;
     PIPNN_TRY(read_u64(off + L, &M));
-    if (L) {
-        unsigned *mx = nullptr, hmx = 0;
-        PIPNN_TRY(ws.zeros(&mx, 1));
-        max_leaf_size<<<grid_for(L, 256, 1024), 256, 0, stream()>>>(leaf_size, L, mx);
-        PIPNN_LAUNCH_CHECK();
-        PIPNN_CUDA(cudaMemcpyAsync(&hmx, mx, 4, cudaMemcpyDeviceToHost, stream()));
-        PIPNN_CUDA(cudaStreamSynchronize(stream()));
-        if (hmx > TC_MAX_LEAF)
-            return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes leaves of at most %u members",
-                             TC_MAX_LEAF);
-    }
-    // a copy of the members with every leaf in ascending id order: column order is then id order,
-    // which is the tie order of (D, id)
-    uint32_t *smem_members = nullptr;
-    PIPNN_TRY(ws.alloc(&smem_members, M));
+    if (M >= 0x7FFFFF00ull) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes < 2^31 leaf members");
+    uint32_t *tile_grp = nullptr, *tile_row0 = nullptr;
+    uint64_t ntiles = 0;
+    PIPNN_TRY(make_tiles(leaf_size, L, ROWS, &tile_grp, &tile_row0, &ntiles, ws));
+    // a copy of the members with every 128-member tile of a leaf in ascending id order
+    uint32_t *tile_members = nullptr;
+    PIPNN_TRY(ws.alloc(&tile_members, M));
     uint2 *mpieces = nullptr;
     PIPNN_TRY(ws.alloc(&mpieces, M));
     if (M) {
-        PIPNN_CUDA(cudaMemcpyAsync(smem_members, mem, M * 4, cudaMemcpyDeviceToDevice, stream()));
-        sort_leaf_members_warp<<<grid_for(L, 8, 152u * 32u), 256, 0, stream()>>>(off, L, smem_members);
+        PIPNN_CUDA(cudaMemcpyAsync(tile_members, mem, M * 4, cudaMemcpyDeviceToDevice, stream()));
+        sort_tile_members<<<grid_for(ntiles, 8, 152u * 32u), 256, 0, stream()>>>(tile_grp, tile_row0, ntiles, off,
+                                                                                 tile_members);
         PIPNN_LAUNCH_CHECK();
-        sort_leaf_members<<<grid_for(L, 1, 152u * 16u), 1024, 0, stream()>>>(off, L, smem_members);
-        PIPNN_LAUNCH_CHECK();
-        mem = smem_members;
+        mem = tile_members;
         member_pieces<<<grid_for(M, 256), 256, 0, stream()>>>(mem, M, sqnorm, mpieces);
         PIPNN_LAUNCH_CHECK();
     }
-    if (M >= 0x7FFFFF00ull) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes < 2^31 leaf members");
     __nv_bfloat16 *staged = nullptr;
     PIPNN_TRY(ws.alloc(&staged, (M ? M : 1) * kp));
     if (M) {
         PIPNN_TRY(stage_rows_bf16(X, d, kp, dtype, mem, M, staged));
     }
-    uint32_t *tile_grp = nullptr, *tile_row0 = nullptr;
-    uint64_t ntiles = 0;
-    PIPNN_TRY(make_tiles(leaf_size, L, ROWS, &tile_grp, &tile_row0, &ntiles, ws));
     TcUnit *units = nullptr;
     PIPNN_TRY(ws.alloc(&units, ntiles));
     if (ntiles) {

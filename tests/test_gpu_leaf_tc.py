@@ -94,6 +94,16 @@ def test_tc_pick_extreme_values_exact(kind):
     check(X, off, mem, 2)
 
 
+@pytest.mark.parametrize("k", [2, 3])
+def test_tc_pick_ties_across_tiles_of_a_large_leaf(k):
+    # values in 0..2: most distances tie, so the id order inside every 128-member tile and the
+    # (D, id) merge across 36 tiles both decide picks; the leaf is larger than any the partition makes
+    n = 6000
+    X = synth.uniform_points(n, 128, synth.U8, lo=0, hi=3, seed=60)
+    off, mem = random_leaves(n, [4500, 257, 31], seed=11)
+    check(X, off, mem, k)
+
+
 @pytest.mark.parametrize("d,dtype", [(8, synth.U8), (64, synth.I8), (100, synth.I8), (100, synth.U8),
                                      (127, synth.U8), (128, synth.I8)])
 def test_tc_pick_dimensions(d, dtype):
