@@ -192,42 +192,110 @@ __global__ void classify_buckets(uint64_t OB, const uint8_t *ob_kind, const uint
     }
 }
 
+// Instances per block and hash-table entries (at most half full) of the block-aggregated scatter.
 template <int FMAX>
-__global__ void scatter_instances(uint64_t N, uint32_t F, const uint32_t *inst, const uint32_t *inst_seg,
-                                  const uint64_t *lead_off, const uint32_t *lead_cnt, const uint16_t *assign,
-                                  const uint32_t *rank_ob, const uint8_t *ob_kind, const uint32_t *ob_raw,
-                                  const uint64_t *leaf_pos, const uint64_t *next_pos, const uint64_t *rec_idx,
-                                  uint32_t *ob_fill, uint32_t *leafmem, uint32_t *next_inst, uint32_t *next_seg,
-                                  unsigned *err) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t s = inst_seg[i];
-        const uint32_t f = F < lead_cnt[s] ? F : lead_cnt[s];
-        const uint32_t pt = inst[i];
-        // the instance's groups so far, in registers (FMAX >= f; fully unrolled indexing)
-        uint32_t seen[FMAX];
+struct ScatterCfg {
+    static constexpr uint32_t IB = FMAX <= 16 ? 256 : 128;
+    static constexpr uint32_t HT = FMAX <= 2 ? 1024 : FMAX <= 4 ? 2048 : FMAX <= 8 ? 4096 : 8192;
+    static constexpr uint32_t SMEM = HT * 12;  // key, count, base
+    static_assert(HT >= 2 * IB * FMAX, "load factor");
+};
+
+// Every instance joins the output buckets of its (distinct) picks.  A block first ranks its picks
+// per bucket in a shared-memory hash table, then reserves each bucket's run with one global
+// atomic and writes; the order inside a bucket is arbitrary (as with one atomic per pick).
+template <int FMAX>
+__global__ void __launch_bounds__(256) scatter_instances(
+    uint64_t N, uint32_t F, const uint32_t *inst, const uint32_t *inst_seg, const uint64_t *lead_off,
+    const uint32_t *lead_cnt, const uint16_t *assign, const uint32_t *rank_ob, const uint8_t *ob_kind,
+    const uint32_t *ob_raw, const uint64_t *leaf_pos, const uint64_t *next_pos, const uint64_t *rec_idx,
+    uint32_t *ob_fill, uint32_t *leafmem, uint32_t *next_inst, uint32_t *next_seg, unsigned *err) {
+    using C = ScatterCfg<FMAX>;
+    extern __shared__ uint32_t sc_smem[];
+    uint32_t *key = sc_smem, *cnt = sc_smem + C::HT, *base = sc_smem + 2 * C::HT;
+    for (uint32_t e = threadIdx.x; e < C::HT; e += blockDim.x) {
+        key[e] = OB_NONE;
+        cnt[e] = 0;
+    }
+    __syncthreads();
+    for (uint64_t i0 = (uint64_t)blockIdx.x * C::IB; i0 < N; i0 += (uint64_t)gridDim.x * C::IB) {
+        const uint64_t i = i0 + threadIdx.x;
+        const bool live = threadIdx.x < C::IB && i < N;
+        uint32_t f = 0, pt = 0, s = 0;
+        if (live) {
+            s = inst_seg[i];
+            f = F < lead_cnt[s] ? F : lead_cnt[s];
+            pt = inst[i];
+        }
+        // the instance's buckets (duplicates and OB_NONE dropped), their table slots and ranks
+        uint32_t ob[FMAX], sl[FMAX], lr[FMAX];
 #pragma unroll
         for (int j = 0; j < FMAX; j++) {
-            if ((uint32_t)j >= f) break;
-            const uint32_t ob = rank_ob[lead_off[s] + assign[i * F + j]];
+            ob[j] = OB_NONE;
+            if ((uint32_t)j >= f) continue;
+            const uint32_t o = rank_ob[lead_off[s] + assign[i * F + j]];
             bool dup = false;
 #pragma unroll
-            for (int q = 0; q < j; q++) dup = dup || seen[q] == ob;
-            seen[j] = ob;
-            if (dup || ob == OB_NONE) continue;
-            const uint32_t pos = atomicAdd(&ob_fill[ob], 1u);
-            if (pos >= ob_raw[ob]) {
+            for (int q = 0; q < j; q++) dup = dup || ob[q] == o;
+            if (dup || o == OB_NONE) continue;
+            ob[j] = o;
+            uint32_t h = (o * 0x9E3779B1u) & (C::HT - 1);
+            for (;;) {
+                const uint32_t old = atomicCAS(&key[h], OB_NONE, o);
+                if (old == OB_NONE || old == o) break;
+                h = (h + 1) & (C::HT - 1);
+            }
+            sl[j] = h;
+            lr[j] = atomicAdd(&cnt[h], 1u);
+        }
+        __syncthreads();
+        // one reservation per bucket touched by the block
+        for (uint32_t e = threadIdx.x; e < C::HT; e += blockDim.x)
+            if (key[e] != OB_NONE) base[e] = atomicAdd(&ob_fill[key[e]], cnt[e]);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < FMAX; j++) {
+            if (ob[j] == OB_NONE) continue;
+            const uint32_t o = ob[j];
+            const uint32_t pos = base[sl[j]] + lr[j];
+            if (pos >= ob_raw[o]) {
                 atomicOr(err, DERR_CAPACITY);
                 continue;
             }
-            if (ob_kind[ob] == OB_RECURSE) {
-                const uint64_t q = next_pos[ob] + pos;
+            if (ob_kind[o] == OB_RECURSE) {
+                const uint64_t q = next_pos[o] + pos;
                 next_inst[q] = pt;
-                next_seg[q] = (uint32_t)rec_idx[ob];
+                next_seg[q] = (uint32_t)rec_idx[o];
             } else {
-                leafmem[leaf_pos[ob] + pos] = pt;
+                leafmem[leaf_pos[o] + pos] = pt;
             }
         }
+        __syncthreads();
+        // empty the slots this thread filled (several threads may clear one slot: same values)
+#pragma unroll
+        for (int j = 0; j < FMAX; j++) {
+            if (ob[j] == OB_NONE) continue;
+            key[sl[j]] = OB_NONE;
+            cnt[sl[j]] = 0;
+        }
+        __syncthreads();
     }
+}
+
+template <int FMAX>
+int launch_scatter(uint64_t N, uint32_t F, const uint32_t *inst, const uint32_t *inst_seg, const uint64_t *lead_off,
+                   const uint32_t *lead_cnt, const uint16_t *assign, const uint32_t *rank_ob, const uint8_t *ob_kind,
+                   const uint32_t *ob_raw, const uint64_t *leaf_pos, const uint64_t *next_pos,
+                   const uint64_t *rec_idx, uint32_t *ob_fill, uint32_t *leafmem, uint32_t *next_inst,
+                   uint32_t *next_seg, unsigned *err) {
+    using C = ScatterCfg<FMAX>;
+    auto kern = scatter_instances<FMAX>;
+    PIPNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    kern<<<grid_for(N, C::IB, 152u * 8u), 256, C::SMEM, stream()>>>(N, F, inst, inst_seg, lead_off, lead_cnt, assign,
+                                                                  rank_ob, ob_kind, ob_raw, leaf_pos, next_pos,
+                                                                  rec_idx, ob_fill, leafmem, next_inst, next_seg, err);
+    PIPNN_LAUNCH_CHECK();
+    return PIPNN_OK;
 }
 
 __global__ void emit_descriptors(uint64_t OB, const uint8_t *ob_kind, const uint32_t *ob_fill, const uint64_t *ob_child,
@@ -509,18 +577,15 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         PIPNN_TRY(tw.alloc(&guard_size, n_guard));
         // guards add at least two runs each; the exact count is known after the scatter
         {
-            const unsigned sg = grid_for(N, 256);
 #define PIPNN_SCATTER(FM)                                                                                         \
-    scatter_instances<FM><<<sg, 256, 0, stream()>>>(N, F, cur->inst, cur->inst_seg, lead_off, lead_cnt, assign,   \
-                                                    rank_ob, ob_kind, ob_raw, leafsz, nextsz, is_rec, ob_fill,      \
-                                                    lv.mem, next->inst, next->inst_seg, err)
+    PIPNN_TRY(launch_scatter<FM>(N, F, cur->inst, cur->inst_seg, lead_off, lead_cnt, assign, rank_ob, ob_kind,     \
+                                 ob_raw, leafsz, nextsz, is_rec, ob_fill, lv.mem, next->inst, next->inst_seg, err))
             if (F <= 2) PIPNN_SCATTER(2);
             else if (F <= 4) PIPNN_SCATTER(4);
             else if (F <= 8) PIPNN_SCATTER(8);
             else if (F <= 16) PIPNN_SCATTER(16);
             else PIPNN_SCATTER(32);
 #undef PIPNN_SCATTER
-            PIPNN_LAUNCH_CHECK();
         }
         uint64_t *lstart_tmp;
         uint32_t *lsize_tmp;
