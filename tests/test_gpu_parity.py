@@ -64,6 +64,21 @@ def case(request):
 
 
 # ---------------------------------------------------------------- A0
+@pytest.mark.parametrize("d,dtype,m", [(37, synth.U8, 12), (30, synth.I8, 16), (45, synth.F32, 5),
+                                       (128, synth.U8, 16), (8, synth.I8, 1), (4, synth.F32, 12)])
+def test_sketch_parity_widths(d, dtype, m):
+    # four coordinates per step (d % 4 == 0) and one at a time (otherwise): both bit-exact
+    X = synth.mixture(3000, d, dtype, 10, 10.0 if dtype != synth.F32 else 0.3, seed=37 + d)
+    H = synth.hyperplanes(m, d, seed=9)
+    S, nrm = pk.pipnn_sketch(dev(X), dev(H))
+    S_o, nrm_o = oracle.sketch(X, H)
+    assert np.array_equal(host(S).view(np.uint32), S_o.view(np.uint32))
+    if X.dtype == np.float32:
+        assert np.all(np.abs(host(nrm).astype(np.float64) - nrm_o) <= (d + 1) * U * nrm_o)
+    else:
+        assert np.array_equal(host(nrm).astype(np.float64), nrm_o)
+
+
 def test_sketch_parity(case):
     name, X, metric, H = case
     S, nrm = pk.pipnn_sketch(dev(X), dev(H))
