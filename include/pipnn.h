@@ -82,6 +82,11 @@ typedef struct pipnn_params {
     int32_t leaf_engine;    /* PIPNN_LEAF_SIMT / PIPNN_LEAF_TC                                  */
     const float *hyperplanes; /* Sec. 3: the m x d random hyperplanes H (row i = H_i), float32,
                                  host or device; required                                      */
+    uint32_t replicas;      /* Sec. 4.1 replication (Sec. 5 "extra replicate"): independent RBC
+                               copies whose candidates feed the same HashPrune reservoirs
+                               (1..16; 0 means 1).  Replica r partitions with the seed
+                               seed + r * 0x9E3779B97F4A7C15 (mod 2^64), so replica 0 is the
+                               single-replica build.                                          */
 } pipnn_params;
 
 /* Output graph: ids[v*R + j] for j < deg[v] are v's out-neighbours in prune order; the rest of

@@ -11,6 +11,7 @@ Every function returns numpy arrays and follows the paper's definitions:
   hashprune_closed .. the closed form of the history-independence lemma (App. A.6)
   final_prune ....... Alg. 2 RobustPrune (standard or lazy) to degree R
   build ............. Alg. 4 end to end
+  build_replicated .. Alg. 4 with Sec. 4.1 replication (independent RBC copies, one HashPrune)
   knn / beam_search / recall .. Def. 1, Alg. 1 and Def. 2 for evaluating graphs
 """
 from __future__ import annotations
@@ -253,6 +254,38 @@ def build(X, bp: Params, H, seed, metric=L2):
                            _p(deg), C.byref(st)), "build")
     return adj, deg, dict(leaves=st.leaves, leaf_members=st.leaf_members, levels=st.levels,
                           candidates=st.candidates)
+
+
+REPLICA_SEED_STEP = 0x9E3779B97F4A7C15
+
+
+def replica_seed(seed, r):
+    """Seed of replica r: seed + r * 0x9E3779B97F4A7C15 (mod 2^64); replica 0 keeps the build seed."""
+    return (int(seed) + int(r) * REPLICA_SEED_STEP) % (1 << 64)
+
+
+def build_replicated(X, bp: Params, H, seed, replicas, metric=L2):
+    """Alg. 4 with Sec. 4.1 replication: `replicas` independent runs of Alg. 5 (replica r with
+    replica_seed(seed, r)), every replica's bi-directed candidates into one HashPrune (Alg. 3 in
+    its closed form over the union, which the history-independence lemma makes equal to streaming
+    the replicas one after another), then Alg. 2 as in build().  Returns (adjacency, degrees)."""
+    X = np.ascontiguousarray(X)
+    n = X.shape[0]
+    S, _ = sketch(X, H)
+    parts = []
+    for r in range(replicas):
+        off, mem, _ = partition(X, bp, replica_seed(seed, r), metric)
+        parts.append(leaf_pick(X, off, mem, k=bp.leaf_k, metric=metric))
+    dst, src, dist = (np.concatenate([p[i] for p in parts]) for i in range(3))
+    res, cnt = hashprune_closed(dst, src, dist, S, n, bp.l_max)
+    if bp.final_prune:
+        return final_prune(X, res, cnt, bp.R, bp.alpha, metric)
+    # without the final prune: the first R reservoir entries in (distance, id) order
+    R = bp.R
+    c = np.minimum(cnt, R).astype(np.uint32)
+    ids = ((res[:, :R] >> np.uint64(16)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    ids[np.arange(R)[None, :] >= c[:, None]] = 0xFFFFFFFF
+    return ids, c
 
 
 def knn(X, Q, k=10, metric=L2):

@@ -45,7 +45,8 @@ class pipnn_params(C.Structure):
                 ("p_samp", C.c_float), ("fanout", C.c_uint32 * 4), ("fanout_levels", C.c_uint32),
                 ("leaf_k", C.c_uint32), ("hash_bits", C.c_uint32), ("l_max", C.c_uint32),
                 ("R", C.c_uint32), ("alpha", C.c_float), ("final_prune", C.c_int32),
-                ("dtype", C.c_int32), ("leaf_engine", C.c_int32), ("hyperplanes", C.c_void_p)]
+                ("dtype", C.c_int32), ("leaf_engine", C.c_int32), ("hyperplanes", C.c_void_p),
+                ("replicas", C.c_uint32)]
 
 
 class pipnn_graph(C.Structure):
@@ -146,7 +147,7 @@ def _take(ptr, count, typestr, view=None):
 
 def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.005, fanout=(2,), leaf_k=2,
            hash_bits=12, l_max=64, R=64, alpha=1.2, final_prune=True, leaf_engine=PIPNN_LEAF_SIMT,
-           hyperplanes=None) -> pipnn_params:
+           hyperplanes=None, replicas=1) -> pipnn_params:
     """BP of Alg. 4.  `hyperplanes` (hash_bits x d float32, numpy or torch) must stay alive for the call."""
     p = pipnn_params()
     p.c_max = c_max
@@ -165,6 +166,7 @@ def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.0
     p.dtype = dtype
     p.leaf_engine = leaf_engine
     p.hyperplanes = _ptr(hyperplanes)
+    p.replicas = replicas
     p._keep = hyperplanes
     return p
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 namespace pipnn {
 void set_stream(cudaStream_t s);
@@ -84,6 +85,7 @@ int check_params(const pipnn_params *bp) {
     if (bp->leaf_engine != PIPNN_LEAF_SIMT && bp->leaf_engine != PIPNN_LEAF_TC)
         return set_error(PIPNN_EINVAL, "unknown leaf_engine %d", bp->leaf_engine);
     if (!bp->hyperplanes) return set_error(PIPNN_EINVAL, "hyperplanes is NULL");
+    if (bp->replicas > 16) return set_error(PIPNN_EINVAL, "replicas above 16");
     return PIPNN_OK;
 }
 
@@ -177,48 +179,65 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     tm.mark(1);
     const int32_t *sqn_bytes = dtype == PIPNN_F32 ? nullptr : sqn;
 
-    // A1
-    pipnn_leaves leaves;
-    PIPNN_TRY(partition_points(X, n, d, dtype, metric, sqn_bytes, bp, seed, &leaves));
-    tm.mark(2);
-    st.levels = leaves.levels;
-    st.leaves = leaves.num_leaves;
-    st.leaf_members = leaves.num_members;
-    {
-        double *acc;
-        PIPNN_TRY(ws.zeros(&acc, 1));
+    // A1 .. A5 once per replica (Sec. 4.1 replication): an independent RBC with its own seed whose
+    // candidates join the same reservoirs; HashPrune's result does not depend on the order in
+    // which candidates arrive (Alg. 3, history independence), so the replicas simply run in turn
+    const uint32_t replicas = bp->replicas ? bp->replicas : 1;
+    std::vector<Timer> rt(replicas);
+    for (auto &t : rt) PIPNN_TRY(t.init());
+    double *acc;
+    PIPNN_TRY(ws.zeros(&acc, 1));
+    uint64_t *res = nullptr;
+    uint32_t *cnt = nullptr;
+    for (uint32_t r = 0; r < replicas; r++) {
+        const uint64_t seed_r = seed + (uint64_t)r * 0x9E3779B97F4A7C15ull;
+        rt[r].mark(0);
+        // A1
+        pipnn_leaves leaves;
+        PIPNN_TRY(partition_points(X, n, d, dtype, metric, sqn_bytes, bp, seed_r, &leaves));
+        rt[r].mark(1);
+        st.levels = leaves.levels > st.levels ? leaves.levels : st.levels;
+        st.leaves += leaves.num_leaves;
+        st.leaf_members += leaves.num_members;
         if (leaves.num_leaves) {
             leaf_pairs_kernel<<<grid_for(leaves.num_leaves, 256, 1024), 256, 0, stream()>>>(leaves.offsets,
                                                                                            leaves.num_leaves, acc);
         }
-        PIPNN_CUDA(cudaMemcpyAsync(&st.leaf_pairs, acc, 8, cudaMemcpyDeviceToHost, stream()));
-    }
 
-    // A2 .. A4
-    pipnn_edges edges;
-    int rc = leaf_pick(X, n, d, dtype, metric, sqn_bytes, leaves.offsets, leaves.members, leaves.num_leaves,
-                       bp->leaf_k, bp->leaf_engine, &edges, &st.ms_leaf_kernel, &st.leaf_kernel_launches);
-    dev_free_raw(leaves.offsets);
-    dev_free_raw(leaves.members);
-    if (rc != PIPNN_OK) return rc;
-    tm.mark(3);
-    st.candidates = edges.count;
+        // A2 .. A4
+        pipnn_edges edges;
+        float leaf_ms = 0.0f;
+        uint32_t leaf_launches = 0;
+        int rc = leaf_pick(X, n, d, dtype, metric, sqn_bytes, leaves.offsets, leaves.members, leaves.num_leaves,
+                           bp->leaf_k, bp->leaf_engine, &edges, &leaf_ms, &leaf_launches);
+        dev_free_raw(leaves.offsets);
+        dev_free_raw(leaves.members);
+        if (rc != PIPNN_OK) return rc;
+        rt[r].mark(2);
+        st.ms_leaf_kernel += leaf_ms;
+        st.leaf_kernel_launches += leaf_launches;
+        st.candidates += edges.count;
 
-    // A5
-    uint64_t *res;
-    uint32_t *cnt;
-    rc = ws.alloc(&res, n * bp->l_max);
-    if (rc == PIPNN_OK) rc = ws.zeros(&cnt, n);
-    if (rc == PIPNN_OK) {
-        cudaError_t e = cudaMemsetAsync(res, 0xFF, n * bp->l_max * 8, stream());
-        if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "memset: %s", cudaGetErrorString(e));
+        // A5
+        if (r == 0) {
+            rc = ws.alloc(&res, n * bp->l_max);
+            if (rc == PIPNN_OK) rc = ws.zeros(&cnt, n);
+            if (rc == PIPNN_OK) {
+                cudaError_t e = cudaMemsetAsync(res, 0xFF, n * bp->l_max * 8, stream());
+                if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "memset: %s", cudaGetErrorString(e));
+            }
+        }
+        if (rc == PIPNN_OK)
+            rc = hashprune_merge(edges.dst, edges.src, edges.dist, edges.count, S, m, n, bp->l_max, res, cnt);
+        dev_free_raw(edges.dst);
+        dev_free_raw(edges.src);
+        dev_free_raw(edges.dist);
+        if (rc != PIPNN_OK) return rc;
+        rt[r].mark(3);
     }
-    if (rc == PIPNN_OK) rc = hashprune_merge(edges.dst, edges.src, edges.dist, edges.count, S, m, n, bp->l_max, res, cnt);
-    dev_free_raw(edges.dst);
-    dev_free_raw(edges.src);
-    dev_free_raw(edges.dist);
-    if (rc != PIPNN_OK) return rc;
+    PIPNN_CUDA(cudaMemcpyAsync(&st.leaf_pairs, acc, 8, cudaMemcpyDeviceToHost, stream()));
     tm.mark(4);
+    int rc = PIPNN_OK;
 
     // A6
     uint32_t *adj = nullptr, *deg = nullptr;
@@ -278,9 +297,11 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     tm.mark(6);
     cudaStreamSynchronize(stream());
     st.ms_sketch = tm.ms(0, 1);
-    st.ms_partition = tm.ms(1, 2);
-    st.ms_leaf = tm.ms(2, 3);
-    st.ms_hashprune = tm.ms(3, 4);
+    for (auto &t : rt) {
+        st.ms_partition += t.ms(0, 1);
+        st.ms_leaf += t.ms(1, 2);
+        st.ms_hashprune += t.ms(2, 3);
+    }
     st.ms_prune = tm.ms(4, 5);
     st.ms_total = tm.ms(0, 6);
     st.kernel_launches = launch_count() - launches0;

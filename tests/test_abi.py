@@ -46,6 +46,8 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
 
 def test_params_struct_matches_header_layout():
     import paper_2602_21247_gb300 as pk
-    # 3 x u32, f32, 4 x u32, 6 x u32/f32, 3 x i32, pointer (8-byte aligned)
-    assert ctypes.sizeof(pk.pipnn_params) == 4 * (3 + 1 + 4 + 1 + 4 + 1 + 1 + 2) + 4 + 8
-    assert pk.pipnn_params.hyperplanes.offset % 8 == 0
+    # 3 x u32, f32, 4 x u32, 6 x u32/f32, 3 x i32, pointer (8-byte aligned), u32 replicas, tail
+    # padding to the pointer's alignment
+    assert pk.pipnn_params.hyperplanes.offset == 4 * (3 + 1 + 4 + 1 + 4 + 1 + 1 + 2) + 4 == 72
+    assert pk.pipnn_params.replicas.offset == 80
+    assert ctypes.sizeof(pk.pipnn_params) == 88

@@ -165,6 +165,22 @@ def test_hashprune_grouped_pick_stream_odd_sketch_width():
         assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
 
 
+@pytest.mark.parametrize("engine,dtype", [("tc", synth.U8), ("simt", synth.F32)])
+def test_build_replicas_parity(engine, dtype):
+    # Sec. 4.1 replication: three independent RBC runs feed one set of reservoirs
+    X = synth.mixture(5000, 24, dtype, 25, 10.0 if dtype != synth.F32 else 0.3, seed=26)
+    H = synth.hyperplanes(12, 24, seed=6)
+    kw = dict(c_max=256, l_max=48, R=24, fanout=(3,))
+    adj_o, deg_o = oracle.build_replicated(X, oracle.params(**kw), H, 42, 3)
+    code = {np.uint8: pk.PIPNN_U8, np.float32: pk.PIPNN_F32}[X.dtype.type]
+    eng = pk.PIPNN_LEAF_TC if engine == "tc" else pk.PIPNN_LEAF_SIMT
+    bp = pk.params(dtype=code, hyperplanes=H, leaf_engine=eng, replicas=3, **kw)
+    adj, deg = pk.pipnn_build(dev(X), bp, 42)
+    assert np.array_equal(host(deg), deg_o) and np.array_equal(host(adj), adj_o)
+    st = pk.pipnn_get_stats()
+    assert st["leaf_kernel_launches"] == 3
+
+
 def test_hashprune_hub_node_many_candidates():
     # one node receives far more candidates than a warp buffer holds
     rng = np.random.default_rng(4)

@@ -419,6 +419,43 @@ def test_build_graph_quality_and_structure():
     assert oracle.recall(ids2, gt) >= 0.9
 
 
+def test_replicated_build_pins():
+    # Sec. 4.1 replication.  One replica composes the stages exactly as Alg. 4 (orc_build); more
+    # replicas feed one HashPrune, whose closed form over the union must equal streaming the
+    # replicas' candidates one replica after another (history independence, Sec. 3), and every
+    # replica must be a different RBC run (its own seed).
+    X, Q = synth.mixture(5000, 24, synth.U8, 25, 10.0, seed=26, n_queries=150)
+    H = synth.hyperplanes(12, 24, seed=6)
+    bp = oracle.params(c_max=256, l_max=48, R=24, fanout=(3,))
+    adj1, deg1 = oracle.build_replicated(X, bp, H, 42, 1)
+    adj, deg, _ = oracle.build(X, bp, H, seed=42)
+    assert np.array_equal(adj1, adj) and np.array_equal(deg1, deg)
+    assert oracle.replica_seed(42, 0) == 42 and oracle.replica_seed(2**64 - 1, 1) == 0x9E3779B97F4A7C14
+    S, _ = oracle.sketch(X, H)
+    res, cnt = None, None
+    leafsets = []
+    for r in range(3):
+        off, mem, _ = oracle.partition(X, bp, oracle.replica_seed(42, r))
+        leafsets.append(sorted(tuple(sorted(mem[off[b]:off[b + 1]].tolist())) for b in range(len(off) - 1)))
+        dst, src, dist = oracle.leaf_pick(X, off, mem, k=bp.leaf_k)
+        res, cnt = oracle.hashprune_stream(dst, src, dist, S, X.shape[0], bp.l_max, res, cnt)
+    assert leafsets[0] != leafsets[1] and leafsets[1] != leafsets[2]
+    adj3, deg3 = oracle.build_replicated(X, bp, H, 42, 3)
+    adj_s, deg_s = oracle.final_prune(X, res, cnt, bp.R, bp.alpha)
+    assert np.array_equal(adj3, adj_s) and np.array_equal(deg3, deg_s)
+    # the extra replicates add candidates (Sec. 5: an extra replicate buys quality): with fanout 3
+    # alone one replica reaches recall@10 ~0.6 at L = 32 here, three ~0.94
+    gt = oracle.knn(X, Q, 10)
+    r1 = oracle.recall(oracle.beam_search(X, adj1, deg1, Q, 32)[0], gt)
+    r3 = oracle.recall(oracle.beam_search(X, adj3, deg3, Q, 32)[0], gt)
+    assert r3 > r1 + 0.1
+    # without the final prune: the nearest R reservoir entries, as orc_build keeps them
+    bp.final_prune = 0
+    a0, d0 = oracle.build_replicated(X, bp, H, 42, 1)
+    a1, d1, _ = oracle.build(X, bp, H, seed=42)
+    assert np.array_equal(a0, a1) and np.array_equal(d0, d1)
+
+
 def test_knn_and_beam_search_exact_on_complete_graph():
     X, Q = synth.mixture(300, 8, synth.F32, 5, 0.5, seed=24, n_queries=20)
     gt = oracle.knn(X, Q, 10)
