@@ -125,7 +125,9 @@ typedef struct pipnn_stats {
     uint32_t levels;
     uint64_t leaves, leaf_members, candidates;
     double leaf_pairs;           /* sum over leaves of |b| (|b| - 1), the unordered-pair work x2 */
-    double leaf_pairs_executed;  /* pairs the kernel evaluated (full tiles, both orders)        */
+    double leaf_pairs_executed;  /* sum over leaves of |b|^2: the full square the leaf kernels
+                                    evaluate (both orders and the diagonal; the tensor-core
+                                    kernel also evaluates the padding of ragged tiles)          */
     uint64_t kernel_launches;    /* kernels this library launched during the build              */
 } pipnn_stats;
 

@@ -303,6 +303,7 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
         st.ms_hashprune += t.ms(2, 3);
     }
     st.ms_prune = tm.ms(4, 5);
+    st.leaf_pairs_executed = st.leaf_pairs + (double)st.leaf_members;
     st.ms_total = tm.ms(0, 6);
     st.kernel_launches = launch_count() - launches0;
     g_stats = st;
