@@ -120,12 +120,6 @@ __global__ void __launch_bounds__(128) sketch_kernel_vec(const void *X, uint64_t
     }
 }
 
-template <int DT>
-__global__ void to_bf16_kernel(const void *X, uint64_t count, __nv_bfloat16 *out) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        out[i] = __float2bfloat16_rn(coordf<DT>(X, i));
-}
 }  // namespace
 
 int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float *H, uint32_t m, float *S,
@@ -138,24 +132,18 @@ int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float 
     const size_t xalign = dtype == PIPNN_F32 ? 16 : 4;
     if (m >= 1 && S && d % 4 == 0 && hbytes <= 48 * 1024 && reinterpret_cast<uintptr_t>(X) % xalign == 0 &&
         reinterpret_cast<uintptr_t>(H) % 16 == 0) {
-        if (dtype == PIPNN_F32) sketch_kernel_vec<PIPNN_F32><<<grid, 128, hbytes, stream()>>>(X, n, d, H, m, S, sqnorm, err);
-        else if (dtype == PIPNN_U8) sketch_kernel_vec<PIPNN_U8><<<grid, 128, hbytes, stream()>>>(X, n, d, H, m, S, sqnorm, err);
-        else sketch_kernel_vec<PIPNN_I8><<<grid, 128, hbytes, stream()>>>(X, n, d, H, m, S, sqnorm, err);
+        if (dtype == PIPNN_F32)
+            sketch_kernel_vec<PIPNN_F32><<<grid, 128, hbytes, stream()>>>(X, n, d, H, m, S, sqnorm, err);
+        else if (dtype == PIPNN_U8)
+            sketch_kernel_vec<PIPNN_U8><<<grid, 128, hbytes, stream()>>>(X, n, d, H, m, S, sqnorm, err);
+        else
+            sketch_kernel_vec<PIPNN_I8><<<grid, 128, hbytes, stream()>>>(X, n, d, H, m, S, sqnorm, err);
         PIPNN_LAUNCH_CHECK();
         return PIPNN_OK;
     }
     if (dtype == PIPNN_F32) sketch_kernel<PIPNN_F32><<<grid, 128, 0, stream()>>>(X, n, d, H, m, S, sqnorm, err);
     else if (dtype == PIPNN_U8) sketch_kernel<PIPNN_U8><<<grid, 128, 0, stream()>>>(X, n, d, H, m, S, sqnorm, err);
     else sketch_kernel<PIPNN_I8><<<grid, 128, 0, stream()>>>(X, n, d, H, m, S, sqnorm, err);
-    PIPNN_LAUNCH_CHECK();
-    return PIPNN_OK;
-}
-
-int points_to_bf16(const void *X, uint64_t count, int dtype, __nv_bfloat16 *out) {
-    unsigned grid = grid_for(count, 256);
-    if (dtype == PIPNN_F32) to_bf16_kernel<PIPNN_F32><<<grid, 256, 0, stream()>>>(X, count, out);
-    else if (dtype == PIPNN_U8) to_bf16_kernel<PIPNN_U8><<<grid, 256, 0, stream()>>>(X, count, out);
-    else to_bf16_kernel<PIPNN_I8><<<grid, 256, 0, stream()>>>(X, count, out);
     PIPNN_LAUNCH_CHECK();
     return PIPNN_OK;
 }
