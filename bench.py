@@ -114,6 +114,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_data_seed(w, rank):
+    """Every rank builds its own seeded instance of the workload (replicas only: no exchange)."""
+    return w["data_seed"] + 7919 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest of every rank's x: the whole job takes as long as its slowest rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank, world, seconds):
+    """Points built per second by the whole job (world ranks, n_per_rank points each)."""
+    return world * n_per_rank / seconds
+
+
 def cpu_baseline(X, H, w):
     import oracle  # the CPU oracle: timed here as a reported baseline only
 
@@ -190,7 +212,7 @@ def main():
             dist.barrier()
 
     n = args.n or w["n"]
-    X = synth.mixture(n, w["d"], w["dtype"], w["centers"], w["sigma"], w["data_seed"] + 7919 * rank)
+    X = synth.mixture(n, w["d"], w["dtype"], w["centers"], w["sigma"], rank_data_seed(w, rank))
     H = synth.hyperplanes(12, w["d"])
     Xd = torch.from_numpy(X).cuda()
     Hd = torch.from_numpy(H).cuda()
@@ -222,12 +244,8 @@ def main():
     barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = sum(step_ms) / len(step_ms)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * n / (ms / 1e3)
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, "cuda")
+    value = job_throughput(n, world, ms / 1e3)
 
     # dominant kernel: the leaf all-pairs Gram + pick
     leaf_ms = sum(s["ms_leaf_kernel"] for s in stats) / max(1, sum(s["leaf_kernel_launches"] for s in stats))
@@ -262,11 +280,8 @@ def main():
     for _ in range(e2e_steps):
         pk.pipnn_build_into(Xh, bp_h, synth.BUILD_SEED, adj_h, deg_h)
         int(deg_h[0])  # the result is read on the host
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e = {"value": world * n / float(te.item()), "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes + H.nbytes),
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
+    e2e = {"value": job_throughput(n, world, e2e_s), "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes + H.nbytes),
            "d2h_bytes_per_step": int(n * R * 4 + n * 4)}
 
     if rank == 0:
