@@ -212,6 +212,14 @@ int pipnn_build(const void *points, uint64_t n, uint32_t d, int32_t metric, cons
                 uint64_t seed, int32_t graph_on_host, pipnn_graph *out);
 void pipnn_free(pipnn_graph *graph);
 
+/* Alg. 4 for `count` independent indexes of one dimension d (independent point sets, each with
+ * its own seed: points[i] holds n[i] rows, host or device), built one after another on the
+ * library stream.  outs[i] receives index i's graph in device memory; free each with pipnn_free.
+ * On an error no graph is returned: the graphs already built are freed, every outs[i] is zeroed
+ * and the error of the failing index is reported.  pipnn_get_stats describes the last build. */
+int pipnn_build_batched(const void *const *points, const uint64_t *n, uint32_t count, uint32_t d, int32_t metric,
+                        const pipnn_params *bp, const uint64_t *seeds, pipnn_graph *outs);
+
 /* Alg. 4 end to end into caller-owned outputs: adj (n x R uint32) and deg (n uint32), host or
  * device pointers, written completely on success (rows padded with 0xFFFFFFFF).  points: host or
  * device.  Allocates only its device workspace. */

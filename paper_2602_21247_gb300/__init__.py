@@ -31,7 +31,7 @@ PIPNN_OK = 0
 # symbols declared in include/pipnn.h
 EXPORTS = ("pipnn_set_stream", "pipnn_last_error", "pipnn_sketch", "pipnn_partition", "pipnn_leaves_free",
            "pipnn_leaf_pick", "pipnn_edges_free", "pipnn_hashprune", "pipnn_final_prune", "pipnn_build",
-           "pipnn_free", "pipnn_build_into", "pipnn_get_stats", "pipnn_hashprune_noalloc")
+           "pipnn_free", "pipnn_build_into", "pipnn_get_stats", "pipnn_hashprune_noalloc", "pipnn_build_batched")
 
 
 class PipnnError(RuntimeError):
@@ -99,6 +99,8 @@ def lib():
         L.pipnn_free.argtypes = [C.POINTER(pipnn_graph)]
         L.pipnn_free.restype = None
         L.pipnn_build_into.argtypes = [vp, u64, u32, i32, C.POINTER(pipnn_params), u64, vp, vp]
+        L.pipnn_build_batched.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_uint64), u32, u32, i32,
+                                          C.POINTER(pipnn_params), C.POINTER(C.c_uint64), C.POINTER(pipnn_graph)]
         L.pipnn_get_stats.argtypes = [C.POINTER(pipnn_stats)]
         _lib = L
     return _lib
@@ -290,6 +292,36 @@ def pipnn_build_into(points, bp: pipnn_params, seed: int, adj, deg, metric=PIPNN
     pipnn_set_stream()
     _check(lib().pipnn_build_into(_ptr(points), n, d, metric, C.byref(bp), seed, _ptr(adj), _ptr(deg)))
     return adj, deg
+
+
+def pipnn_build_batched(points_list, bp: pipnn_params, seeds, metric=PIPNN_L2):
+    """Alg. 4 for several independent indexes of one dimension and dtype (torch tensors or numpy
+    arrays, host or device), seeds[i] for index i.  Returns a list of (adjacency n_i x R uint32,
+    degree n_i uint32) device tensors."""
+    count = len(points_list)
+    if count != len(seeds):
+        raise ValueError("one seed per index")
+    d = points_list[0].shape[1] if count else 0
+    if any(p.shape[1] != d or dtype_code(p) != dtype_code(points_list[0]) for p in points_list):
+        raise ValueError("every index needs the same dimension and dtype")
+    if count:
+        bp.dtype = dtype_code(points_list[0])
+    ptrs = (C.c_void_p * max(1, count))(*[_ptr(p) for p in points_list])
+    ns = (C.c_uint64 * max(1, count))(*[p.shape[0] for p in points_list])
+    sd = (C.c_uint64 * max(1, count))(*[int(s) for s in seeds])
+    outs = (pipnn_graph * max(1, count))()
+    pipnn_set_stream()
+    _check(lib().pipnn_build_batched(ptrs, ns, count, d, metric, C.byref(bp), sd, outs))
+    graphs = []
+    try:
+        for i, p in enumerate(points_list):
+            n, R = p.shape[0], outs[i].R
+            graphs.append((_take(outs[i].ids, n * R, "<i4", torch.uint32).view(n, R),
+                           _take(outs[i].deg, n, "<i4", torch.uint32)))
+    finally:
+        for i in range(count):
+            lib().pipnn_free(C.byref(outs[i]))
+    return graphs
 
 
 def pipnn_get_stats() -> dict:

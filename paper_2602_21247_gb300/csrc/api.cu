@@ -428,6 +428,20 @@ void pipnn_free(pipnn_graph *g) {
     memset(g, 0, sizeof(*g));
 }
 
+int pipnn_build_batched(const void *const *points, const uint64_t *n, uint32_t count, uint32_t d, int32_t metric,
+                        const pipnn_params *bp, const uint64_t *seeds, pipnn_graph *outs) {
+    if (count && (!points || !n || !seeds || !outs)) return set_error(PIPNN_EINVAL, "points/n/seeds/outs are NULL");
+    for (uint32_t i = 0; i < count; i++) memset(&outs[i], 0, sizeof(pipnn_graph));
+    for (uint32_t i = 0; i < count; i++) {
+        const int rc = build_impl(points[i], n[i], d, metric, bp, seeds[i], 0, &outs[i]);
+        if (rc != PIPNN_OK) {
+            for (uint32_t j = 0; j <= i; j++) pipnn_free(&outs[j]);
+            return rc;
+        }
+    }
+    return PIPNN_OK;
+}
+
 int pipnn_get_stats(pipnn_stats *out) {
     if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
     *out = g_stats;

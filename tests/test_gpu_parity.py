@@ -263,6 +263,26 @@ def test_build_single_leaf_sizes(n):
     assert np.array_equal(deg, deg_o) and np.array_equal(adj, adj_o)
 
 
+def test_build_batched_independent_indexes():
+    # several independent indexes of one dimension in one call, each with its own seed: every graph
+    # equals the oracle's build of that index alone (sizes span a multi-level partition, a single
+    # leaf and a three-point index; host and device inputs mixed)
+    H = synth.hyperplanes(12, 16, seed=2)
+    kw = dict(c_max=300, l_max=16, R=8, fanout=(3, 2), p_samp=0.01)
+    Xs = [synth.mixture(n, 16, synth.U8, 10, 10.0, seed=40 + n) for n in (4000, 250, 3)]
+    seeds = [11, 12, 13]
+    bp = pk.params(dtype=pk.PIPNN_U8, hyperplanes=H, **kw)
+    got = pk.pipnn_build_batched([dev(Xs[0]), Xs[1], dev(Xs[2])], bp, seeds)
+    assert len(got) == 3
+    for X, s, (adj, deg) in zip(Xs, seeds, got):
+        adj_o, deg_o, _ = oracle.build(X, oracle.params(**kw), H, seed=s)
+        assert np.array_equal(host(deg), deg_o) and np.array_equal(host(adj), adj_o)
+    # one invalid index (no points): an error, and no graph is returned
+    with pytest.raises(pk.PipnnError) as e:
+        pk.pipnn_build_batched([dev(Xs[0]), dev(Xs[0][:0])], bp, [1, 2])
+    assert e.value.code == -1
+
+
 def test_build_duplicate_points_guard():
     X = np.zeros((4000, 8), np.uint8)
     X[::5] = 7
