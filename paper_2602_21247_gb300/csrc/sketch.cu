@@ -1,8 +1,8 @@
 // sketch.cu -- A0: sketches Sketch(v) = [v . H_i] (Sec. 3 "Implementation") and squared norms.
 //
-// One thread per point (four coordinates per step when d % 4 == 0).  Every sketch coordinate is a binary32 fused-multiply-add chain over the
-// point's coordinates in index order, so it equals the CPU evaluation of the same definition bit
-// for bit.  Squared norms: binary32 FMA chain for float data, exact int32 for byte data.  The
+// One thread per point (four coordinates per step when d % 4 == 0).  Every sketch coordinate is a
+// binary32 fused-multiply-add chain over the point's coordinates in index order, so it equals the
+// CPU evaluation of the same definition bit for bit.  Squared norms: binary32 FMA chain for float data, exact int32 for byte data.  The
 // pass also rejects non-finite float coordinates (NaN would make every comparison false).
 #include "internal.cuh"
 
