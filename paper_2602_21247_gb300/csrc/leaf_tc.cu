@@ -341,9 +341,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         // D_ij = -2 acc is an integer below 2^23 (d <= 128 bytes), so fma(-2, acc, 2^23) = D + 2^23
         // exactly and its bit pattern is 0x4B000000 + D: times 128 plus the column in the tile it is
         // a 32-bit key ordered by (D, column), i.e. by (D, id) -- every 128-member tile of a leaf is
-        // in ascending id order.  Two smallest per chain: k2 = min(k2, max(k1, key)),
-        // k1 = min(k1, key).  Warp (quarter, half) takes chunks half and half + 2 of every tile; one
-        // chunk's TMEM load is always in flight while the other is ranked, across tiles and units.
+        // in ascending id order.  Two smallest per chain: k2 = min(k2, max(k1, key)), k1 = min(k1, key).  Warp
+        // (quarter, half) takes chunks half and half + 2 of every tile; one chunk's TMEM load is
+        // always in flight while the other is ranked, across tiles and units.
         const int ew = warp - EPI_WARP0;
         const int half = ew >> 2;
         const int quarter = warp & 3;
