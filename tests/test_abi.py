@@ -51,3 +51,19 @@ def test_params_struct_matches_header_layout():
     assert pk.pipnn_params.hyperplanes.offset == 4 * (3 + 1 + 4 + 1 + 4 + 1 + 1 + 2) + 4 == 72
     assert pk.pipnn_params.replicas.offset == 80
     assert ctypes.sizeof(pk.pipnn_params) == 88
+
+
+def test_batched_build_argument_checks_need_no_gpu():
+    # the binding validates the index list before it calls the library
+    import numpy as np
+
+    import paper_2602_21247_gb300 as pk
+
+    a = np.zeros((10, 8), np.uint8)
+    bp = pk.params(dtype=pk.PIPNN_U8)
+    with pytest.raises(ValueError):
+        pk.pipnn_build_batched([a, a], bp, [1])                       # one seed per index
+    with pytest.raises(ValueError):
+        pk.pipnn_build_batched([a, np.zeros((10, 9), np.uint8)], bp, [1, 2])    # one dimension
+    with pytest.raises(ValueError):
+        pk.pipnn_build_batched([a, np.zeros((10, 8), np.int8)], bp, [1, 2])     # one dtype
