@@ -98,6 +98,8 @@ def lib():
         L.orc_build.argtypes = [vp, u64, u32, i32, i32, C.POINTER(Params), vp, u64, vp, vp,
                                 C.POINTER(_Stats)]
         L.orc_knn.argtypes = [vp, u64, vp, u64, u32, i32, i32, u32, vp]
+        L.orc_ceil_of_product.argtypes = [C.c_float, u64]
+        L.orc_ceil_of_product.restype = u64
         L.orc_medoid.argtypes = [vp, u64, u32, i32, i32]
         L.orc_medoid.restype = u32
         L.orc_beam_search.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, vp, u64, u32, u32, u32,
@@ -295,6 +297,12 @@ def knn(X, Q, k=10, metric=L2):
     _check(lib().orc_knn(_p(X), X.shape[0], _p(Q), Q.shape[0], X.shape[1], _dtype_code(X), metric,
                          k, _p(ids)), "knn")
     return ids
+
+
+def ceil_of_product(p, n):
+    """ceil(p * n) of the exact real product of the binary32 value p and the integer n (the leader
+    count of Alg. 5 before its clamps)."""
+    return int(lib().orc_ceil_of_product(float(p), int(n)))
 
 
 def medoid(X, metric=L2):

@@ -303,11 +303,29 @@ static int cmp_u64(const void *a, const void *b)
 }
 
 /* Number of leaders of a subproblem of size np: l = max(2, min(ceil(P_samp * np), cap)), and
- * never more than np. */
+ * never more than np.  The ceiling is of the exact real product P_samp * np, where P_samp is the
+ * binary32 parameter: writing P_samp = M * 2^E (M the integer significand), it is the integer
+ * ceil(M * np / 2^-E), evaluated with a quotient and a remainder. */
+static uint64_t ceil_of_product(float p, uint64_t np)
+{
+    uint32_t bits;
+    memcpy(&bits, &p, 4);
+    uint32_t biased = (bits >> 23) & 0xFFu;
+    uint64_t M = biased ? ((bits & 0x7FFFFFu) | 0x800000u) : (bits & 0x7FFFFFu);
+    int E = biased ? (int)biased - 150 : -149;
+    uint64_t prod = M * np;
+    if (E >= 0) return prod << E;
+    int sh = -E;
+    if (sh >= 64) return prod != 0;
+    uint64_t q = prod >> sh, rem = prod - (q << sh);
+    return q + (rem != 0);
+}
+
+uint64_t orc_ceil_of_product(float p, uint64_t np) { return ceil_of_product(p, np); }
+
 static uint64_t leader_count(const orc_params *bp, uint64_t np)
 {
-    double want = ceil((double)bp->p_samp * (double)np);
-    uint64_t l = want < 1.0 ? 1 : (uint64_t)want;
+    uint64_t l = ceil_of_product(bp->p_samp, np);
     if (l > bp->max_leaders) l = bp->max_leaders;
     if (l < 2) l = 2;
     if (l > np) l = np;

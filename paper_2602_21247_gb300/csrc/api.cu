@@ -108,11 +108,12 @@ struct Timer {
     }
 };
 
-__global__ void leaf_pairs_kernel(const uint64_t *off, uint64_t L, double *acc) {
-    double local = 0.0;
+// sum over leaves of |b| (|b| - 1), in 64-bit integers
+__global__ void leaf_pairs_kernel(const uint64_t *off, uint64_t L, unsigned long long *acc) {
+    unsigned long long local = 0;
     for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < L; b += (uint64_t)gridDim.x * blockDim.x) {
-        double s = (double)(off[b + 1] - off[b]);
-        local += s * (s - 1.0);
+        const unsigned long long s = off[b + 1] - off[b];
+        local += s * (s ? s - 1 : 0);
     }
     atomicAdd(acc, local);
 }
@@ -185,7 +186,7 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     const uint32_t replicas = bp->replicas ? bp->replicas : 1;
     std::vector<Timer> rt(replicas);
     for (auto &t : rt) PIPNN_TRY(t.init());
-    double *acc;
+    unsigned long long *acc;
     PIPNN_TRY(ws.zeros(&acc, 1));
     uint64_t *res = nullptr;
     uint32_t *cnt = nullptr;
@@ -235,7 +236,8 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
         if (rc != PIPNN_OK) return rc;
         rt[r].mark(3);
     }
-    PIPNN_CUDA(cudaMemcpyAsync(&st.leaf_pairs, acc, 8, cudaMemcpyDeviceToHost, stream()));
+    unsigned long long leaf_pairs = 0;
+    PIPNN_CUDA(cudaMemcpyAsync(&leaf_pairs, acc, 8, cudaMemcpyDeviceToHost, stream()));
     tm.mark(4);
     int rc = PIPNN_OK;
 
@@ -303,6 +305,7 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
         st.ms_hashprune += t.ms(2, 3);
     }
     st.ms_prune = tm.ms(4, 5);
+    st.leaf_pairs = (double)leaf_pairs;
     st.leaf_pairs_executed = st.leaf_pairs + (double)st.leaf_members;
     st.ms_total = tm.ms(0, 6);
     st.kernel_launches = launch_count() - launches0;

@@ -32,17 +32,45 @@ constexpr uint32_t DEPTH_CAP = 12;
 constexpr uint32_t OB_NONE = 0xFFFFFFFFu;
 enum : uint8_t { OB_LEAF = 0, OB_MERGED = 1, OB_RECURSE = 2, OB_GUARD = 3 };
 
+// ceil(p * np) of the exact real product of the binary32 p = M * 2^E and the integer np, in
+// integer arithmetic (M < 2^24 and np < 2^32, so M * np fits 64 bits).
+__device__ __forceinline__ uint64_t ceil_mul_f32(float p, uint64_t np) {
+    const uint32_t bits = __float_as_uint(p);
+    const uint32_t ex = (bits >> 23) & 0xFFu;
+    const uint64_t M = ex ? ((bits & 0x7FFFFFu) | 0x800000u) : (bits & 0x7FFFFFu);
+    const int E = ex ? (int)ex - 150 : -149;
+    const uint64_t prod = M * np;
+    if (E >= 0) return prod << E;  // p <= 1 keeps E negative; kept for completeness
+    const int sh = -E;
+    if (sh >= 64) return prod ? 1 : 0;
+    const uint64_t q = prod >> sh;
+    return q + ((prod & ((1ull << sh) - 1)) ? 1 : 0);
+}
+
 __device__ __forceinline__ uint32_t leader_count(uint64_t np, float p_samp, uint32_t cap) {
-    double want = ceil((double)p_samp * (double)np);
-    uint64_t l = want < 1.0 ? 1 : (uint64_t)want;
+    uint64_t l = ceil_mul_f32(p_samp, np);
     if (l > cap) l = cap;
     if (l < 2) l = 2;
     if (l > np) l = np;
     return (uint32_t)l;
 }
 
+__device__ __forceinline__ uint32_t isqrt_u32(uint32_t v) {
+    uint32_t s = 0;
+    while ((s + 1) * (s + 1) <= v) s++;
+    return s;
+}
+
+// Candidate threshold of the leader sample: a member is collected when its 32-bit priority is
+// below thr = min(2^32, expect * 2^32 / n), so about `expect` of the n members are collected.
+// Any threshold gives the same leaders (the l smallest priorities of those collected, retried
+// when fewer than l or more than the buffer arrive); this only sizes the work.
+__device__ __forceinline__ unsigned long long sample_threshold(uint64_t expect, uint32_t n) {
+    return expect >= n ? (1ull << 32) : (unsigned long long)((expect << 32) / n);
+}
+
 __global__ void seg_setup(uint64_t S, const uint32_t *seg_size, float p_samp, uint32_t cap_leaders,
-                          uint32_t *lead_cnt, uint64_t *lead_cnt64, uint64_t *cand_cap, double *mult,
+                          uint32_t *lead_cnt, uint64_t *lead_cnt64, uint64_t *cand_cap, uint64_t *expect,
                           unsigned long long *thr, uint8_t *active, uint32_t *ccnt) {
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S; s += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t n = seg_size[s];
@@ -50,10 +78,9 @@ __global__ void seg_setup(uint64_t S, const uint32_t *seg_size, float p_samp, ui
         lead_cnt[s] = l;
         lead_cnt64[s] = l;
         cand_cap[s] = n < CAND_CAP ? n : CAND_CAP;
-        mult[s] = 1.0;
-        double e = (double)l + 5.0 * sqrt((double)l) + 10.0;
-        double p = e / (double)n;
-        thr[s] = p >= 1.0 ? (1ull << 32) : (unsigned long long)(p * 4294967296.0);
+        const uint64_t e = (uint64_t)l + 5u * isqrt_u32(l) + 10u;
+        expect[s] = e;
+        thr[s] = sample_threshold(e, n);
         active[s] = 1;
         ccnt[s] = 0;
     }
@@ -75,8 +102,9 @@ __global__ void collect_candidates(uint64_t N, const uint32_t *inst, const uint3
     }
 }
 
+// Too few candidates: expect twice as many; too many: three fifths as many.
 __global__ void check_candidates(uint64_t S, const uint32_t *seg_size, const uint32_t *lead_cnt,
-                                 const uint64_t *cand_cap, uint32_t *ccnt, double *mult,
+                                 const uint64_t *cand_cap, uint32_t *ccnt, uint64_t *expect,
                                  unsigned long long *thr, uint8_t *active, unsigned *nbad) {
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S; s += (uint64_t)gridDim.x * blockDim.x) {
         if (!active[s]) continue;
@@ -87,11 +115,12 @@ __global__ void check_candidates(uint64_t S, const uint32_t *seg_size, const uin
             continue;
         }
         atomicAdd(nbad, 1u);
-        mult[s] *= under ? 2.0 : 0.6;
-        uint32_t l = lead_cnt[s];
-        double e = ((double)l + 5.0 * sqrt((double)l) + 10.0) * mult[s];
-        double p = e / (double)seg_size[s];
-        thr[s] = p >= 1.0 ? (1ull << 32) : (unsigned long long)(p * 4294967296.0);
+        uint64_t e = expect[s];
+        e = under ? 2 * e : (3 * e) / 5;
+        if (e < 1) e = 1;
+        if (e > (1ull << 32)) e = 1ull << 32;
+        expect[s] = e;
+        thr[s] = sample_threshold(e, seg_size[s]);
         ccnt[s] = 0;
     }
 }
@@ -440,7 +469,7 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         Workspace tw;  // temporaries of this level
         uint32_t *lead_cnt, *ccnt, *lead, *bucket_cnt;
         uint64_t *lead_cnt64, *lead_off, *cand_cap, *cand_off, *cbuf, *tot;
-        double *mult;
+        uint64_t *expect;
         unsigned long long *thr;
         uint8_t *active;
         unsigned *nbad;
@@ -449,7 +478,7 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         PIPNN_TRY(tw.alloc(&lead_off, S));
         PIPNN_TRY(tw.alloc(&cand_cap, S));
         PIPNN_TRY(tw.alloc(&cand_off, S));
-        PIPNN_TRY(tw.alloc(&mult, S));
+        PIPNN_TRY(tw.alloc(&expect, S));
         PIPNN_TRY(tw.alloc(&thr, S));
         PIPNN_TRY(tw.alloc(&active, S));
         PIPNN_TRY(tw.alloc(&ccnt, S));
@@ -457,7 +486,7 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         PIPNN_TRY(tw.zeros(&nbad, 1));
         const unsigned gs = grid_for(S, 256);
         seg_setup<<<gs, 256, 0, stream()>>>(S, cur->seg_size, bp->p_samp, bp->max_leaders, lead_cnt, lead_cnt64,
-                                            cand_cap, mult, thr, active, ccnt);
+                                            cand_cap, expect, thr, active, ccnt);
         PIPNN_LAUNCH_CHECK();
         uint64_t h2[2];
         PIPNN_TRY(exclusive_scan_u64(lead_cnt64, lead_off, S, tot, tw));
@@ -476,7 +505,7 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
                                                                        active, cand_off, cand_cap, ccnt, cbuf, seed);
             PIPNN_LAUNCH_CHECK();
             PIPNN_CUDA(cudaMemsetAsync(nbad, 0, sizeof(unsigned), stream()));
-            check_candidates<<<gs, 256, 0, stream()>>>(S, cur->seg_size, lead_cnt, cand_cap, ccnt, mult, thr, active,
+            check_candidates<<<gs, 256, 0, stream()>>>(S, cur->seg_size, lead_cnt, cand_cap, ccnt, expect, thr, active,
                                                        nbad);
             PIPNN_LAUNCH_CHECK();
             unsigned hb = 0;

@@ -2,7 +2,9 @@
 hand-worked sequences of Alg. 2 and Alg. 3, exact integer arithmetic, error bounds, brute force
 on tiny inputs, the history-independence theorem (Sec. 3) and the invariants of Alg. 5."""
 import itertools
+import math
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -327,7 +329,7 @@ def _level0_reference(X, bp, seed):
     """Level 0 of Alg. 5 computed independently: leaders are the l smallest (Philox priority, id)
     under subproblem 0, every point joins its f nearest leaders (ties to the earlier-drawn one)."""
     n = X.shape[0]
-    l = int(max(2, min(np.ceil(np.float64(np.float32(bp.p_samp)) * n), bp.max_leaders)))
+    l = int(max(2, min(math.ceil(Fraction(float(np.float32(bp.p_samp))) * n), bp.max_leaders)))
     prio = np.array([oracle.philox4x32_10([i, 0, 0, 0x1EAD], [seed & 0xFFFFFFFF, seed >> 32])[0]
                      for i in range(n)], np.uint64)
     leaders = np.lexsort((np.arange(n), prio))[:l]
@@ -480,3 +482,41 @@ def test_invalid_parameters_rejected():
     Xf[3, 2] = np.nan
     with pytest.raises(RuntimeError):
         oracle.partition(Xf, oracle.params(c_max=64), seed=1)
+
+
+# --------------------------------------------------------------------------------------------
+# Leader count (Sec. 4.1: ceil(P_samp |P|)) and the beam-search start (medoid)
+# --------------------------------------------------------------------------------------------
+def test_leader_count_ceiling_is_exact():
+    """ceil of the exact real product of the binary32 P_samp and |P|, checked with rationals,
+    including products that are integers and products just above one (where a rounded
+    double product can land on the integer below)."""
+    rng = np.random.default_rng(5)
+    ps = [0.005, 0.01, 0.5, 1.0, 2.0 ** -20, float(np.float32(1 / 3)), 1e-30]
+    ps += [float(np.float32(v)) for v in rng.uniform(1e-4, 1.0, 40)]
+    ns = [1, 2, 3, 199, 200, 201, 1 << 20, (1 << 32) - 2, 123456789, 4000000001]
+    ns += [int(v) for v in rng.integers(1, 1 << 32, 40)]
+    for p in ps:
+        pf = Fraction(float(np.float32(p)))
+        for n in ns:
+            assert oracle.ceil_of_product(p, n) == math.ceil(pf * n), (p, n)
+    # p = M 2^-24 with M odd and n = M^-1 (mod 2^24) + 200 2^24: the exact product is an integer
+    # plus 2^-24, which a binary64 product of this size rounds away
+    M = (1 << 23) + 12345
+    n = pow(M, -1, 1 << 24) + 200 * (1 << 24)
+    p = M / 2.0 ** 24
+    k = (M * n) >> 24
+    assert float(np.float64(p) * np.float64(n)) == k  # the rounded product sits on the integer
+    assert oracle.ceil_of_product(p, n) == k + 1
+
+
+@pytest.mark.parametrize("dtype", [synth.F32, synth.U8, synth.I8])
+def test_medoid_is_point_nearest_to_mean(dtype):
+    X = synth.mixture(2000, 24, dtype, 10, 0.3 if dtype == synth.F32 else 10.0, seed=31)
+    Xd = X.astype(np.float64)
+    dist = ((Xd - Xd.mean(0)) ** 2).sum(1)
+    want = int(np.argmin(dist))  # first index among equals, like the oracle's strict comparison
+    assert oracle.medoid(X) == want
+    # a planted exact centre: the mean of a symmetric set is one of its points
+    Y = np.array([[0, 0], [2, 0], [-2, 0], [0, 2], [0, -2], [1, 1], [-1, -1]], np.float32)
+    assert oracle.medoid(Y) == 0
