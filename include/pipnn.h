@@ -187,7 +187,9 @@ int pipnn_hashprune(const uint32_t *dst, const uint32_t *src, const float *dist,
  * (each term rounded up to 256); larger inputs return PIPNN_EINVAL with the sizes in the
  * message, before any GPU work.  The first call on each device looks up the array's device
  * address (with that device current) and remembers it; make that first call before any stream
- * capture.  All calls share the array and clear what they need on entry, so calls that overlap
+ * capture.  The remembered address does not survive cudaDeviceReset: after a reset of a device,
+ * do not call this entry point on it again in the same process.  All calls share the array and
+ * clear what they need on entry, so calls that overlap
  * on the GPU (different streams or threads on one device) race and must be serialised by the
  * caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
 int pipnn_hashprune_noalloc(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count,

@@ -468,7 +468,9 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
 // slots and the error word) lives in one file-scope device array of HP_STATIC_BYTES that every
 // GPU loading this library keeps until the process exits.  Host code cannot use the array's
 // name as a device address, so the first call on each device, with that device current, asks
-// the runtime for the address once (cudaGetSymbolAddress) and later calls reuse it.  Every call
+// the runtime for the address once (cudaGetSymbolAddress) and later calls reuse it; the remembered
+// address does not survive cudaDeviceReset (the library's module is reloaded afterwards, possibly
+// elsewhere), so a process that resets a device must not call this entry point again.  Every call
 // shares the array and reuses whatever the previous call left there, so the parts that must
 // start at zero are cleared on each call; two calls whose work overlaps on the GPU (different
 // streams or host threads on the same device) race on it.
@@ -529,12 +531,14 @@ int hashprune_noalloc_impl(const uint32_t *dst, const uint32_t *src, const float
     if (n == 0 || n >= 0xFFFFFFFFull) return set_error(PIPNN_EINVAL, "n outside 1..2^32-2");
     if (m < 1 || m > 16) return set_error(PIPNN_EINVAL, "hash_bits %u outside 1..16", m);
     if (l_max < 1 || l_max > 256) return set_error(PIPNN_EINVAL, "l_max %u outside 1..256", l_max);
-    const StaticLayout L = static_layout(n, count);
-    if (L.bytes > HP_STATIC_BYTES)
+    // bound n and count first, so the layout arithmetic below cannot wrap around
+    const bool too_big = count > HP_STATIC_BYTES / 8 || n > HP_STATIC_BYTES / 12;
+    const StaticLayout L = too_big ? StaticLayout{0, 0, 0, 0, 0, 0, ~(size_t)0} : static_layout(n, count);
+    if (too_big || L.bytes > HP_STATIC_BYTES)
         return set_error(PIPNN_EINVAL,
-                         "n = %llu nodes and %llu candidates need %zu bytes of scratch; the static scratch "
-                         "holds %zu bytes (use pipnn_hashprune or split the stream)",
-                         (unsigned long long)n, (unsigned long long)count, L.bytes, HP_STATIC_BYTES);
+                         "n = %llu nodes and %llu candidates need more than the %zu bytes the static scratch "
+                         "holds (use pipnn_hashprune or split the stream)",
+                         (unsigned long long)n, (unsigned long long)count, HP_STATIC_BYTES);
     unsigned char *base = nullptr;
     PIPNN_TRY(static_scratch_address(&base));
     unsigned *err = reinterpret_cast<unsigned *>(base + L.err);

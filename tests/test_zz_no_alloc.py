@@ -56,6 +56,11 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls():
         assert np.array_equal(as_np(got_cnt), as_np(ref_cnt))
         assert np.array_equal(as_np(got_res), as_np(ref_res))
 
+    # and both equal the oracle's closed form of Alg. 3 over the whole stream
+    want_res, want_cnt = oracle.hashprune_closed(dst, src, dist, S, n, l_max)
+    assert np.array_equal(as_np(got_cnt).astype(np.uint32), want_cnt)
+    assert np.array_equal(as_np(got_res).view(np.uint64), want_res)
+
     # a fresh pair of reservoirs after the scratch holds the previous call's contents
     ref2, rc2 = empty_reservoirs(n, l_max)
     got2, gc2 = empty_reservoirs(n, l_max)
