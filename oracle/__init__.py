@@ -12,7 +12,7 @@ Every function returns numpy arrays and follows the paper's definitions:
   final_prune ....... Alg. 2 RobustPrune (standard or lazy) to degree R
   build ............. Alg. 4 end to end
   build_replicated .. Alg. 4 with Sec. 4.1 replication (independent RBC copies, one HashPrune)
-  knn / beam_search / recall .. Def. 1, Alg. 1 and Def. 2 for evaluating graphs
+  knn / knn_bytes / beam_search / recall .. Def. 1, Alg. 1 and Def. 2 for evaluating graphs
 """
 from __future__ import annotations
 
@@ -297,6 +297,45 @@ def knn(X, Q, k=10, metric=L2):
     _check(lib().orc_knn(_p(X), X.shape[0], _p(Q), Q.shape[0], X.shape[1], _dtype_code(X), metric,
                          k, _p(ids)), "knn")
     return ids
+
+
+def knn_bytes(X, Q, k=10, chunk=256):
+    """Exact k nearest points of every query by (squared L2, id) for byte data (Def. 1), the same
+    result as knn() but through a float32 matrix product: u8 / i8 coordinates are integers of
+    magnitude <= 255, so every product and every partial sum of a d <= 128 dot product is an
+    integer below 2^24 and exact in binary32 whatever the summation order; the distances
+    ||q||^2 + ||x||^2 - 2<q, x> are then formed exactly in int64.  Rows whose k-th and (k+1)-th
+    distances tie are resolved by id with an exact scan of that row."""
+    import torch
+
+    X = np.ascontiguousarray(X)
+    Q = np.ascontiguousarray(Q, dtype=X.dtype)
+    if X.dtype not in (np.uint8, np.int8) or X.shape[1] > 128:
+        raise ValueError("knn_bytes takes byte data with d <= 128")
+    Xf = torch.from_numpy(X.astype(np.float32))
+    nx = torch.from_numpy((X.astype(np.int64) ** 2).sum(1))
+    out = np.zeros((Q.shape[0], k), np.uint32)
+    for s in range(0, Q.shape[0], chunk):
+        q = Q[s:s + chunk]
+        dot = (torch.from_numpy(q.astype(np.float32)) @ Xf.T).to(torch.int64)
+        nq = torch.from_numpy((q.astype(np.int64) ** 2).sum(1))
+        D = nq[:, None] + nx[None, :] - 2 * dot
+        kk = min(k + 1, X.shape[0])
+        val, idx = torch.topk(D, kk, dim=1, largest=False, sorted=True)
+        val, idx = val.numpy(), idx.numpy()
+        Dn = None
+        for r in range(q.shape[0]):
+            if kk > k and val[r, k] == val[r, k - 1] or len(set(val[r, :k].tolist())) < k:
+                # ties inside or at the edge of the top k: order every candidate up to the k-th
+                # distance by (distance, id)
+                if Dn is None:
+                    Dn = D.numpy()
+                c = np.nonzero(Dn[r] <= val[r, k - 1])[0]
+                o = np.lexsort((c, Dn[r, c]))[:k]
+                out[s + r] = c[o]
+            else:
+                out[s + r] = idx[r, :k]
+    return out
 
 
 def ceil_of_product(p, n):

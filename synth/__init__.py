@@ -104,6 +104,19 @@ def mixture(n, d, dtype, centers, sigma, seed, normalize=False, n_queries=0, que
     return pts
 
 
+def queries(name, n_queries=None):
+    """Only the queries of a named workload (the same draws workload() returns beside the points)."""
+    w = WORKLOADS[name]
+    nq = w["queries"] if n_queries is None else n_queries
+    rng_q = np.random.default_rng([w["query_seed"], 2])
+    rc = np.random.default_rng([w["data_seed"], 0])
+    if w["dtype"] == F32:
+        return _mixture_f32(nq, w["d"], w["centers"], w["sigma"], rc, rng_q, w["metric"] == IP)
+    if w["dtype"] == U8:
+        return _mixture_u8(nq, w["d"], w["centers"], w["sigma"], rc, rng_q)
+    return _mixture_i8(nq, w["d"], w["centers"], w["sigma"], rc, rng_q)
+
+
 def workload(name, n=None, n_queries=None):
     """Points and queries of a named workload (n may be overridden for reduced test sizes)."""
     w = WORKLOADS[name]

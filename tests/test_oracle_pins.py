@@ -520,3 +520,19 @@ def test_medoid_is_point_nearest_to_mean(dtype):
     # a planted exact centre: the mean of a symmetric set is one of its points
     Y = np.array([[0, 0], [2, 0], [-2, 0], [0, 2], [0, -2], [1, 1], [-1, -1]], np.float32)
     assert oracle.medoid(Y) == 0
+
+
+@pytest.mark.parametrize("dtype", [synth.U8, synth.I8])
+def test_knn_bytes_equals_plain_knn_and_brute_force(dtype):
+    """The matrix-product ground truth equals the plain scan (Def. 1, ties by id), including rows
+    with planted ties at the k-th distance."""
+    X, Q = synth.mixture(3000, 128, dtype, 20, 10.0, seed=44, n_queries=60, query_seed=45)
+    X = X.copy()
+    X[100:130] = X[99]  # 31 identical points: ties across the k-th position for queries near them
+    Q = np.concatenate([Q, X[99:100], X[5:6]])
+    want = oracle.knn(X, Q, 10)
+    got = oracle.knn_bytes(X, Q, 10, chunk=16)
+    assert np.array_equal(got, want)
+    D = ((Q[:, None, :].astype(np.int64) - X[None, :, :].astype(np.int64)) ** 2).sum(2)
+    brute = np.lexsort((np.broadcast_to(np.arange(X.shape[0]), D.shape), D), axis=1)[:, :10]
+    assert np.array_equal(got, brute)
