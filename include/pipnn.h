@@ -56,12 +56,31 @@ enum { PIPNN_L2 = 0, PIPNN_IP = 1 };
  *  PIPNN_LEAF_TC:   tcgen05 tensor-core tiles with BF16 operands and FP32 accumulation in TMEM
  *                   that produce n_j - 2<x_i, x_j> directly (the norm enters as extra K
  *                   columns).  For byte data with d <= 128 every product and partial sum is an
- *                   integer below 2^24, so the result is exact.  The leaf step returns
- *                   PIPNN_EUNSUPPORTED for float data and d > 128; the assignment (byte data,
+ *                   integer below 2^24, so the result is exact.  Float data runs the leaf
+ *                   step at the reduced precision chosen by pipnn_params.prec (BF16 or FP8,
+ *                   below) with an exact re-rank; the leaf step returns PIPNN_EUNSUPPORTED for
+ *                   d > 128 and for float data at PIPNN_PREC_FP32; the assignment (byte data,
  *                   d <= 128, fanout of the level <= 16) and the final prune (byte data,
  *                   d <= 128, l_max <= 127) run on the tensor cores where they apply and on the
  *                   CUDA cores otherwise. */
 enum { PIPNN_LEAF_SIMT = 0, PIPNN_LEAF_TC = 1 };
+
+/* Operand precision of the leaf Gram GEMM on the tensor cores (Sec. 4.2 forms the leaf's
+ * all-pairs distances with a GEMM; the conclusion names quantised GEMMs as the next step).
+ * Every precision gives the same picks -- those of the defining binary32 / exact-integer
+ * dissimilarity -- so the graph does not depend on it:
+ *  PIPNN_PREC_FP32: the defining precision.  Float data runs the leaf step on the CUDA cores
+ *                   (the tensor-core engine rejects it); byte data runs exactly on either engine.
+ *  PIPNN_PREC_BF16: float data on PIPNN_LEAF_TC: leaf-centred BF16 operands, FP32 accumulation
+ *                   in TMEM, then the candidates within a proven error band of every row's k-th
+ *                   are re-ranked with the defining binary32 evaluation (rows whose band does
+ *                   not fit the tracked candidates are evaluated in full).
+ *  PIPNN_PREC_FP8:  as BF16 with e4m3 operands and one scale per leaf (448 over the leaf's
+ *                   largest centred coordinate).
+ *  PIPNN_PREC_INT8: byte data only; the exact integer Gram (the tensor-core engine holds u8 / i8
+ *                   values exactly in BF16 with FP32 accumulation, exact for d <= 128).
+ * For byte data every precision is exact and they are interchangeable. */
+enum { PIPNN_PREC_FP32 = 0, PIPNN_PREC_BF16 = 1, PIPNN_PREC_FP8 = 2, PIPNN_PREC_INT8 = 3 };
 
 /* Hyper-parameters BP of Alg. 4. */
 typedef struct pipnn_params {
@@ -87,6 +106,7 @@ typedef struct pipnn_params {
                                (1..16; 0 means 1).  Replica r partitions with the seed
                                seed + r * 0x9E3779B97F4A7C15 (mod 2^64), so replica 0 is the
                                single-replica build.                                          */
+    int32_t prec;           /* PIPNN_PREC_*: operand precision of the tensor-core leaf Gram      */
 } pipnn_params;
 
 /* Output graph: ids[v*R + j] for j < deg[v] are v's out-neighbours in prune order; the rest of
@@ -129,6 +149,8 @@ typedef struct pipnn_stats {
                                     evaluate (both orders and the diagonal; the tensor-core
                                     kernel also evaluates the padding of ragged tiles)          */
     uint64_t kernel_launches;    /* kernels this library launched during the build              */
+    uint64_t leaf_full_rows;     /* reduced-precision leaf engine: rows whose error band did not
+                                    fit the tracked candidates and were evaluated in full        */
 } pipnn_stats;
 
 /* Sets the CUDA stream (a cudaStream_t, or NULL for the default stream) used by later calls. */
@@ -157,10 +179,12 @@ void pipnn_leaves_free(pipnn_leaves *leaves);
 /* A2-A4 -- for every leaf (offsets/members as produced by pipnn_partition, device, distinct
  * members), the k nearest other members of every member by (dissimilarity, id), emitted in both
  * directions (Sec. 4.2, App. A.3): 2 * |b| * min(k, |b|-1) edges per leaf, in no particular
- * order.  engine: PIPNN_LEAF_SIMT or PIPNN_LEAF_TC.  Free the result with pipnn_edges_free. */
+ * order.  engine: PIPNN_LEAF_SIMT or PIPNN_LEAF_TC; prec: PIPNN_PREC_* (float data on the
+ * tensor cores needs BF16 or FP8; the edges are the same for every engine and precision).  Free
+ * the result with pipnn_edges_free. */
 int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
                     const uint64_t *offsets, const uint32_t *members, uint64_t num_leaves,
-                    uint32_t k, int32_t engine, pipnn_edges *out);
+                    uint32_t k, int32_t engine, int32_t prec, pipnn_edges *out);
 void pipnn_edges_free(pipnn_edges *edges);
 
 /* A5 -- Alg. 3 HashPrune of a candidate stream into the reservoirs of n nodes.

@@ -15,8 +15,8 @@ int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float 
 int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                      const pipnn_params *bp, uint64_t seed, pipnn_leaves *out);
 int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-              const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, pipnn_edges *out,
-              float *ms_kernel, uint32_t *launches);
+              const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, int prec,
+              pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows);
 int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
                     uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt);
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
@@ -86,6 +86,9 @@ int check_params(const pipnn_params *bp) {
         return set_error(PIPNN_EINVAL, "unknown leaf_engine %d", bp->leaf_engine);
     if (!bp->hyperplanes) return set_error(PIPNN_EINVAL, "hyperplanes is NULL");
     if (bp->replicas > 16) return set_error(PIPNN_EINVAL, "replicas above 16");
+    if (bp->prec < PIPNN_PREC_FP32 || bp->prec > PIPNN_PREC_INT8) return set_error(PIPNN_EINVAL, "unknown prec %d", bp->prec);
+    if (bp->dtype == PIPNN_F32 && bp->prec == PIPNN_PREC_INT8)
+        return set_error(PIPNN_EUNSUPPORTED, "PIPNN_PREC_INT8 takes byte data");
     return PIPNN_OK;
 }
 
@@ -142,8 +145,9 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     PIPNN_TRY(check_params(bp));
     const int dtype = bp->dtype;
     PIPNN_TRY(check_points(points, n, d, dtype, metric));
-    if (bp->leaf_engine == PIPNN_LEAF_TC && dtype == PIPNN_F32)
-        return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes byte data only");
+    if (bp->leaf_engine == PIPNN_LEAF_TC && dtype == PIPNN_F32 && bp->prec != PIPNN_PREC_BF16 &&
+        bp->prec != PIPNN_PREC_FP8)
+        return set_error(PIPNN_EUNSUPPORTED, "float data on the tensor-core leaf engine needs prec BF16 or FP8");
     CallScope cs;
     PIPNN_TRY(cs.init());
     Workspace &ws = cs.ws;
@@ -209,8 +213,10 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
         pipnn_edges edges;
         float leaf_ms = 0.0f;
         uint32_t leaf_launches = 0;
+        uint64_t full_rows = 0;
         int rc = leaf_pick(X, n, d, dtype, metric, sqn_bytes, leaves.offsets, leaves.members, leaves.num_leaves,
-                           bp->leaf_k, bp->leaf_engine, &edges, &leaf_ms, &leaf_launches);
+                           bp->leaf_k, bp->leaf_engine, bp->prec, &edges, &leaf_ms, &leaf_launches, &full_rows);
+        st.leaf_full_rows += full_rows;
         dev_free_raw(leaves.offsets);
         dev_free_raw(leaves.members);
         if (rc != PIPNN_OK) return rc;
@@ -357,7 +363,8 @@ void pipnn_leaves_free(pipnn_leaves *l) {
 }
 
 int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric, const uint64_t *offsets,
-                    const uint32_t *members, uint64_t num_leaves, uint32_t k, int32_t engine, pipnn_edges *out) {
+                    const uint32_t *members, uint64_t num_leaves, uint32_t k, int32_t engine, int32_t prec,
+                    pipnn_edges *out) {
     if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
     memset(out, 0, sizeof(*out));
     CallScope cs;
@@ -366,10 +373,9 @@ int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, i
     if (!offsets || (!members && num_leaves)) return set_error(PIPNN_EINVAL, "offsets/members are NULL");
     if (k < 1 || k > 16) return set_error(PIPNN_EINVAL, "k outside 1..16");
     if (engine != PIPNN_LEAF_SIMT && engine != PIPNN_LEAF_TC) return set_error(PIPNN_EINVAL, "unknown engine");
-    if (engine == PIPNN_LEAF_TC && dtype == PIPNN_F32)
-        return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes byte data only");
-    return leaf_pick(points, n, d, dtype, metric, nullptr, offsets, members, num_leaves, k, engine, out, nullptr,
-                     nullptr);
+    if (prec < PIPNN_PREC_FP32 || prec > PIPNN_PREC_INT8) return set_error(PIPNN_EINVAL, "unknown prec %d", prec);
+    return leaf_pick(points, n, d, dtype, metric, nullptr, offsets, members, num_leaves, k, engine, prec, out, nullptr,
+                     nullptr, nullptr);
 }
 
 void pipnn_edges_free(pipnn_edges *e) {

@@ -12,6 +12,10 @@ int leaf_pick_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t
                  const uint32_t *mem, uint64_t L, const uint32_t *leaf_size, const uint64_t *cand_off, uint32_t k,
                  uint32_t *out_dst, uint32_t *out_src, float *out_dist, Workspace &ws, cudaEvent_t ev0,
                  cudaEvent_t ev1, uint32_t *launches);
+int leaf_pick_tcf(const float *X, uint64_t n, uint32_t d, int metric, int prec, const uint64_t *off,
+                  const uint32_t *mem, uint64_t L, const uint32_t *leaf_size, const uint64_t *cand_off, uint32_t k,
+                  uint32_t *out_dst, uint32_t *out_src, float *out_dist, Workspace &ws, cudaEvent_t ev0,
+                  cudaEvent_t ev1, uint32_t *launches, uint64_t *fallback_rows);
 
 namespace {
 // caller-supplied leaves: offsets non-decreasing, member ids below n
@@ -35,8 +39,11 @@ __global__ void leaf_sizes(const uint64_t *off, uint64_t L, uint32_t k, uint32_t
 }  // namespace
 
 int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-              const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, pipnn_edges *out,
-              float *ms_kernel, uint32_t *launches) {
+              const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, int prec,
+              pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows) {
+    if (full_rows) *full_rows = 0;
+    if (engine == PIPNN_LEAF_TC && dtype == PIPNN_F32 && prec != PIPNN_PREC_BF16 && prec != PIPNN_PREC_FP8)
+        return set_error(PIPNN_EUNSUPPORTED, "float data on the tensor-core leaf engine needs prec BF16 or FP8");
     memset(out, 0, sizeof(*out));
     Workspace ws;
     const int32_t *sqn = sqnorm_bytes;
@@ -71,7 +78,10 @@ int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, cons
         rc = set_error(PIPNN_ECUDA, "event creation failed");
     uint32_t nl = 0;
     if (rc == PIPNN_OK) {
-        if (engine == PIPNN_LEAF_TC) {
+        if (engine == PIPNN_LEAF_TC && dtype == PIPNN_F32) {
+            rc = leaf_pick_tcf(static_cast<const float *>(X), n, d, metric, prec, off, mem, L, size, cand_off, k, dst,
+                               src, dist, ws, ev0, ev1, &nl, full_rows);
+        } else if (engine == PIPNN_LEAF_TC) {
             rc = leaf_pick_tc(X, n, d, dtype, sqn, off, mem, L, size, cand_off, k, dst, src, dist, ws, ev0, ev1, &nl);
         } else {
             uint32_t *tile_grp = nullptr, *tile_row0 = nullptr;

@@ -73,7 +73,8 @@ int stage_rows_bf16(const void *X, uint32_t d, uint32_t kp, int dtype, const uin
     return PIPNN_OK;
 }
 
-int encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *base, uint64_t n, uint32_t kp, bool gather) {
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -82,10 +83,33 @@ int encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *base, uint64_t n, uin
                 cudaSuccess ||
             !fn) {
             cudaGetLastError();
-            return set_error(PIPNN_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+            return nullptr;
         }
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    return encode;
+}
+}  // namespace
+
+int encode_bytes_map(CUtensorMap *map, const void *base, uint64_t n, uint32_t kpb) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return set_error(PIPNN_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    if (n >= 0x7FFFFFFFull) return set_error(PIPNN_EUNSUPPORTED, "a tensor map addresses fewer than 2^31 rows");
+    if (kpb % 128 != 0) return set_error(PIPNN_EINVAL, "byte rows of %u bytes (a multiple of 128 is needed)", kpb);
+    const cuuint64_t gdim[2] = {kpb, n};
+    const cuuint64_t gstride[1] = {(cuuint64_t)kpb};
+    const cuuint32_t box[2] = {128, 128};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult rc = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), gdim, gstride, box,
+                               estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rc != CUDA_SUCCESS) return set_error(PIPNN_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)rc);
+    return PIPNN_OK;
+}
+
+int encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *base, uint64_t n, uint32_t kp, bool gather) {
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return set_error(PIPNN_ECUDA, "cuTensorMapEncodeTiled is unavailable");
     if (n >= 0x7FFFFFFFull) return set_error(PIPNN_EUNSUPPORTED, "a tensor map addresses fewer than 2^31 rows");
     const cuuint64_t gdim[2] = {kp, n};
     const cuuint64_t gstride[1] = {(cuuint64_t)kp * 2};

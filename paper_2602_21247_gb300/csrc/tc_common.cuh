@@ -133,6 +133,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
         : "memory");
 }
 
+// Instruction descriptor, kind::f8f6f4: E4M3 x E4M3 -> FP32, both operands K-major (32 K per MMA).
+__device__ __forceinline__ uint32_t idesc_e4m3(uint32_t M, uint32_t N) {
+    return (1u << 4)              // D: FP32
+           | (0u << 7)            // A: E4M3
+           | (0u << 10)           // B: E4M3
+           | ((N >> 3) << 17)     // N / 8
+           | ((M >> 4) << 24);    // M / 16
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
@@ -251,6 +269,10 @@ int stage_rows_bf16(const void *X, uint32_t d, uint32_t kp, int dtype, const uin
 // Tensor map over an n x kp BF16 row-major matrix with 128-byte swizzle: boxes of 128 rows x 64
 // columns (tiled loads) or, with gather = true, of 1 row x 64 columns (tile::gather4).
 int encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *base, uint64_t n, uint32_t kp, bool gather);
+
+// Tensor map over an n x kpb byte matrix (8-bit operands, kpb a multiple of 128) with 128-byte
+// swizzle: boxes of 128 rows x 128 bytes.
+int encode_bytes_map(CUtensorMap *map, const void *base, uint64_t n, uint32_t kpb);
 
 // ---------------------------------------------------------------- Alg. 5 assignment engine
 constexpr uint32_t ASSIGN_TC_MAX_F = 16;

@@ -50,6 +50,7 @@ def test_params_struct_matches_header_layout():
     # padding to the pointer's alignment
     assert pk.pipnn_params.hyperplanes.offset == 4 * (3 + 1 + 4 + 1 + 4 + 1 + 1 + 2) + 4 == 72
     assert pk.pipnn_params.replicas.offset == 80
+    assert pk.pipnn_params.prec.offset == 84
     assert ctypes.sizeof(pk.pipnn_params) == 88
 
 
