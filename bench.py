@@ -185,6 +185,121 @@ def recall_gate(X, H, w, adj_gpu, deg_gpu, n_queries):
     return rec, cpu
 
 
+PREC_MODES = (("fp32", "simt", 0), ("bf16x3", "tc", 4), ("bf16", "tc", 1), ("fp8", "tc", 2))
+
+
+def precision_modes(steps, warmup, n_queries=1000, error_leaves=48):
+    """The deep-like-ip workload (1M x 96 float32, unit norm, inner product) built with every leaf
+    precision: the defining FP32 evaluation on the CUDA cores, and the tensor-core Gram at split
+    BF16 (three BF16 products), BF16 and FP8 e4m3, each with its exact FP32 re-rank.  Reports
+    points/s per mode, whether each graph equals the FP32 one, the rows whose error band did not
+    fit and were evaluated in full, the recall@10 of the (shared) graph, and the error of each
+    mode's leaf dissimilarities against FP64 on a sample of the partition's leaves."""
+    import torch
+
+    import oracle
+    import paper_2602_21247_gb300 as pk
+
+    name = "deep-like-ip"
+    w = synth.WORKLOADS[name]
+    X, Q = synth.workload(name, n_queries=n_queries)
+    n, d = X.shape
+    H = synth.hyperplanes(12, d)
+    Xd = torch.from_numpy(X).cuda()
+    Hd = torch.from_numpy(H).cuda()
+    kw = workload_params(w)
+    R = w["R"]
+    adj = torch.empty((n, R), dtype=torch.int32, device="cuda")
+    deg = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    out = {"workload": name, "n": n, "d": d, "metric": "IP", "c_max": w["c_max"], "l_max": w["l_max"], "R": R,
+           "fanout": list(w["fanout"]), "modes": {}}
+    ref = None
+    for mode, eng, prec in PREC_MODES:
+        bp = pk.params(dtype=pk.PIPNN_F32, hyperplanes=Hd, prec=prec,
+                       leaf_engine=pk.PIPNN_LEAF_TC if eng == "tc" else pk.PIPNN_LEAF_SIMT, **kw)
+        for _ in range(warmup):
+            pk.pipnn_build_into(Xd, bp, synth.BUILD_SEED, adj, deg, metric=w["metric"])
+        torch.cuda.synchronize()
+        times, stats = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pk.pipnn_build_into(Xd, bp, synth.BUILD_SEED, adj, deg, metric=w["metric"])
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(pk.pipnn_get_stats())
+        a_np = adj.cpu().numpy().view(np.uint32)
+        d_np = deg.cpu().numpy().view(np.uint32)
+        if ref is None:
+            ref = (a_np.copy(), d_np.copy())
+            same = True
+        else:
+            same = bool(np.array_equal(a_np, ref[0]) and np.array_equal(d_np, ref[1]))
+        ms = statistics.mean(times)
+        st = stats[-1]
+        out["modes"][mode] = {"engine": eng, "ms_per_step": ms, "points_per_s": n / (ms / 1e3),
+                              "ms_leaf": statistics.mean(x["ms_leaf"] for x in stats),
+                              "ms_leaf_kernel": statistics.mean(x["ms_leaf_kernel"] for x in stats),
+                              "rows_evaluated_in_full": int(st["leaf_full_rows"]),
+                              "leaf_rows": int(st["leaf_members"]), "graph_equals_fp32": same}
+    # recall of the graph (every mode's graph is the FP32 one when graph_equals_fp32 holds)
+    gt = oracle.knn(X, Q, 10, metric=w["metric"])
+    start = oracle.medoid(X, metric=w["metric"])
+    out["recall_at_10"] = {str(L): oracle.recall(oracle.beam_search(X, ref[0], ref[1], Q, L, start=start,
+                                                                    metric=w["metric"])[0], gt) for L in RECALL_L}
+    out["recall_queries"] = int(Q.shape[0])
+    # leaf dissimilarity error against FP64 on a sample of the partition's leaves
+    bp = pk.params(dtype=pk.PIPNN_F32, hyperplanes=Hd, **kw)
+    off, mem, _ = pk.pipnn_partition(Xd, bp, synth.BUILD_SEED, metric=w["metric"])
+    off_h = off.view(torch.int64).cpu().numpy()
+    mem_h = mem.view(torch.int32).cpu().numpy().view(np.uint32)
+    pick = np.linspace(0, len(off_h) - 2, error_leaves).astype(np.int64)
+    sub_off = [0]
+    sub_mem = []
+    for b in pick:
+        sub_mem.append(mem_h[off_h[b]:off_h[b + 1]])
+        sub_off.append(sub_off[-1] + len(sub_mem[-1]))
+    sub_mem = np.concatenate(sub_mem).astype(np.uint32)
+    sub_off = np.array(sub_off, np.uint64)
+    D64, D32 = [], []
+    for b in range(len(pick)):
+        Xl = X[sub_mem[sub_off[b]:sub_off[b + 1]]]
+        G = Xl.astype(np.float64) @ Xl.astype(np.float64).T
+        D64.append(1.0 - G)
+        s_ = Xl.shape[0]
+        ii, jj = np.meshgrid(np.arange(s_), np.arange(s_), indexing="ij")
+        ids = sub_mem[sub_off[b]:sub_off[b + 1]]
+        D32.append(oracle.dissimilarity(X, ids[ii.ravel()], ids[jj.ravel()], metric=w["metric"]).reshape(s_, s_))
+
+    def err_stats(approx):
+        ab, rel = [], []
+        for b in range(len(pick)):
+            m_ = ~np.eye(D64[b].shape[0], dtype=bool)
+            e = np.abs(approx[b] - D64[b])[m_]
+            ab.append(e)
+            rel.append(e / np.maximum(np.abs(D64[b][m_]), 1e-12))
+        ab, rel = np.concatenate(ab), np.concatenate(rel)
+        return {"max_abs": float(ab.max()), "mean_abs": float(ab.mean()), "max_rel": float(rel.max()),
+                "mean_rel": float(rel.mean())}
+
+    errs = {"fp32": err_stats(D32)}
+    for mode, eng, prec in PREC_MODES[1:]:
+        g = pk.pipnn_leaf_gram(Xd, torch.from_numpy(sub_off).cuda(), torch.from_numpy(sub_mem).cuda(), prec,
+                               metric=w["metric"]).cpu().numpy()
+        blocks, at = [], 0
+        for b in range(len(pick)):
+            s_ = int(sub_off[b + 1] - sub_off[b])
+            blocks.append(g[at:at + s_ * s_].reshape(s_, s_).astype(np.float64))
+            at += s_ * s_
+        errs[mode] = err_stats(blocks)
+    out["distance_error_vs_fp64"] = errs
+    out["error_sample"] = f"{len(pick)} leaves of the partition, {int(sum(x.size for x in D64)):,} ordered pairs"
+    return out
+
+
 def run_reference(args, w):
     """Reference arm: the CPU oracle as it stands, on bounded samples of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -229,6 +344,8 @@ def main():
     ap.add_argument("--no-recall", action="store_true", help="skip the recall gate (oracle build + beam search)")
     ap.add_argument("--queries", type=int, default=None, help="queries of the recall gate (default: the workload's)")
     ap.add_argument("--profile", action="store_true", help="timed steps only (for profiler launch lists)")
+    ap.add_argument("--no-precision-modes", action="store_true",
+                    help="skip the float workload built at every leaf precision")
     args = ap.parse_args()
     w = dict(synth.WORKLOADS[WORKLOAD])
     if args.impl == "reference":
@@ -340,6 +457,8 @@ def main():
                 line["cpu_baseline"] = cpu
         elif world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(X, H, w)
+        if world == 1 and not args.no_precision_modes:
+            line["precision_modes"] = precision_modes(min(args.steps, 5), min(args.warmup, 2))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

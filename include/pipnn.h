@@ -79,8 +79,15 @@ enum { PIPNN_LEAF_SIMT = 0, PIPNN_LEAF_TC = 1 };
  *                   largest centred coordinate).
  *  PIPNN_PREC_INT8: byte data only; the exact integer Gram (the tensor-core engine holds u8 / i8
  *                   values exactly in BF16 with FP32 accumulation, exact for d <= 128).
+ *  PIPNN_PREC_BF16X3: float data on PIPNN_LEAF_TC: every centred coordinate split into a BF16
+ *                   high part and a BF16 remainder, and the Gram formed from three BF16 products
+ *                   (hi.hi + lo.hi + hi.lo) with FP32 accumulation: relative operand error about
+ *                   2^-16 instead of 2^-8, so the error band stays narrower than the gaps between
+ *                   a row's nearest neighbours even in leaves whose spread is far larger than
+ *                   those distances, where single BF16 or FP8 leave most rows to the full
+ *                   evaluation.
  * For byte data every precision is exact and they are interchangeable. */
-enum { PIPNN_PREC_FP32 = 0, PIPNN_PREC_BF16 = 1, PIPNN_PREC_FP8 = 2, PIPNN_PREC_INT8 = 3 };
+enum { PIPNN_PREC_FP32 = 0, PIPNN_PREC_BF16 = 1, PIPNN_PREC_FP8 = 2, PIPNN_PREC_INT8 = 3, PIPNN_PREC_BF16X3 = 4 };
 
 /* Hyper-parameters BP of Alg. 4. */
 typedef struct pipnn_params {
@@ -107,6 +114,13 @@ typedef struct pipnn_params {
                                seed + r * 0x9E3779B97F4A7C15 (mod 2^64), so replica 0 is the
                                single-replica build.                                          */
     int32_t prec;           /* PIPNN_PREC_*: operand precision of the tensor-core leaf Gram      */
+    uint64_t wave_members;  /* A2..A5 run in waves of consecutive leaves holding at most this many
+                               members (a larger leaf forms a wave of its own); each wave's
+                               candidates are merged into the reservoirs before the next wave's
+                               are formed, which bounds the candidate and staging memory.  By
+                               the history independence of Alg. 3 (Sec. 3) the graph does not
+                               depend on the split.  0: as many members as the free device
+                               memory holds (one wave whenever everything fits).              */
 } pipnn_params;
 
 /* Output graph: ids[v*R + j] for j < deg[v] are v's out-neighbours in prune order; the rest of
@@ -151,6 +165,11 @@ typedef struct pipnn_stats {
     uint64_t kernel_launches;    /* kernels this library launched during the build              */
     uint64_t leaf_full_rows;     /* reduced-precision leaf engine: rows whose error band did not
                                     fit the tracked candidates and were evaluated in full        */
+    uint32_t waves;              /* leaf / HashPrune waves of the build (summed over replicas)   */
+    uint32_t pad_;
+    uint64_t peak_device_bytes;  /* device memory in use (total minus free, so including memory
+                                    the allocators hold in reserve) at the fullest point the
+                                    build sampled: after the partition and inside every wave  */
 } pipnn_stats;
 
 /* Sets the CUDA stream (a cudaStream_t, or NULL for the default stream) used by later calls. */
@@ -180,12 +199,22 @@ void pipnn_leaves_free(pipnn_leaves *leaves);
  * members), the k nearest other members of every member by (dissimilarity, id), emitted in both
  * directions (Sec. 4.2, App. A.3): 2 * |b| * min(k, |b|-1) edges per leaf, in no particular
  * order.  engine: PIPNN_LEAF_SIMT or PIPNN_LEAF_TC; prec: PIPNN_PREC_* (float data on the
- * tensor cores needs BF16 or FP8; the edges are the same for every engine and precision).  Free
+ * tensor cores needs BF16, FP8 or BF16X3; the edges are the same for every engine and precision).  Free
  * the result with pipnn_edges_free. */
 int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
                     const uint64_t *offsets, const uint32_t *members, uint64_t num_leaves,
                     uint32_t k, int32_t engine, int32_t prec, pipnn_edges *out);
 void pipnn_edges_free(pipnn_edges *edges);
+
+/* The leaf dissimilarities as the reduced-precision tensor-core engine forms them (Sec. 4.2's
+ * leaf GEMM at BF16 or FP8 operands, before the exact re-rank), for error reports against FP64:
+ * for leaf b, gram[g_b + i |b| + j] = D~(members[off_b + i], members[off_b + j]) with
+ * g_b = sum over earlier leaves of |c|^2 (the diagonal included).  points: float32, n x d,
+ * device; offsets/members as for pipnn_leaf_pick; prec: PIPNN_PREC_BF16, _FP8 or _BF16X3;
+ * gram: caller-owned device buffer of sum |b|^2 floats.  The picks never use these values
+ * directly: every pick is re-ranked with the defining binary32 evaluation. */
+int pipnn_leaf_gram(const void *points, uint64_t n, uint32_t d, int32_t metric, const uint64_t *offsets,
+                    const uint32_t *members, uint64_t num_leaves, int32_t prec, float *gram);
 
 /* A5 -- Alg. 3 HashPrune of a candidate stream into the reservoirs of n nodes.
  * dst/src/dist: `count` candidates, device.  sketch: n x m float32 device (from pipnn_sketch).

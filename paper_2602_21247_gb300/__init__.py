@@ -26,13 +26,14 @@ LIB_PATH = os.path.join(PKG, "libpipnn.so")
 PIPNN_F32, PIPNN_U8, PIPNN_I8 = 0, 1, 2
 PIPNN_L2, PIPNN_IP = 0, 1
 PIPNN_LEAF_SIMT, PIPNN_LEAF_TC = 0, 1
-PIPNN_PREC_FP32, PIPNN_PREC_BF16, PIPNN_PREC_FP8, PIPNN_PREC_INT8 = 0, 1, 2, 3
+PIPNN_PREC_FP32, PIPNN_PREC_BF16, PIPNN_PREC_FP8, PIPNN_PREC_INT8, PIPNN_PREC_BF16X3 = 0, 1, 2, 3, 4
 PIPNN_OK = 0
 
 # symbols declared in include/pipnn.h
 EXPORTS = ("pipnn_set_stream", "pipnn_last_error", "pipnn_sketch", "pipnn_partition", "pipnn_leaves_free",
            "pipnn_leaf_pick", "pipnn_edges_free", "pipnn_hashprune", "pipnn_final_prune", "pipnn_build",
-           "pipnn_free", "pipnn_build_into", "pipnn_get_stats", "pipnn_hashprune_noalloc", "pipnn_build_batched")
+           "pipnn_free", "pipnn_build_into", "pipnn_get_stats", "pipnn_hashprune_noalloc", "pipnn_build_batched",
+           "pipnn_leaf_gram")
 
 
 class PipnnError(RuntimeError):
@@ -47,7 +48,7 @@ class pipnn_params(C.Structure):
                 ("leaf_k", C.c_uint32), ("hash_bits", C.c_uint32), ("l_max", C.c_uint32),
                 ("R", C.c_uint32), ("alpha", C.c_float), ("final_prune", C.c_int32),
                 ("dtype", C.c_int32), ("leaf_engine", C.c_int32), ("hyperplanes", C.c_void_p),
-                ("replicas", C.c_uint32), ("prec", C.c_int32)]
+                ("replicas", C.c_uint32), ("prec", C.c_int32), ("wave_members", C.c_uint64)]
 
 
 class pipnn_graph(C.Structure):
@@ -70,7 +71,8 @@ class pipnn_stats(C.Structure):
                 ("ms_leaf_kernel", C.c_float), ("leaf_kernel_launches", C.c_uint32), ("levels", C.c_uint32),
                 ("leaves", C.c_uint64), ("leaf_members", C.c_uint64), ("candidates", C.c_uint64),
                 ("leaf_pairs", C.c_double), ("leaf_pairs_executed", C.c_double),
-                ("kernel_launches", C.c_uint64), ("leaf_full_rows", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("leaf_full_rows", C.c_uint64), ("waves", C.c_uint32),
+                ("pad_", C.c_uint32), ("peak_device_bytes", C.c_uint64)]
 
 
 _lib = None
@@ -91,6 +93,7 @@ def lib():
         L.pipnn_leaves_free.argtypes = [C.POINTER(pipnn_leaves)]
         L.pipnn_leaves_free.restype = None
         L.pipnn_leaf_pick.argtypes = [vp, u64, u32, i32, i32, vp, vp, u64, u32, i32, i32, C.POINTER(pipnn_edges)]
+        L.pipnn_leaf_gram.argtypes = [vp, u64, u32, i32, vp, vp, u64, i32, vp]
         L.pipnn_edges_free.argtypes = [C.POINTER(pipnn_edges)]
         L.pipnn_edges_free.restype = None
         L.pipnn_hashprune.argtypes = [vp, vp, vp, u64, vp, u32, u64, u32, vp, vp]
@@ -150,7 +153,7 @@ def _take(ptr, count, typestr, view=None):
 
 def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.005, fanout=(2,), leaf_k=2,
            hash_bits=12, l_max=64, R=64, alpha=1.2, final_prune=True, leaf_engine=PIPNN_LEAF_SIMT,
-           hyperplanes=None, replicas=1, prec=PIPNN_PREC_FP32) -> pipnn_params:
+           hyperplanes=None, replicas=1, prec=PIPNN_PREC_FP32, wave_members=0) -> pipnn_params:
     """BP of Alg. 4.  `hyperplanes` (hash_bits x d float32, numpy or torch) must stay alive for the call."""
     p = pipnn_params()
     p.c_max = c_max
@@ -171,6 +174,7 @@ def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.0
     p.hyperplanes = _ptr(hyperplanes)
     p.replicas = replicas
     p.prec = prec
+    p.wave_members = wave_members
     p._keep = hyperplanes
     return p
 
@@ -226,6 +230,20 @@ def pipnn_leaf_pick(points: torch.Tensor, offsets: torch.Tensor, members: torch.
     finally:
         lib().pipnn_edges_free(C.byref(out))
     return dst, src, dist
+
+
+def pipnn_leaf_gram(points: torch.Tensor, offsets: torch.Tensor, members: torch.Tensor, prec, metric=PIPNN_L2):
+    """The reduced-precision engine's leaf dissimilarities before the re-rank: a flat float32
+    tensor holding every leaf's |b| x |b| block in leaf order."""
+    n, d = points.shape
+    o = offsets.view(torch.int64) if offsets.dtype == torch.uint64 else offsets.to(torch.int64)
+    sizes = o[1:] - o[:-1]
+    total = int((sizes * sizes).sum())
+    gram = torch.empty(max(total, 1), dtype=torch.float32, device=points.device)
+    pipnn_set_stream()
+    _check(lib().pipnn_leaf_gram(_ptr(points), n, d, metric, _ptr(offsets), _ptr(members), offsets.numel() - 1, prec,
+                                 _ptr(gram)))
+    return gram[:total]
 
 
 def pipnn_hashprune(dst, src, dist, sketch, n, l_max, reservoir=None, count=None):

@@ -24,6 +24,8 @@ int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, co
                 uint32_t *adj, uint32_t *deg);
 int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, uint32_t *adj,
                     uint32_t *deg);
+int leaf_gram_tcf(const float *X, uint32_t d, int metric, int prec, const uint64_t *off, const uint32_t *mem,
+                  uint64_t L, float *gram, Workspace &ws);
 
 namespace {
 thread_local pipnn_stats g_stats;
@@ -86,7 +88,7 @@ int check_params(const pipnn_params *bp) {
         return set_error(PIPNN_EINVAL, "unknown leaf_engine %d", bp->leaf_engine);
     if (!bp->hyperplanes) return set_error(PIPNN_EINVAL, "hyperplanes is NULL");
     if (bp->replicas > 16) return set_error(PIPNN_EINVAL, "replicas above 16");
-    if (bp->prec < PIPNN_PREC_FP32 || bp->prec > PIPNN_PREC_INT8) return set_error(PIPNN_EINVAL, "unknown prec %d", bp->prec);
+    if (bp->prec < PIPNN_PREC_FP32 || bp->prec > PIPNN_PREC_BF16X3) return set_error(PIPNN_EINVAL, "unknown prec %d", bp->prec);
     if (bp->dtype == PIPNN_F32 && bp->prec == PIPNN_PREC_INT8)
         return set_error(PIPNN_EUNSUPPORTED, "PIPNN_PREC_INT8 takes byte data");
     return PIPNN_OK;
@@ -121,6 +123,60 @@ __global__ void leaf_pairs_kernel(const uint64_t *off, uint64_t L, unsigned long
     atomicAdd(acc, local);
 }
 
+__global__ void rebase_offsets(const uint64_t *off, uint64_t count, uint64_t *out) {
+    const uint64_t base = off[0];
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = off[i] - base;
+}
+
+int leaf_offsets_to_host(const uint64_t *off, uint64_t L, std::vector<uint64_t> *h) {
+    h->assign(L + 1, 0);
+    PIPNN_CUDA(cudaMemcpyAsync(h->data(), off, (L + 1) * 8, cudaMemcpyDeviceToHost, stream()));
+    PIPNN_CUDA(cudaStreamSynchronize(stream()));
+    return PIPNN_OK;
+}
+
+// Device memory in use now (total minus free, so including what the allocators hold in reserve),
+// kept as the build's peak.
+void note_peak(pipnn_stats *st) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const uint64_t used = (uint64_t)(tot - fr);
+    if (used > st->peak_device_bytes) st->peak_device_bytes = used;
+}
+
+// Leaf members one wave may hold: the free device memory (less the per-node HashPrune arrays and
+// a reserve) divided by a member's share of the leaf step (staged operand row, member and key
+// arrays, candidate edges, grouped HashPrune slots), capped below the tensor maps' 2^31 rows.
+uint64_t auto_wave_members(uint64_t n, uint32_t d, int dtype, const pipnn_params *bp) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 1ull << 26;
+    }
+    // memory the stream-ordered pool holds but no allocation uses is available too
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t reserved = 0, used = 0;
+        if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+            fr += (size_t)(reserved - used);
+    }
+    cudaGetLastError();
+    const uint64_t kp = ((uint64_t)d + 63) / 64 * 64;
+    const uint64_t per_member = kp * 2 + 64 + (uint64_t)bp->leaf_k * 2 * (12 + 8) * 2;
+    const uint64_t reserve = (2ull << 30) + 24 * n;
+    (void)dtype;
+    uint64_t w = fr > reserve ? (fr - reserve) / per_member : (1ull << 20);
+    if (w < (1ull << 20)) w = 1ull << 20;
+    if (w > 0x7FF00000ull) w = 0x7FF00000ull;
+    return w;
+}
+
 // Keeps freed stream-ordered allocations in the device's default pool (the build allocates and
 // frees the same large buffers every call).
 void keep_pool_memory() {
@@ -146,8 +202,8 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     const int dtype = bp->dtype;
     PIPNN_TRY(check_points(points, n, d, dtype, metric));
     if (bp->leaf_engine == PIPNN_LEAF_TC && dtype == PIPNN_F32 && bp->prec != PIPNN_PREC_BF16 &&
-        bp->prec != PIPNN_PREC_FP8)
-        return set_error(PIPNN_EUNSUPPORTED, "float data on the tensor-core leaf engine needs prec BF16 or FP8");
+        bp->prec != PIPNN_PREC_FP8 && bp->prec != PIPNN_PREC_BF16X3)
+        return set_error(PIPNN_EUNSUPPORTED, "float data on the tensor-core leaf engine needs prec BF16, FP8 or BF16X3");
     CallScope cs;
     PIPNN_TRY(cs.init());
     Workspace &ws = cs.ws;
@@ -209,23 +265,8 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
                                                                                            leaves.num_leaves, acc);
         }
 
-        // A2 .. A4
-        pipnn_edges edges;
-        float leaf_ms = 0.0f;
-        uint32_t leaf_launches = 0;
-        uint64_t full_rows = 0;
-        int rc = leaf_pick(X, n, d, dtype, metric, sqn_bytes, leaves.offsets, leaves.members, leaves.num_leaves,
-                           bp->leaf_k, bp->leaf_engine, bp->prec, &edges, &leaf_ms, &leaf_launches, &full_rows);
-        st.leaf_full_rows += full_rows;
-        dev_free_raw(leaves.offsets);
-        dev_free_raw(leaves.members);
-        if (rc != PIPNN_OK) return rc;
-        rt[r].mark(2);
-        st.ms_leaf_kernel += leaf_ms;
-        st.leaf_kernel_launches += leaf_launches;
-        st.candidates += edges.count;
-
-        // A5
+        // A5's reservoirs (once, for every replica and wave)
+        int rc = PIPNN_OK;
         if (r == 0) {
             rc = ws.alloc(&res, n * bp->l_max);
             if (rc == PIPNN_OK) rc = ws.zeros(&cnt, n);
@@ -234,13 +275,65 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
                 if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "memset: %s", cudaGetErrorString(e));
             }
         }
-        if (rc == PIPNN_OK)
-            rc = hashprune_merge(edges.dst, edges.src, edges.dist, edges.count, S, m, n, bp->l_max, res, cnt);
-        dev_free_raw(edges.dst);
-        dev_free_raw(edges.src);
-        dev_free_raw(edges.dist);
+        // A2 .. A5 in waves of consecutive leaves: every wave's candidates are merged into the
+        // reservoirs before the next wave's are formed (Alg. 3's history independence makes the
+        // result independent of the split)
+        std::vector<uint64_t> hoff;
+        uint64_t W = 0;
+        if (rc == PIPNN_OK) rc = leaf_offsets_to_host(leaves.offsets, leaves.num_leaves, &hoff);
+        if (rc == PIPNN_OK) {
+            note_peak(&st);
+            W = bp->wave_members ? bp->wave_members : auto_wave_members(n, d, dtype, bp);
+        }
+        for (uint64_t b0 = 0; rc == PIPNN_OK && b0 < leaves.num_leaves;) {
+            uint64_t b1 = b0 + 1;
+            while (b1 < leaves.num_leaves && hoff[b1 + 1] - hoff[b0] <= W) b1++;
+            const uint64_t Lw = b1 - b0;
+            Timer wt;
+            rc = wt.init();
+            uint64_t *off_w = nullptr;
+            Workspace wave_ws;
+            if (rc == PIPNN_OK) rc = wave_ws.alloc(&off_w, Lw + 1);
+            if (rc == PIPNN_OK) {
+                wt.mark(0);
+                rebase_offsets<<<grid_for(Lw + 1, 256), 256, 0, stream()>>>(leaves.offsets + b0, Lw + 1, off_w);
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "rebase: %s", cudaGetErrorString(e));
+                count_launch();
+            }
+            pipnn_edges edges{};
+            if (rc == PIPNN_OK) {
+                float leaf_ms = 0.0f;
+                uint32_t leaf_launches = 0;
+                uint64_t full_rows = 0;
+                rc = leaf_pick(X, n, d, dtype, metric, sqn_bytes, off_w, leaves.members + hoff[b0], Lw, bp->leaf_k,
+                               bp->leaf_engine, bp->prec, &edges, &leaf_ms, &leaf_launches, &full_rows);
+                st.leaf_full_rows += full_rows;
+                st.ms_leaf_kernel += leaf_ms;
+                st.leaf_kernel_launches += leaf_launches;
+                st.candidates += edges.count;
+                wt.mark(1);
+            }
+            if (rc == PIPNN_OK) {
+                note_peak(&st);
+                rc = hashprune_merge(edges.dst, edges.src, edges.dist, edges.count, S, m, n, bp->l_max, res, cnt);
+                wt.mark(2);
+            }
+            dev_free_raw(edges.dst);
+            dev_free_raw(edges.src);
+            dev_free_raw(edges.dist);
+            if (rc == PIPNN_OK) {
+                cudaStreamSynchronize(stream());
+                st.ms_leaf += wt.ms(0, 1);
+                st.ms_hashprune += wt.ms(1, 2);
+                st.waves++;
+            }
+            b0 = b1;
+        }
+        dev_free_raw(leaves.offsets);
+        dev_free_raw(leaves.members);
         if (rc != PIPNN_OK) return rc;
-        rt[r].mark(3);
+        rt[r].mark(2);
     }
     unsigned long long leaf_pairs = 0;
     PIPNN_CUDA(cudaMemcpyAsync(&leaf_pairs, acc, 8, cudaMemcpyDeviceToHost, stream()));
@@ -305,11 +398,7 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     tm.mark(6);
     cudaStreamSynchronize(stream());
     st.ms_sketch = tm.ms(0, 1);
-    for (auto &t : rt) {
-        st.ms_partition += t.ms(0, 1);
-        st.ms_leaf += t.ms(1, 2);
-        st.ms_hashprune += t.ms(2, 3);
-    }
+    for (auto &t : rt) st.ms_partition += t.ms(0, 1);
     st.ms_prune = tm.ms(4, 5);
     st.leaf_pairs = (double)leaf_pairs;
     st.leaf_pairs_executed = st.leaf_pairs + (double)st.leaf_members;
@@ -373,9 +462,20 @@ int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, i
     if (!offsets || (!members && num_leaves)) return set_error(PIPNN_EINVAL, "offsets/members are NULL");
     if (k < 1 || k > 16) return set_error(PIPNN_EINVAL, "k outside 1..16");
     if (engine != PIPNN_LEAF_SIMT && engine != PIPNN_LEAF_TC) return set_error(PIPNN_EINVAL, "unknown engine");
-    if (prec < PIPNN_PREC_FP32 || prec > PIPNN_PREC_INT8) return set_error(PIPNN_EINVAL, "unknown prec %d", prec);
+    if (prec < PIPNN_PREC_FP32 || prec > PIPNN_PREC_BF16X3) return set_error(PIPNN_EINVAL, "unknown prec %d", prec);
     return leaf_pick(points, n, d, dtype, metric, nullptr, offsets, members, num_leaves, k, engine, prec, out, nullptr,
                      nullptr, nullptr);
+}
+
+int pipnn_leaf_gram(const void *points, uint64_t n, uint32_t d, int32_t metric, const uint64_t *offsets,
+                    const uint32_t *members, uint64_t num_leaves, int32_t prec, float *gram) {
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    PIPNN_TRY(check_points(points, n, d, PIPNN_F32, metric));
+    if (!offsets || !gram || (!members && num_leaves)) return set_error(PIPNN_EINVAL, "offsets/members/gram are NULL");
+    PIPNN_TRY(leaf_gram_tcf(static_cast<const float *>(points), d, metric, prec, offsets, members, num_leaves, gram,
+                            cs.ws));
+    return check_device_error("leaf gram");
 }
 
 void pipnn_edges_free(pipnn_edges *e) {

@@ -42,8 +42,9 @@ int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, cons
               const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, int prec,
               pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows) {
     if (full_rows) *full_rows = 0;
-    if (engine == PIPNN_LEAF_TC && dtype == PIPNN_F32 && prec != PIPNN_PREC_BF16 && prec != PIPNN_PREC_FP8)
-        return set_error(PIPNN_EUNSUPPORTED, "float data on the tensor-core leaf engine needs prec BF16 or FP8");
+    if (engine == PIPNN_LEAF_TC && dtype == PIPNN_F32 && prec != PIPNN_PREC_BF16 && prec != PIPNN_PREC_FP8 &&
+        prec != PIPNN_PREC_BF16X3)
+        return set_error(PIPNN_EUNSUPPORTED, "float data on the tensor-core leaf engine needs prec BF16, FP8 or BF16X3");
     memset(out, 0, sizeof(*out));
     Workspace ws;
     const int32_t *sqn = sqnorm_bytes;

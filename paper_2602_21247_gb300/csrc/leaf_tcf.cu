@@ -40,6 +40,7 @@
 // than 2^(CB-23) of its value, which the threshold adds as well.
 #include <cuda_fp8.h>
 
+#include "allpairs.cuh"
 #include "tc_common.cuh"
 
 namespace pipnn {
@@ -48,7 +49,7 @@ namespace {
 
 using namespace tc;
 
-enum : int { PREC_BF16 = PIPNN_PREC_BF16, PREC_FP8 = PIPNN_PREC_FP8 };
+enum : int { PREC_BF16 = PIPNN_PREC_BF16, PREC_FP8 = PIPNN_PREC_FP8, PREC_SPLIT = PIPNN_PREC_BF16X3 };
 
 struct LeafInfoF {
     float R;      // max over the leaf of |x'_j| (rounded up)
@@ -86,29 +87,43 @@ struct TcfArgs {
     uint8_t *ccnt;             // candidates per member row; 0xFF: full evaluation
     uint32_t *ovf;             // (unit << 7 | row) of rows that need a full evaluation
     unsigned *novf;
+    unsigned *leaf_ovf;        // rows of every leaf that need a full evaluation
     unsigned *err;
+    float *gram;               // dump mode: the approximate dissimilarities, leaf by leaf
+    const uint64_t *gram_off;  // dump mode: first entry of every leaf's |b| x |b| block
 };
 
+// KB: 128-byte K blocks of one operand (for the split form: of each of its hi and lo halves).
 template <int PREC, int KB, int KP>
 struct TcfCfg {
+    static constexpr bool SPLIT = PREC == PREC_SPLIT;
     static constexpr int NMAX = 128;
-    static constexpr int S = PREC == PREC_FP8 ? 4 : 3;  // B stages
-    static constexpr int T = 4;                         // accumulator buffers
+    static constexpr int KBA = SPLIT ? 2 * KB : KB;    // K blocks of an A tile (hi then lo)
+    static constexpr int KBB = KB;                     // K blocks of one B job (hi or lo half)
+    static constexpr int JPT = SPLIT ? 2 : 1;          // B jobs per 128-column tile
+    static constexpr int S = SPLIT ? (KB == 2 ? 2 : 4) : (PREC == PREC_FP8 ? 4 : 3);  // B stages
+    static constexpr int T = 4;                        // accumulator buffers
     static constexpr int REGION = tc::REGION;
+    // norm slices (32 bytes per row each, four per 128-byte row): A buffer x uses slice x of the
+    // AN region; B stage x slice BSLICE0 + x of the BN region, which is the AN region itself when
+    // the operand tiles leave no room for a second one
+    static constexpr bool MERGED = SPLIT && KB == 2;
+    static constexpr int BSLICE0 = MERGED ? 2 : 0;
     static constexpr int OFF_A0 = 0;
-    static constexpr int OFF_AN = OFF_A0 + 2 * KB * REGION;
+    static constexpr int OFF_AN = OFF_A0 + 2 * KBA * REGION;
     static constexpr int OFF_B0 = OFF_AN + REGION;
-    static constexpr int OFF_BN = OFF_B0 + S * KB * REGION;
-    static constexpr int OFF_MV = OFF_BN + REGION;                  // 2 x 128 rows x KP keys
+    static constexpr int OFF_BN = MERGED ? OFF_AN : OFF_B0 + S * KBB * REGION;
+    static constexpr int OFF_MV = (MERGED ? OFF_B0 + S * KBB * REGION : OFF_BN + REGION);  // 2 x 128 x KP keys
     static constexpr int OFF_BAR = OFF_MV + 2 * ROWS * KP * 4;
     static constexpr int BAR_FULL_A = 0, BAR_EMPTY_A = 2, BAR_FULL = 4, BAR_EMPTY = BAR_FULL + S,
-                         BAR_TFULL = BAR_EMPTY + S, BAR_TEMPTY = BAR_TFULL + T, NBAR = BAR_TEMPTY + T;
+                         BAR_TFULL = BAR_EMPTY + S, BAR_TEMPTY = BAR_TFULL + T, BAR_DRAIN = BAR_TEMPTY + T,
+                         NBAR = BAR_DRAIN + 1;
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr int BYTES = OFF_MISC + 16;
     static constexpr int SMEM = BYTES + 1024;
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(T * NMAX <= (int)TMEM_COLS, "TMEM budget");
-    static_assert(S <= 4, "norm slices per 128-byte row");
+    static_assert(BSLICE0 + S <= 4, "norm slices per 128-byte row");
 };
 
 // Keeps K[0] < K[1] < ... < K[KP-1], the KP smallest keys seen (keys are unique).
@@ -136,7 +151,9 @@ __device__ __forceinline__ float band_key(const BandCoef &c, int metric, float r
     return c.safety * e * sigma;
 }
 
-template <int PREC, int KB, int KP>
+// DUMP: instead of ranking, every row writes its approximate dissimilarities (the accumulator
+// converted back to D units, before any re-rank) to a.gram.
+template <int PREC, int KB, int KP, bool DUMP>
 __global__ void __launch_bounds__(THREADS, 1)
     leaf_gram_tcf(const __grid_constant__ CUtensorMap map, const TcfArgs a, uint32_t nunits, uint32_t ksteps) {
     using C = TcfCfg<PREC, KB, KP>;
@@ -162,6 +179,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(bar(C::BAR_TFULL + i), 1);
             mbar_init(bar(C::BAR_TEMPTY + i), EPI_WARPS * 32);
         }
+        mbar_init(bar(C::BAR_DRAIN), 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async();
@@ -177,25 +195,31 @@ __global__ void __launch_bounds__(THREADS, 1)
         // norm slices: A buffer x = [1,1,1,1, a-pieces, 0 x 8], B stage x = [b-pieces, 1,1,1,1, 0 x 8]
         for (uint32_t r = lane; r < (uint32_t)ROWS; r += 32) {
             const uint32_t one2 = 0x3F803F80u;
-            for (uint32_t q = 0; q < 4; q++) {
-                const bool lo = (q & 1) == 0;
+            for (uint32_t q = 0; q < 8; q++) {
+                const bool first = (q & 1) == 0;
+                const bool b_type = C::MERGED && (q >> 1) >= 2;
                 asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + C::OFF_AN + r * 128 +
                                                                               ((q ^ (r & 7)) << 4)),
-                             "r"(lo ? one2 : 0u), "r"(lo ? one2 : 0u), "r"(0u), "r"(0u)
+                             "r"(first && !b_type ? one2 : 0u), "r"(first && !b_type ? one2 : 0u),
+                             "r"(first && b_type ? one2 : 0u), "r"(first && b_type ? one2 : 0u)
                              : "memory");
             }
-            for (uint32_t q = 0; q < 2u * C::S; q++) {
-                const bool lo = (q & 1) == 0;
-                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + C::OFF_BN + r * 128 +
-                                                                              ((q ^ (r & 7)) << 4)),
-                             "r"(0u), "r"(0u), "r"(lo ? one2 : 0u), "r"(lo ? one2 : 0u)
-                             : "memory");
+            if (!C::MERGED) {
+                for (uint32_t q = 0; q < 8; q++) {
+                    const bool first = (q & 1) == 0;
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(sbase + C::OFF_BN + r * 128 +
+                                                                                  ((q ^ (r & 7)) << 4)),
+                                 "r"(0u), "r"(0u), "r"(first ? one2 : 0u), "r"(first ? one2 : 0u)
+                                 : "memory");
+                }
             }
         }
         fence_proxy_async();
+        // job stream: per unit one A job, then per 128-column tile one B job (two for the split
+        // form: its hi half, which carries the column norms, then its lo half)
         struct Job {
             uint32_t kind;  // 0 A, 1 B, 2 end
-            uint32_t i, u, t, s, first;
+            uint32_t i, u, t, s, first, h;
             uint64_t off;
         };
         auto unit_job = [&](uint32_t i, uint32_t u) {
@@ -209,6 +233,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             q.i = i;
             q.u = u;
             q.t = 0;
+            q.h = 0;
             q.s = un.s;
             q.first = un.row0;
             q.off = un.off;
@@ -219,12 +244,18 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (c.kind == 0) {
                 q.kind = 1;
                 q.t = 0;
+                q.h = 0;
                 q.first = 0;
+                return q;
+            }
+            if (C::SPLIT && c.h == 0) {
+                q.h = 1;
                 return q;
             }
             const uint32_t nct = (c.s + C::NMAX - 1) / C::NMAX;
             if (c.t + 1 < nct) {
                 q.t = c.t + 1;
+                q.h = 0;
                 q.first = q.t * C::NMAX;
                 return q;
             }
@@ -234,7 +265,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int e = 0; e < 4; e++) {
                 const uint32_t r = q.first + 4 * lane + e;
-                nr[e] = (q.kind <= 1 && r < q.s) ? a.pieces[q.off + r] : make_uint2(0u, 0u);
+                nr[e] = (q.kind <= 1 && q.h == 0 && r < q.s) ? a.pieces[q.off + r] : make_uint2(0u, 0u);
             }
         };
         // TMA x coordinate of K block kb: 64 BF16 elements or 128 e4m3 bytes
@@ -263,10 +294,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                     fence_proxy_async();
                     const uint32_t fb = bar(C::BAR_FULL_A + ua);
                     if (lane == 0) {
-                        mbar_arrive_tx(fb, KB * C::REGION);
-                        const uint32_t dst = sbase + C::OFF_A0 + ua * KB * C::REGION;
+                        mbar_arrive_tx(fb, C::KBA * C::REGION);
+                        const uint32_t dst = sbase + C::OFF_A0 + ua * C::KBA * C::REGION;
 #pragma unroll
-                        for (int kb = 0; kb < KB; kb++)
+                        for (int kb = 0; kb < C::KBA; kb++)
                             tma_load_tile(dst + kb * C::REGION, &map, kb * XSTEP, (int32_t)(cur.off + cur.first), fb);
                     } else {
                         mbar_arrive(fb);
@@ -275,12 +306,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             } else {
                 const uint32_t st = j % C::S;
                 ok = mbar_wait(bar(C::BAR_EMPTY + st), ((j / C::S) & 1) ^ 1, abort, a.err);
-                if (ok) {
+                if (ok && cur.h == 0) {
+                    const uint32_t sl = C::BSLICE0 + st;
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
                         const uint32_t r = 4 * lane + e;
                         asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(sbase + C::OFF_BN + r * 128 +
-                                                                             (((2 * st) ^ (r & 7)) << 4)),
+                                                                             (((2 * sl) ^ (r & 7)) << 4)),
                                      "r"(nr[e].x), "r"(nr[e].y)
                                      : "memory");
                     }
@@ -290,11 +322,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (ok) {
                     const uint32_t fb = bar(C::BAR_FULL + st);
                     if (lane == 0) {
-                        mbar_arrive_tx(fb, KB * C::REGION);
-                        const uint32_t dst = sbase + C::OFF_B0 + st * KB * C::REGION;
+                        mbar_arrive_tx(fb, C::KBB * C::REGION);
+                        const uint32_t dst = sbase + C::OFF_B0 + st * C::KBB * C::REGION;
 #pragma unroll
-                        for (int kb = 0; kb < KB; kb++)
-                            tma_load_tile(dst + kb * C::REGION, &map, kb * XSTEP, (int32_t)(cur.off + cur.first), fb);
+                        for (int kb = 0; kb < C::KBB; kb++)
+                            tma_load_tile(dst + kb * C::REGION, &map, (cur.h * KB + kb) * XSTEP,
+                                          (int32_t)(cur.off + cur.first), fb);
                     } else {
                         mbar_arrive(fb);
                     }
@@ -308,18 +341,30 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
+        // B job jb (one stage load) uses stage jb % S; tile j uses accumulator buffer j % T.  The
+        // split form issues hi.hi and lo.hi and the norm step on the tile's hi job, hi.lo on its
+        // lo job.
         if (lane == 0) {
-            uint32_t j = 0, issued_j = 0;
+            uint32_t j = 0, jb = 0, issued_j = 0;
             bool any = false, stop = false;
+            auto products = [&](uint32_t d, uint32_t aB, uint32_t bB, uint32_t nn, bool first) {
+                for (uint32_t kk = 0; kk < ksteps; kk++) {
+                    const uint64_t ad = smem_desc_sw128(aB + (kk >> 2) * C::REGION + (kk & 3) * 32);
+                    const uint64_t bd = smem_desc_sw128(bB + (kk >> 2) * C::REGION + (kk & 3) * 32);
+                    const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                    if (PREC == PREC_FP8) mma_e4m3(d, ad, bd, idesc_e4m3(128, nn), acc);
+                    else mma_bf16(d, ad, bd, idesc_bf16(128, nn), acc);
+                }
+            };
             for (uint32_t i = 0, u = blockIdx.x; u < nunits && !stop; i++, u += gridDim.x) {
                 const uint32_t s = a.units[u].s;
                 const uint32_t ua = i & 1;
                 if (!mbar_wait(bar(C::BAR_FULL_A + ua), (i >> 1) & 1, abort, a.err)) break;
-                const uint32_t aB = sbase + C::OFF_A0 + ua * KB * C::REGION;
+                const uint32_t aB = sbase + C::OFF_A0 + ua * C::KBA * C::REGION;
                 const uint32_t nct = (s + C::NMAX - 1) / C::NMAX;
                 for (uint32_t t = 0; t < nct; t++, j++) {
-                    const uint32_t st = j % C::S, tb = j % C::T;
-                    if (!mbar_wait(bar(C::BAR_FULL + st), (j / C::S) & 1, abort, a.err) ||
+                    const uint32_t st = jb % C::S, tb = j % C::T;
+                    if (!mbar_wait(bar(C::BAR_FULL + st), (jb / C::S) & 1, abort, a.err) ||
                         !mbar_wait(bar(C::BAR_TEMPTY + tb), ((j / C::T) & 1) ^ 1, abort, a.err)) {
                         stop = true;
                         break;
@@ -328,26 +373,43 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const uint32_t c0 = t * C::NMAX;
                     const uint32_t ncols = s - c0 < (uint32_t)C::NMAX ? s - c0 : C::NMAX;
                     const uint32_t nn = (ncols + 15) & ~15u;
-                    const uint32_t bB = sbase + C::OFF_B0 + st * KB * C::REGION;
+                    const uint32_t bB = sbase + C::OFF_B0 + st * C::KBB * C::REGION;
                     const uint32_t d = tmem + tb * C::NMAX;
-                    for (uint32_t kk = 0; kk < ksteps; kk++) {
-                        const uint64_t ad = smem_desc_sw128(aB + (kk >> 2) * C::REGION + (kk & 3) * 32);
-                        const uint64_t bd = smem_desc_sw128(bB + (kk >> 2) * C::REGION + (kk & 3) * 32);
-                        if (PREC == PREC_FP8) mma_e4m3(d, ad, bd, idesc_e4m3(128, nn), kk > 0 ? 1u : 0u);
-                        else mma_bf16(d, ad, bd, idesc_bf16(128, nn), kk > 0 ? 1u : 0u);
-                    }
+                    products(d, aB, bB, nn, true);                                   // hi . hi
+                    if (C::SPLIT) products(d, aB + KB * C::REGION, bB, nn, false);    // lo . hi
                     // - v_i - v_j from the BF16 norm slices of this A buffer and this B stage
                     mma_bf16(d, smem_desc_sw128(sbase + C::OFF_AN + ua * 32),
-                             smem_desc_sw128(sbase + C::OFF_BN + st * 32), idesc_bf16(128, nn), 1u);
+                             smem_desc_sw128(sbase + C::OFF_BN + (C::BSLICE0 + st) * 32), idesc_bf16(128, nn), 1u);
                     mma_commit(bar(C::BAR_EMPTY + st));
+                    jb++;
+                    if (C::SPLIT) {
+                        const uint32_t st2 = jb % C::S;
+                        if (!mbar_wait(bar(C::BAR_FULL + st2), (jb / C::S) & 1, abort, a.err)) {
+                            stop = true;
+                            any = true;
+                            issued_j = j;
+                            break;
+                        }
+                        fence_after();
+                        products(d, aB, sbase + C::OFF_B0 + st2 * C::KBB * C::REGION, nn, false);  // hi . lo
+                        mma_commit(bar(C::BAR_EMPTY + st2));
+                        jb++;
+                    }
                     mma_commit(bar(C::BAR_TFULL + tb));
                     any = true;
                     issued_j = j;
                 }
                 if (!stop) mma_commit(bar(C::BAR_EMPTY_A + ua));
             }
-            if (stop && any)
-                mbar_wait(bar(C::BAR_TFULL + issued_j % C::T), (issued_j / C::T) & 1, abort, a.err);
+            if (stop && any) {
+                // let the MMAs already issued complete before TMEM is released: a commit to a
+                // barrier of its own, waited for with a time bound only (the abort flag is set)
+                (void)issued_j;
+                mma_commit(bar(C::BAR_DRAIN));
+                const unsigned long long t0 = globaltimer();
+                while (!mbar_try_wait(bar(C::BAR_DRAIN), 0) && globaltimer() - t0 < WAIT_NS) {
+                }
+            }
         }
         __syncwarp();
     } else {
@@ -368,7 +430,25 @@ __global__ void __launch_bounds__(THREADS, 1)
             fence_after();
             return ok;
         };
+        uint32_t u = blockIdx.x, i = 0, j = 0, t = 0;
+        TcUnitF un = a.units[u];
+        TcUnitF unx = a.units[u + gridDim.x < nunits ? u + gridDim.x : u];
         auto rank_chunk = [&](uint32_t (&g)[32], uint32_t base, uint32_t s, uint32_t self_col, uint32_t (&K)[KP]) {
+            if constexpr (DUMP) {
+                // self_col is this row's leaf column; rows past the leaf write nothing
+                if (self_col >= s) return;
+                const LeafInfoF li = a.info[un.leaf];
+                const float sigma = (a.metric == PIPNN_L2 ? 0.5f : 1.0f) * li.scale * li.scale;
+                float *row = a.gram + a.gram_off[un.leaf] + (uint64_t)self_col * s;
+#pragma unroll
+                for (int jj = 0; jj < 32; jj++) {
+                    if (base + jj < s) {
+                        const float D = __fdiv_rn(-__uint_as_float(g[jj]), sigma);
+                        row[base + jj] = a.metric == PIPNN_L2 ? D : __fsub_rn(D, li.P);
+                    }
+                }
+                return;
+            }
             uint32_t key[32];
 #pragma unroll
             for (int jj = 0; jj < 32; jj++)
@@ -381,9 +461,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int jj = 0; jj < 32; jj++) keep_smallest<KP>(K, key[jj]);
         };
-        uint32_t u = blockIdx.x, i = 0, j = 0, t = 0;
-        TcUnitF un = a.units[u];
-        TcUnitF unx = a.units[u + gridDim.x < nunits ? u + gridDim.x : u];
         uint32_t K[KP];
 #pragma unroll
         for (int p = 0; p < KP; p++) K[p] = ~0u;
@@ -432,7 +509,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 for (int p = 0; p < KP; p++) m[p] = K[p];
             }
             failed = named_barrier_or(1, EPI_WARPS * 32, failed || *abort);
-            if (half == 0 && un.row0 + r < un.s && !failed) {
+            if (!DUMP && half == 0 && un.row0 + r < un.s && !failed) {
 #pragma unroll
                 for (int p = 0; p < KP; p++) keep_smallest<KP>(K, m[p]);
                 const uint64_t row = un.off + un.row0 + r;
@@ -467,6 +544,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (full) {
                     const unsigned slot = atomicAdd(a.novf, 1u);
                     a.ovf[slot] = (u << 7) | r;
+                    atomicAdd(a.leaf_ovf + un.leaf, 1u);
                 }
             }
             u += gridDim.x;
@@ -637,7 +715,24 @@ __global__ void __launch_bounds__(STAGE_THREADS) leaf_stage_f32(const float *X, 
                 const uint32_t t = 4 * lane + q;
                 c4[q] = t < d ? __fsub_rn(x[t], mu[t]) : 0.0f;
             }
-            if (PREC == PREC_FP8) {
+            if (PREC == PREC_SPLIT) {
+                // [hi (dp) | lo (dp)] with dp = row_bytes / 4 BF16 values per half
+                const uint32_t dp = row_bytes / 4;
+                uint32_t hw[2], lw[2];
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(c4[2 * q]), h1 = __float2bfloat16_rn(c4[2 * q + 1]);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(__fsub_rn(c4[2 * q], __bfloat162float(h0)));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(__fsub_rn(c4[2 * q + 1], __bfloat162float(h1)));
+                    hw[q] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    lw[q] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+                if (4 * lane < dp) {
+                    uint2 *rowp = reinterpret_cast<uint2 *>(staged + row * row_bytes);
+                    rowp[lane] = make_uint2(hw[0], hw[1]);
+                    rowp[dp / 4 + lane] = make_uint2(lw[0], lw[1]);
+                }
+            } else if (PREC == PREC_FP8) {
                 uint32_t w = 0;
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
@@ -754,12 +849,14 @@ __global__ void __launch_bounds__(128) rerank_rows(const float *X, uint32_t d, c
 template <int MET>
 __global__ void __launch_bounds__(256) rerank_full(const float *X, uint32_t d, const TcUnitF *units,
                                                    const uint32_t *ovf, uint32_t novf, const uint32_t *members,
-                                                   uint32_t k, uint32_t *out_dst, uint32_t *out_src, float *out_dist) {
+                                                   const uint32_t *simt_size, uint32_t k, uint32_t *out_dst,
+                                                   uint32_t *out_src, float *out_dist) {
     const int lane = threadIdx.x & 31;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t w_ = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; w_ < novf; w_ += nw) {
         const uint32_t e = ovf[w_];
         const TcUnitF un = units[e >> 7];
+        if (simt_size[un.leaf]) continue;  // the whole leaf is evaluated on the CUDA cores
         const uint32_t r = e & 127u, row = un.row0 + r;
         const uint32_t kk = un.s - 1 < k ? un.s - 1 : k;
         const uint32_t me = members[un.off + row];
@@ -818,6 +915,13 @@ __global__ void build_units_f(const uint32_t *tile_grp, const uint32_t *tile_row
     }
 }
 
+// Leaves where more than one row in eight needs a full evaluation are evaluated whole by the
+// CUDA-core all-pairs kernel (tiled, far cheaper per row than one warp per row).
+__global__ void simt_leaves(const uint32_t *size, const unsigned *leaf_ovf, uint64_t L, uint32_t *simt_size) {
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < L; b += (uint64_t)gridDim.x * blockDim.x)
+        simt_size[b] = (uint64_t)leaf_ovf[b] * 8 > size[b] ? size[b] : 0u;
+}
+
 __global__ void max_leaf_size(const uint32_t *size, uint64_t L, unsigned *out) {
     unsigned m = 0;
     for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < L; b += (uint64_t)gridDim.x * blockDim.x)
@@ -825,10 +929,10 @@ __global__ void max_leaf_size(const uint32_t *size, uint64_t L, unsigned *out) {
     atomicMax(out, m);
 }
 
-template <int PREC, int KB, int KP>
+template <int PREC, int KB, int KP, bool DUMP = false>
 int launch_tcf(const CUtensorMap &map, const TcfArgs &args, uint64_t ntiles, uint32_t ksteps) {
     using C = TcfCfg<PREC, KB, KP>;
-    auto kern = leaf_gram_tcf<PREC, KB, KP>;
+    auto kern = leaf_gram_tcf<PREC, KB, KP, DUMP>;
     PIPNN_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     int dev = 0, sms = 0;
     PIPNN_CUDA(cudaGetDevice(&dev));
@@ -846,6 +950,9 @@ int launch_stage(int prec, const float *X, uint32_t d, const uint64_t *off, cons
     if (prec == PREC_FP8)
         leaf_stage_f32<MET, PREC_FP8><<<g, STAGE_THREADS, 0, stream()>>>(X, d, off, mem, L, row_bytes, info, pieces,
                                                                         rnorm, staged);
+    else if (prec == PREC_SPLIT)
+        leaf_stage_f32<MET, PREC_SPLIT><<<g, STAGE_THREADS, 0, stream()>>>(X, d, off, mem, L, row_bytes, info, pieces,
+                                                                          rnorm, staged);
     else
         leaf_stage_f32<MET, PREC_BF16><<<g, STAGE_THREADS, 0, stream()>>>(X, d, off, mem, L, row_bytes, info, pieces,
                                                                          rnorm, staged);
@@ -858,20 +965,24 @@ BandCoef band_coefficients(int prec, uint32_t d, int metric) {
     const double uc = std::ldexp(1.0, -24);
     const double uq = prec == PREC_FP8 ? std::ldexp(1.0, -4) : std::ldexp(1.0, -8);
     const double a0 = prec == PREC_FP8 ? std::ldexp(1.0, -10) : 0.0;
-    const double uacc = prec == PREC_FP8 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -16);
+    const double uacc = prec == PREC_FP8 ? std::ldexp(1.0, -11) : std::ldexp(1.0, -22);
     const uint32_t kstep = prec == PREC_FP8 ? 32 : 16;
-    const double steps = (double)((d + kstep - 1) / kstep + 1);
+    const uint32_t products = prec == PREC_SPLIT ? 3 : 1;
+    const double steps = (double)(products * ((d + kstep - 1) / kstep) + 1);
     const double sd = std::sqrt((double)d);
-    const double gram = (2.0 * uq + uq * uq) * (1.0 + 4.0 * uc);
+    // |G~ - G| / sum |x_t y_t|: one rounding per operand, or for the split form x = hi + lo + e with
+    // |e| <= 2^-16 |x| and |lo| <= 2^-8 (1 + 2^-8) |x| (the dropped lo.lo term included)
+    const double gram = (prec == PREC_SPLIT ? 3.0 * std::ldexp(1.0, -16) + std::ldexp(1.0, -22)
+                                            : 2.0 * uq + uq * uq) * (1.0 + 4.0 * uc);
     BandCoef c{};
     if (metric == PIPNN_L2) {
         // 2|dG| + |dn_i| + |dn_j| + accumulation + defining-order error + centring perturbation
-        c.rR = (float)(2.0 * gram + 2.0 * steps * uacc * (1.0 + uq) * (1.0 + uq) + 2.0 * (d + 4) * uc + 8.0 * uc);
+        c.rR = (float)(2.0 * gram + 2.0 * steps * uacc * (1.0 + uq) * (1.0 + uq) * 1.02 + 2.0 * (d + 4) * uc + 8.0 * uc);
         c.sq = (float)((d + 6) * uc + steps * uacc + (d + 4) * uc + 4.0 * uc);
         c.lin = (float)(2.0 * a0 * (1.0 + uq) * sd);
         c.zero = (float)(2.0 * d * a0 * a0);
     } else {
-        c.rR = (float)(gram + steps * uacc * (1.0 + uq) * (1.0 + uq));
+        c.rR = (float)(gram + steps * uacc * (1.0 + uq) * (1.0 + uq) * 1.02);
         c.lin = (float)(a0 * (1.0 + uq) * sd);
         c.zero = (float)(d * a0 * a0);
         c.W = (float)(2.0 * (d + 6) * uc + 2.0 * steps * uacc);
@@ -882,7 +993,81 @@ BandCoef band_coefficients(int prec, uint32_t d, int metric) {
     return c;
 }
 
+__global__ void gram_sizes(const uint32_t *size, uint64_t L, uint64_t *sq) {
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < L; b += (uint64_t)gridDim.x * blockDim.x)
+        sq[b] = (uint64_t)size[b] * size[b];
+}
+
+__global__ void sizes_of(const uint64_t *off, uint64_t L, uint32_t *size) {
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < L; b += (uint64_t)gridDim.x * blockDim.x)
+        size[b] = (uint32_t)(off[b + 1] - off[b]);
+}
+
 }  // namespace
+
+// The approximate dissimilarities of the reduced-precision engine, before any re-rank: for leaf b
+// the |b| x |b| block gram[sum_{c<b} |c|^2 ..] (row = member i, column = member j, both in the
+// leaf's member order).  For the FP64 error reports and the error-bound tests.
+int leaf_gram_tcf(const float *X, uint32_t d, int metric, int prec, const uint64_t *off, const uint32_t *mem,
+                  uint64_t L, float *gram, Workspace &ws) {
+    if (prec != PREC_BF16 && prec != PREC_FP8 && prec != PREC_SPLIT)
+        return set_error(PIPNN_EUNSUPPORTED, "the reduced-precision leaf engine takes BF16, FP8 or BF16X3");
+    if (d > 128) return set_error(PIPNN_EUNSUPPORTED, "the reduced-precision leaf engine takes d <= 128");
+    uint64_t M = 0;
+    PIPNN_TRY(read_u64(off + L, &M));
+    if (M == 0 || L == 0) return PIPNN_OK;
+    if (M >= 0x7FFFFF00ull) return set_error(PIPNN_EUNSUPPORTED, "the tensor-core leaf engine takes < 2^31 leaf members");
+    uint32_t *size;
+    uint64_t *goff, *tot;
+    PIPNN_TRY(ws.alloc(&size, L));
+    PIPNN_TRY(ws.alloc(&goff, L));
+    PIPNN_TRY(ws.alloc(&tot, 1));
+    sizes_of<<<grid_for(L, 256), 256, 0, stream()>>>(off, L, size);
+    PIPNN_LAUNCH_CHECK();
+    gram_sizes<<<grid_for(L, 256), 256, 0, stream()>>>(size, L, goff);
+    PIPNN_LAUNCH_CHECK();
+    PIPNN_TRY(exclusive_scan_u64(goff, goff, L, tot, ws));
+    const uint32_t KB = prec == PREC_FP8 ? 1 : (d + 63) / 64;
+    // 64 BF16 or 128 e4m3 values per K block; the split form stores a hi and a lo half
+    const uint32_t row_bytes = 128 * KB * (prec == PREC_SPLIT ? 2 : 1);
+    const uint32_t ksteps = prec == PREC_FP8 ? (d + 31) / 32 : (d + 15) / 16;
+    LeafInfoF *info;
+    uint2 *pieces;
+    float *rnorm;
+    unsigned char *staged;
+    PIPNN_TRY(ws.alloc(&info, L));
+    PIPNN_TRY(ws.alloc(&pieces, M));
+    PIPNN_TRY(ws.alloc(&rnorm, M));
+    PIPNN_TRY(ws.alloc(&staged, M * row_bytes));
+    if (metric == PIPNN_L2) PIPNN_TRY(launch_stage<PIPNN_L2>(prec, X, d, off, mem, L, row_bytes, info, pieces, rnorm, staged));
+    else PIPNN_TRY(launch_stage<PIPNN_IP>(prec, X, d, off, mem, L, row_bytes, info, pieces, rnorm, staged));
+    uint32_t *tile_grp = nullptr, *tile_row0 = nullptr;
+    uint64_t ntiles = 0;
+    PIPNN_TRY(make_tiles(size, L, ROWS, &tile_grp, &tile_row0, &ntiles, ws));
+    TcUnitF *units;
+    PIPNN_TRY(ws.alloc(&units, ntiles));
+    build_units_f<<<grid_for(ntiles, 256), 256, 0, stream()>>>(tile_grp, tile_row0, ntiles, off, goff, 0, units);
+    PIPNN_LAUNCH_CHECK();
+    CUtensorMap map;
+    if (prec == PREC_FP8) PIPNN_TRY(encode_bytes_map(&map, staged, M, row_bytes));
+    else PIPNN_TRY(encode_rows_map(&map, reinterpret_cast<const __nv_bfloat16 *>(staged), M, row_bytes / 2, false));
+    TcfArgs a{};
+    a.units = units;
+    a.pieces = pieces;
+    a.rnorm = rnorm;
+    a.info = info;
+    a.metric = metric;
+    a.colbits = 16;
+    a.err = device_error_word();
+    a.gram = gram;
+    a.gram_off = goff;
+    if (prec == PREC_FP8) return launch_tcf<PREC_FP8, 1, 4, true>(map, a, ntiles, ksteps);
+    if (prec == PREC_SPLIT)
+        return KB == 1 ? launch_tcf<PREC_SPLIT, 1, 4, true>(map, a, ntiles, ksteps)
+                       : launch_tcf<PREC_SPLIT, 2, 4, true>(map, a, ntiles, ksteps);
+    if (KB == 1) return launch_tcf<PREC_BF16, 1, 4, true>(map, a, ntiles, ksteps);
+    return launch_tcf<PREC_BF16, 2, 4, true>(map, a, ntiles, ksteps);
+}
 
 // A2..A4 for float data on the reduced-precision tensor-core engine (see the file comment).
 // X: n x d float32 device; off/mem: leaves; leaf_size/cand_off: per-leaf size and first output
@@ -893,8 +1078,8 @@ int leaf_pick_tcf(const float *X, uint64_t n, uint32_t d, int metric, int prec, 
                   uint32_t *out_dst, uint32_t *out_src, float *out_dist, Workspace &ws, cudaEvent_t ev0,
                   cudaEvent_t ev1, uint32_t *launches, uint64_t *fallback_rows) {
     (void)n;
-    if (prec != PREC_BF16 && prec != PREC_FP8)
-        return set_error(PIPNN_EUNSUPPORTED, "the reduced-precision leaf engine takes BF16 or FP8");
+    if (prec != PREC_BF16 && prec != PREC_FP8 && prec != PREC_SPLIT)
+        return set_error(PIPNN_EUNSUPPORTED, "the reduced-precision leaf engine takes BF16, FP8 or BF16X3");
     if (d > 128) return set_error(PIPNN_EUNSUPPORTED, "the reduced-precision leaf engine takes d <= 128");
     if (k > 16) return set_error(PIPNN_EINVAL, "k above 16");
     *launches = 0;
@@ -916,7 +1101,8 @@ int leaf_pick_tcf(const float *X, uint64_t n, uint32_t d, int metric, int prec, 
     if (colbits < 7) colbits = 7;
 
     const uint32_t KB = prec == PREC_FP8 ? 1 : (d + 63) / 64;
-    const uint32_t row_bytes = 128 * KB;  // 64 BF16 or 128 e4m3 values per K block
+    // 64 BF16 or 128 e4m3 values per K block; the split form stores a hi and a lo half
+    const uint32_t row_bytes = 128 * KB * (prec == PREC_SPLIT ? 2 : 1);
     const uint32_t ksteps = prec == PREC_FP8 ? (d + 31) / 32 : (d + 15) / 16;
     LeafInfoF *info;
     uint2 *pieces;
@@ -938,19 +1124,23 @@ int leaf_pick_tcf(const float *X, uint64_t n, uint32_t d, int metric, int prec, 
     build_units_f<<<grid_for(ntiles, 256), 256, 0, stream()>>>(tile_grp, tile_row0, ntiles, off, cand_off, k, units);
     PIPNN_LAUNCH_CHECK();
 
-    const int KP = prec == PREC_FP8 ? (k <= 2 ? 8 : 16) : (k <= 2 ? 4 : (k <= 4 ? 8 : 16));
+    const int KP = prec == PREC_BF16 ? (k <= 2 ? 4 : (k <= 4 ? 8 : 16)) : (k <= 2 ? 8 : 16);
     uint16_t *cand;
     uint8_t *ccnt;
     uint32_t *ovf;
     unsigned *novf;
     PIPNN_TRY(ws.alloc(&cand, M * KP));
     PIPNN_TRY(ws.alloc(&ccnt, M));
+    unsigned *leaf_ovf;
+    uint32_t *simt_size;
     PIPNN_TRY(ws.alloc(&ovf, M));
     PIPNN_TRY(ws.zeros(&novf, 1));
+    PIPNN_TRY(ws.zeros(&leaf_ovf, L));
+    PIPNN_TRY(ws.alloc(&simt_size, L));
 
     CUtensorMap map;
     if (prec == PREC_FP8) PIPNN_TRY(encode_bytes_map(&map, staged, M, row_bytes));
-    else PIPNN_TRY(encode_rows_map(&map, reinterpret_cast<const __nv_bfloat16 *>(staged), M, 64 * KB, false));
+    else PIPNN_TRY(encode_rows_map(&map, reinterpret_cast<const __nv_bfloat16 *>(staged), M, row_bytes / 2, false));
     TcfArgs a{};
     a.units = units;
     a.pieces = pieces;
@@ -964,12 +1154,20 @@ int leaf_pick_tcf(const float *X, uint64_t n, uint32_t d, int metric, int prec, 
     a.ccnt = ccnt;
     a.ovf = ovf;
     a.novf = novf;
+    a.leaf_ovf = leaf_ovf;
     a.err = device_error_word();
 
     cudaEventRecord(ev0, stream());
     int rc;
     if (prec == PREC_FP8) {
         rc = KP == 8 ? launch_tcf<PREC_FP8, 1, 8>(map, a, ntiles, ksteps) : launch_tcf<PREC_FP8, 1, 16>(map, a, ntiles, ksteps);
+    } else if (prec == PREC_SPLIT) {
+        if (KB == 1)
+            rc = KP == 8 ? launch_tcf<PREC_SPLIT, 1, 8>(map, a, ntiles, ksteps)
+                         : launch_tcf<PREC_SPLIT, 1, 16>(map, a, ntiles, ksteps);
+        else
+            rc = KP == 8 ? launch_tcf<PREC_SPLIT, 2, 8>(map, a, ntiles, ksteps)
+                         : launch_tcf<PREC_SPLIT, 2, 16>(map, a, ntiles, ksteps);
     } else if (KB == 1) {
         rc = KP == 4 ? launch_tcf<PREC_BF16, 1, 4>(map, a, ntiles, ksteps)
                      : KP == 8 ? launch_tcf<PREC_BF16, 1, 8>(map, a, ntiles, ksteps)
@@ -999,12 +1197,34 @@ int leaf_pick_tcf(const float *X, uint64_t n, uint32_t d, int metric, int prec, 
     PIPNN_CUDA(cudaMemcpyAsync(&hovf, novf, 4, cudaMemcpyDeviceToHost, stream()));
     PIPNN_CUDA(cudaStreamSynchronize(stream()));
     if (hovf) {
+        simt_leaves<<<grid_for(L, 256), 256, 0, stream()>>>(leaf_size, leaf_ovf, L, simt_size);
+        PIPNN_LAUNCH_CHECK();
         const unsigned gf = grid_for((uint64_t)hovf * 32, 256);
         if (metric == PIPNN_L2)
-            rerank_full<PIPNN_L2><<<gf, 256, 0, stream()>>>(X, d, units, ovf, hovf, mem, k, out_dst, out_src, out_dist);
+            rerank_full<PIPNN_L2><<<gf, 256, 0, stream()>>>(X, d, units, ovf, hovf, mem, simt_size, k, out_dst, out_src,
+                                                            out_dist);
         else
-            rerank_full<PIPNN_IP><<<gf, 256, 0, stream()>>>(X, d, units, ovf, hovf, mem, k, out_dst, out_src, out_dist);
+            rerank_full<PIPNN_IP><<<gf, 256, 0, stream()>>>(X, d, units, ovf, hovf, mem, simt_size, k, out_dst, out_src,
+                                                            out_dist);
         PIPNN_LAUNCH_CHECK();
+        uint32_t *sg = nullptr, *sr = nullptr;
+        uint64_t nst = 0;
+        PIPNN_TRY(make_tiles(simt_size, L, AP_ROWS, &sg, &sr, &nst, ws));
+        if (nst) {
+            AllPairsArgs ap{};
+            ap.X = X;
+            ap.d = d;
+            ap.tile_grp = sg;
+            ap.tile_row0 = sr;
+            ap.leaf_off = off;
+            ap.members = mem;
+            ap.cand_off = cand_off;
+            ap.k = k;
+            ap.out_dst = out_dst;
+            ap.out_src = out_src;
+            ap.out_dist = out_dist;
+            PIPNN_TRY(launch_allpairs<MODE_PICK>(PIPNN_F32, metric, k, ap, nst));
+        }
     }
     if (fallback_rows) *fallback_rows = hovf;
     return PIPNN_OK;

@@ -51,7 +51,8 @@ def test_params_struct_matches_header_layout():
     assert pk.pipnn_params.hyperplanes.offset == 4 * (3 + 1 + 4 + 1 + 4 + 1 + 1 + 2) + 4 == 72
     assert pk.pipnn_params.replicas.offset == 80
     assert pk.pipnn_params.prec.offset == 84
-    assert ctypes.sizeof(pk.pipnn_params) == 88
+    assert pk.pipnn_params.wave_members.offset == 88
+    assert ctypes.sizeof(pk.pipnn_params) == 96
 
 
 def test_batched_build_argument_checks_need_no_gpu():
