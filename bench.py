@@ -2,14 +2,21 @@
 """Benchmark: PiPNN index build (Alg. 4) on GB300, points per second.
 
 One step = one full build (sketches, partition, leaf all-pairs + pick, HashPrune, final prune) of
-the bigann-like-u8 workload: 1,000,000 points x 128 uint8 (1,000-cluster mixture), squared L2,
-C_max 2048, l_max 96, R 64, multi-level fanout [10, 3], k = 2, m = 12 hash bits, alpha 1.2.
-The input is resident in HBM when a step starts; L2 is flushed (256 MB write) before every step,
-outside the timed events.  Each rank builds its own independently seeded instance of the workload
-(independent indexes: no collective on the data path), so the job's throughput is the number of
-points all ranks built divided by the slowest rank's time.
+the spacev-like-i8 workload: 100,000,000 points x 128 int8 (10,000-cluster mixture, the largest
+workload that fits one GPU), squared L2, C_max 2048, l_max 64, R 64, multi-level fanout [10, 3],
+k = 2, m = 12 hash bits, alpha 1.2, the leaf and HashPrune steps in memory-bounded waves.  The
+input is resident in HBM when a step starts (and far larger than L2); L2 is also flushed (256 MB
+write) before every step, outside the timed events.  Each rank builds its own independently
+seeded instance (independent indexes: no collective on the data path), so the job's throughput is
+the number of points all ranks built divided by the slowest rank's time.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--engine tc|simt] [--impl reference]
+Beside the headline line (rank 0, one GPU) the JSON carries: recall@10 of the 100M graph on a
+sample of the workload's queries; the 1M-point bigann-like-u8 build with its recall gate against
+the oracle's graph (the oracle cannot build 100M points inside a run); and the 1M-point
+deep-like-ip float build at every leaf precision with each precision's error against FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--engine tc|simt]
+                  [--impl reference]
 
 --impl reference times the CPU oracle on a bounded sample of the same workload (rank 0 only).
 """
@@ -32,21 +39,26 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-WORKLOAD = "bigann-like-u8"
+WORKLOAD = "spacev-like-i8"
+CONTEXT = "bigann-like-u8"
 METRIC = "build points/sec at recall@10>=oracle-0.3pp; GEMM tensor-pipe % and prune HBM GB/s"
-CPU_SAMPLE = 50_000
+CPU_SAMPLE = 200_000
+CONTEXT_CPU_SAMPLE = 50_000
 REF_SAMPLE = 20_000
+HEADLINE_QUERIES = 200
+DTYPE_NAME = {synth.F32: "f32", synth.U8: "u8", synth.I8: "i8"}
 
 
 def workload_params(w):
     return dict(c_max=w["c_max"], l_max=w["l_max"], R=w["R"], fanout=tuple(w["fanout"]))
 
 
-def config_dict(w, engine, n):
-    return {"workload": WORKLOAD, "n": n, "d": w["d"], "dtype": "u8", "metric": "L2", "c_max": w["c_max"],
-            "c_min": w["c_max"] // 16, "l_max": w["l_max"], "R": w["R"], "fanout": list(w["fanout"]), "leaf_k": 2,
-            "hash_bits": 12, "alpha": 1.2, "p_samp": 0.005, "max_leaders": 1000, "leaf_engine": engine,
-            "l2": "flushed before every step (256 MB write)", "input": "resident in HBM",
+def config_dict(name, w, engine, n):
+    return {"workload": name, "n": n, "d": w["d"], "dtype": DTYPE_NAME[w["dtype"]],
+            "metric": "IP" if w["metric"] == synth.IP else "L2", "c_max": w["c_max"], "c_min": w["c_max"] // 16,
+            "l_max": w["l_max"], "R": w["R"], "fanout": list(w["fanout"]), "leaf_k": 2, "hash_bits": 12,
+            "alpha": 1.2, "p_samp": 0.005, "max_leaders": 1000, "leaf_engine": engine,
+            "l2": "flushed before every step (256 MB write); inputs larger than L2", "input": "resident in HBM",
             "data": "synthetic, seeded per rank"}
 
 
@@ -136,16 +148,16 @@ def job_throughput(n_per_rank, world, seconds):
     return world * n_per_rank / seconds
 
 
-def cpu_baseline(X, H, w):
+def cpu_baseline(X, H, w, name, n_sample):
     import oracle  # the CPU oracle: timed here as a reported baseline only
 
-    n = min(CPU_SAMPLE, X.shape[0])
+    n = min(n_sample, X.shape[0])
     bp = oracle.params(**workload_params(w))
     t = time.perf_counter()
-    oracle.build(X[:n], bp, H, synth.BUILD_SEED)
+    oracle.build(np.ascontiguousarray(X[:n]), bp, H, synth.BUILD_SEED, metric=w["metric"])
     dt = time.perf_counter() - t
     return {"value": n / dt, "unit": "points/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"first {n:,} points of the {WORKLOAD} workload, full Alg. 4 build ({dt:.1f} s)"}
+            "sample": f"first {n:,} points of the {name} workload, full Alg. 4 build ({dt:.1f} s)"}
 
 
 RECALL_L = (16, 32, 64, 128)
@@ -164,10 +176,10 @@ def recall_gate(X, H, w, adj_gpu, deg_gpu, n_queries):
     adj_o, deg_o, _ = oracle.build(X, bp, H, synth.BUILD_SEED)
     dt = time.perf_counter() - t
     cpu = {"value": X.shape[0] / dt, "unit": "points/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-           "sample": f"the full {X.shape[0]:,}-point {WORKLOAD} workload, full Alg. 4 build ({dt:.1f} s)"}
+           "sample": f"the full {X.shape[0]:,}-point {CONTEXT} workload, full Alg. 4 build ({dt:.1f} s)"}
     identical = bool(np.array_equal(deg_o, deg_gpu) and np.array_equal(adj_o, adj_gpu))
     rows_differ = int(((adj_o != adj_gpu).any(axis=1) | (deg_o != deg_gpu)).sum())
-    Q = synth.queries(WORKLOAD, n_queries)
+    Q = synth.queries(CONTEXT, n_queries)
     t = time.perf_counter()
     gt = oracle.knn_bytes(X, Q, 10)
     t_gt = time.perf_counter() - t
@@ -300,6 +312,106 @@ def precision_modes(steps, warmup, n_queries=1000, error_leaves=48):
     return out
 
 
+def timed_builds(pk, Xd, bp, adj, deg, steps, warmup, metric, barrier, sampler=None):
+    """W untimed builds, then K builds each bracketed by CUDA events on the current stream (L2
+    flushed before each, outside the events).  Returns the per-step ms and the library's stats."""
+    import torch
+
+    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")  # 256 MB > 129 MB L2
+    for _ in range(warmup):
+        pk.pipnn_build_into(Xd, bp, synth.BUILD_SEED, adj, deg, metric=metric)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stats = []
+    barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        pk.pipnn_build_into(Xd, bp, synth.BUILD_SEED, adj, deg, metric=metric)
+        evs[i][1].record(stream)
+        stats.append(pk.pipnn_get_stats())
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    del flush
+    return [a.elapsed_time(b) for a, b in evs], stats, clocks
+
+
+def leaf_roofline(stats, d, engine, kernel_file, profile_file):
+    """The leaf all-pairs kernel against the burst BF16 peak: unique-pair flops of every build
+    (sum over leaves of |b| (|b| - 1) d) over the kernel time of that build (summed over its
+    launches, one per wave)."""
+    flops = sum(s["leaf_pairs"] * d for s in stats)
+    ms = sum(s["ms_leaf_kernel"] for s in stats)
+    launches = sum(s["leaf_kernel_launches"] for s in stats)
+    peaks, peak_kind = measured_peaks()
+    # the kernel runs for milliseconds to a second inside a build: the burst peak applies
+    peak = peaks["bf16_tflops"]
+    achieved = flops / (ms / 1e3) / 1e12
+    traffic = profiled_traffic(kernel_file, profile_file) if engine == "tc" else None
+    return {"kernel": "leaf all-pairs Gram + k-NN pick (" + engine + ")", "bound": "tensor", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": f"{peak_kind} bf16 burst",
+            "traffic": traffic, "algorithmic_flops_per_build": flops / len(stats),
+            "ms_per_build": ms / len(stats), "launches_per_build": launches / len(stats)}
+
+
+def phases(stats):
+    return {k: statistics.mean(s[k] for s in stats)
+            for k in ("ms_sketch", "ms_partition", "ms_leaf", "ms_hashprune", "ms_prune")}
+
+
+def context_block(pk, steps, warmup, engine, n_queries, cpu_sample, recall=True):
+    """The 1M-point bigann-like-u8 build (the configuration the oracle can build inside a run):
+    points/s, and the recall gate against the oracle's graph of the same points."""
+    import torch
+
+    w = dict(synth.WORKLOADS[CONTEXT])
+    X = synth.mixture(w["n"], w["d"], w["dtype"], w["centers"], w["sigma"], w["data_seed"])
+    H = synth.hyperplanes(12, w["d"])
+    Xd = torch.from_numpy(X).cuda()
+    eng = pk.PIPNN_LEAF_TC if engine == "tc" else pk.PIPNN_LEAF_SIMT
+    bp = pk.params(dtype=pk.PIPNN_U8, hyperplanes=torch.from_numpy(H).cuda(), leaf_engine=eng, **workload_params(w))
+    n, R = w["n"], w["R"]
+    adj = torch.empty((n, R), dtype=torch.int32, device="cuda")
+    deg = torch.empty(n, dtype=torch.int32, device="cuda")
+    times, stats, _ = timed_builds(pk, Xd, bp, adj, deg, steps, warmup, w["metric"], lambda: None)
+    ms = statistics.mean(times)
+    out = {"config": config_dict(CONTEXT, w, engine, n), "value": n / (ms / 1e3), "unit": "points/s",
+           "ms_per_step": ms, "steps": steps, "phases_ms": phases(stats),
+           "roofline": leaf_roofline(stats, w["d"], engine, "leaf_tc.cu", "leaf_gram_tc_bigann-like-u8.md")}
+    if recall:
+        adj_g = adj.cpu().numpy().view(np.uint32)
+        deg_g = deg.cpu().numpy().view(np.uint32)
+        out["recall"], out["cpu_baseline"] = recall_gate(X, H, w, adj_g, deg_g, n_queries)
+    else:
+        out["cpu_baseline"] = cpu_baseline(X, H, w, CONTEXT, cpu_sample)
+    del Xd, adj, deg
+    return out
+
+
+def headline_recall(Xh, adj_h, deg_h, w, n_queries):
+    """Recall@10 (Def. 2) of the GPU graph of the headline workload under the oracle's beam search
+    (Alg. 1) from the medoid, on a sample of the workload's queries, against exact ground truth."""
+    import oracle
+
+    Q = synth.queries_device(n_queries, w["d"], w["dtype"], w["centers"], w["sigma"], w["data_seed"],
+                             w["query_seed"])
+    t = time.perf_counter()
+    gt = oracle.knn_bytes(Xh, Q, 10, chunk=n_queries, db_chunk=1 << 20)
+    t_gt = time.perf_counter() - t
+    start = oracle.medoid(Xh)
+    rec = [oracle.recall(oracle.beam_search(Xh, adj_h, deg_h, Q, L, start=start)[0], gt) for L in RECALL_L]
+    return {"k": 10, "L": list(RECALL_L), "gpu": rec, "oracle": None, "queries": int(Q.shape[0]), "start": "medoid",
+            "ground_truth": f"exact 10-NN by (L2, id) over all points ({t_gt:.1f} s)",
+            "oracle_graph": "not built at this size (hours on the host); the oracle-gated recall is in "
+                            "the bigann_like_u8 block, and the wave-split build equals the oracle's graph "
+                            "in the parity tests"}
+
+
 def run_reference(args, w):
     """Reference arm: the CPU oracle as it stands, on bounded samples of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -312,24 +424,38 @@ def run_reference(args, w):
     H = synth.hyperplanes(12, w["d"])
     bp = oracle.params(**workload_params(w))
     for _ in range(args.warmup):
-        oracle.build(X, bp, H, synth.BUILD_SEED)
+        oracle.build(X, bp, H, synth.BUILD_SEED, metric=w["metric"])
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        oracle.build(X, bp, H, synth.BUILD_SEED)
+        oracle.build(X, bp, H, synth.BUILD_SEED, metric=w["metric"])
         times.append(time.perf_counter() - t)
     ms = 1e3 * sum(times) / len(times)
     value = n / (ms / 1e3)
     cores = len(os.sched_getaffinity(0))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {**config_dict(w, "cpu-oracle", n), "sample": f"first {n:,} points per step"},
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[w["dtype"]], "data": "synthetic",
+            "config": {**config_dict(args.workload, w, "cpu-oracle", w["n"]),
+                       "sample": f"{n:,} points of the workload's mixture per step"},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {n:,} points of the {WORKLOAD} workload per step"},
+                             "sample": f"{n:,} points of the {args.workload} workload's mixture per step"},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def make_points(name, w, n, rank):
+    """The workload's points on the device: drawn on the GPU for the 100M workload (its host draw
+    would take minutes), else drawn on the host and copied."""
+    import torch
+
+    seed = rank_data_seed(w, rank)
+    if n > 20_000_000:
+        return synth.mixture_device(n, w["d"], w["dtype"], w["centers"], w["sigma"], seed,
+                                    normalize=w["metric"] == synth.IP)
+    X = synth.mixture(n, w["d"], w["dtype"], w["centers"], w["sigma"], seed, normalize=w["metric"] == synth.IP)
+    return torch.from_numpy(X).cuda()
 
 
 def main():
@@ -338,16 +464,20 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS))
     ap.add_argument("--engine", default="tc", choices=["tc", "simt"])
+    ap.add_argument("--prec", default=None, choices=["fp32", "bf16", "fp8", "bf16x3"],
+                    help="leaf precision for float workloads (default bf16x3 on the tc engine)")
     ap.add_argument("--n", type=int, default=None, help="override the workload size (tests)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-recall", action="store_true", help="skip the recall gate (oracle build + beam search)")
-    ap.add_argument("--queries", type=int, default=None, help="queries of the recall gate (default: the workload's)")
-    ap.add_argument("--profile", action="store_true", help="timed steps only (for profiler launch lists)")
+    ap.add_argument("--no-recall", action="store_true", help="skip the recall measurements")
+    ap.add_argument("--no-context", action="store_true", help="skip the 1M bigann-like-u8 block")
     ap.add_argument("--no-precision-modes", action="store_true",
                     help="skip the float workload built at every leaf precision")
+    ap.add_argument("--queries", type=int, default=None, help="queries of the recall measurement")
+    ap.add_argument("--profile", action="store_true", help="timed steps only (for profiler launch lists)")
     args = ap.parse_args()
-    w = dict(synth.WORKLOADS[WORKLOAD])
+    w = dict(synth.WORKLOADS[args.workload])
     if args.impl == "reference":
         return run_reference(args, w)
 
@@ -368,95 +498,87 @@ def main():
             dist.barrier()
 
     n = args.n or w["n"]
-    X = synth.mixture(n, w["d"], w["dtype"], w["centers"], w["sigma"], rank_data_seed(w, rank))
+    Xd = make_points(args.workload, w, n, rank)
     H = synth.hyperplanes(12, w["d"])
-    Xd = torch.from_numpy(X).cuda()
     Hd = torch.from_numpy(H).cuda()
     engine = pk.PIPNN_LEAF_TC if args.engine == "tc" else pk.PIPNN_LEAF_SIMT
-    bp = pk.params(dtype=pk.PIPNN_U8, hyperplanes=Hd, leaf_engine=engine, **workload_params(w))
+    prec_names = {"fp32": pk.PIPNN_PREC_FP32, "bf16": pk.PIPNN_PREC_BF16, "fp8": pk.PIPNN_PREC_FP8,
+                  "bf16x3": pk.PIPNN_PREC_BF16X3}
+    prec = prec_names[args.prec] if args.prec else (
+        pk.PIPNN_PREC_BF16X3 if (w["dtype"] == synth.F32 and args.engine == "tc") else pk.PIPNN_PREC_FP32)
+    dt_code = {synth.F32: pk.PIPNN_F32, synth.U8: pk.PIPNN_U8, synth.I8: pk.PIPNN_I8}[w["dtype"]]
+    bp = pk.params(dtype=dt_code, hyperplanes=Hd, leaf_engine=engine, prec=prec, **workload_params(w))
     R = w["R"]
     adj = torch.empty((n, R), dtype=torch.int32, device="cuda")
     deg = torch.empty(n, dtype=torch.int32, device="cuda")
-    flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")  # 256 MB > 129 MB L2
 
-    for _ in range(args.warmup):
-        pk.pipnn_build_into(Xd, bp, synth.BUILD_SEED, adj, deg)
-    torch.cuda.synchronize()
-
-    stream = torch.cuda.current_stream()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stats = []
     sampler = ClockSampler(torch.cuda.current_device())
-    barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    for i in range(args.steps):
-        flush.zero_()
-        evs[i][0].record(stream)
-        pk.pipnn_build_into(Xd, bp, synth.BUILD_SEED, adj, deg)
-        evs[i][1].record(stream)
-        stats.append(pk.pipnn_get_stats())
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+    step_ms, stats, clocks = timed_builds(pk, Xd, bp, adj, deg, args.steps, args.warmup, w["metric"], barrier,
+                                          sampler)
     ms = max_over_ranks(sum(step_ms) / len(step_ms), world, "cuda")
     value = job_throughput(n, world, ms / 1e3)
-
-    # dominant kernel: the leaf all-pairs Gram + pick
-    leaf_ms = sum(s["ms_leaf_kernel"] for s in stats) / max(1, sum(s["leaf_kernel_launches"] for s in stats))
-    leaf_flops = stats[-1]["leaf_pairs"] * w["d"]  # sum |b|(|b|-1) d: every unordered pair once, 2 flops/MAC
-    peaks, peak_kind = measured_peaks()
-    # the kernel runs for milliseconds inside a build of tens of milliseconds: the burst peak applies
-    peak = peaks["bf16_tflops"]
-    achieved = leaf_flops / (leaf_ms / 1e3) / 1e12
-    traffic = profiled_traffic("leaf_tc.cu", "leaf_gram_tc_bigann-like-u8.md") if args.engine == "tc" else None
-    roofline = {"kernel": "leaf all-pairs Gram + k-NN pick (" + args.engine + ")", "bound": "tensor",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} bf16 burst", "traffic": traffic,
-                "algorithmic_flops_per_launch": leaf_flops, "ms_per_launch": leaf_ms}
-    phases = {k: statistics.mean(s[k] for s in stats)
-              for k in ("ms_sketch", "ms_partition", "ms_leaf", "ms_hashprune", "ms_prune")}
-
+    roofline = leaf_roofline(stats, w["d"], args.engine, "leaf_tc.cu" if w["dtype"] != synth.F32 else "leaf_tcf.cu",
+                             f"leaf_gram_tc_{args.workload}.md")
     if args.profile:
         if rank == 0:
-            print(json.dumps({"profile_run": True, "ms_per_step": ms, "phases_ms": phases}), flush=True)
+            print(json.dumps({"profile_run": True, "ms_per_step": ms, "phases_ms": phases(stats)}), flush=True)
         return 0
 
     # end to end through the public call: pinned host input, host output, copies inside the region
-    Xh = torch.from_numpy(X).pin_memory()
-    adj_h = torch.empty((n, R), dtype=torch.int32).pin_memory()
-    deg_h = torch.empty(n, dtype=torch.int32).pin_memory()
-    Hh = torch.from_numpy(H)
-    bp_h = pk.params(dtype=pk.PIPNN_U8, hyperplanes=Hh, leaf_engine=engine, **workload_params(w))
-    pk.pipnn_build_into(Xh, bp_h, synth.BUILD_SEED, adj_h, deg_h)
-    e2e_steps = max(3, min(args.steps, 5))
+    Xh = torch.empty(tuple(Xd.shape), dtype=Xd.dtype, pin_memory=True)
+    Xh.copy_(Xd)
+    adj_h = torch.empty((n, R), dtype=torch.int32, pin_memory=True)
+    deg_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    del adj, deg, Xd
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    bp_h = pk.params(dtype=dt_code, hyperplanes=torch.from_numpy(H), leaf_engine=engine, prec=prec,
+                     **workload_params(w))
+    pk.pipnn_build_into(Xh, bp_h, synth.BUILD_SEED, adj_h, deg_h, metric=w["metric"])
+    e2e_steps = max(3, min(args.steps, 5)) if n <= 20_000_000 else 3
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        pk.pipnn_build_into(Xh, bp_h, synth.BUILD_SEED, adj_h, deg_h)
+        pk.pipnn_build_into(Xh, bp_h, synth.BUILD_SEED, adj_h, deg_h, metric=w["metric"])
         int(deg_h[0])  # the result is read on the host
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, "cuda")
-    e2e = {"value": job_throughput(n, world, e2e_s), "unit": "points/s", "h2d_bytes_per_step": int(X.nbytes + H.nbytes),
+    e2e = {"value": job_throughput(n, world, e2e_s), "unit": "points/s",
+           "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size() + H.nbytes),
            "d2h_bytes_per_step": int(n * R * 4 + n * 4)}
 
     if rank == 0:
+        st = stats[-1]
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-                "config": config_dict(w, args.engine, n), "roofline": roofline, "e2e": e2e,
+                "vs_baseline": None, "dtype": DTYPE_NAME[w["dtype"]], "data": "synthetic",
+                "config": config_dict(args.workload, w, args.engine, n), "roofline": roofline, "e2e": e2e,
                 "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks,
-                "phases_ms": phases, "leaves": stats[-1]["leaves"], "candidates": stats[-1]["candidates"]}
+                "phases_ms": phases(stats), "leaves": st["leaves"], "candidates": st["candidates"],
+                "waves_per_build": st["waves"], "peak_device_bytes": st["peak_device_bytes"]}
+        if w["dtype"] == synth.F32:
+            line["config"]["prec"] = args.prec or ("bf16x3" if args.engine == "tc" else "fp32")
+        Xnp = Xh.numpy()
+        adj_np = adj_h.numpy().view(np.uint32)
+        deg_np = deg_h.numpy().view(np.uint32)
         if world == 1 and not args.no_recall:
-            torch.cuda.synchronize()
-            adj_g = adj.cpu().numpy().view(np.uint32)
-            deg_g = deg.cpu().numpy().view(np.uint32)
-            line["recall"], cpu = recall_gate(X, H, w, adj_g, deg_g, args.queries or w["queries"])
-            if not args.no_cpu_baseline:
-                line["cpu_baseline"] = cpu
-        elif world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(X, H, w)
+            if args.workload == CONTEXT and n == w["n"]:
+                line["recall"], cpu = recall_gate(Xnp, H, w, adj_np, deg_np, args.queries or w["queries"])
+                if not args.no_cpu_baseline:
+                    line["cpu_baseline"] = cpu
+            elif w["dtype"] != synth.F32:
+                line["recall"] = headline_recall(Xnp, adj_np, deg_np, w, args.queries or HEADLINE_QUERIES)
+        if world == 1 and not args.no_cpu_baseline and "cpu_baseline" not in line:
+            line["cpu_baseline"] = cpu_baseline(Xnp, H, w, args.workload, CPU_SAMPLE)
+        del Xh, adj_h, deg_h, Xnp, adj_np, deg_np
+        pk.pipnn_trim_pool()
+        torch.cuda.empty_cache()
+        if world == 1 and not args.no_context and args.workload != CONTEXT:
+            line["bigann_like_u8"] = context_block(pk, min(args.steps, 10), min(args.warmup, 3), args.engine,
+                                                   args.queries or synth.WORKLOADS[CONTEXT]["queries"],
+                                                   CONTEXT_CPU_SAMPLE, recall=not args.no_recall)
+            pk.pipnn_trim_pool()
+            torch.cuda.empty_cache()
         if world == 1 and not args.no_precision_modes:
             line["precision_modes"] = precision_modes(min(args.steps, 5), min(args.warmup, 2))
         print(json.dumps(line), flush=True)

@@ -281,6 +281,12 @@ int pipnn_build_batched(const void *const *points, const uint64_t *n, uint32_t c
 int pipnn_build_into(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp,
                      uint64_t seed, uint32_t *adj, uint32_t *deg);
 
+/* Returns to the driver the device memory the library's stream-ordered pool keeps for reuse
+ * between builds (the pool otherwise holds its high-water mark, so that repeated builds of one
+ * size allocate nothing new).  Call it between builds of very different sizes, or before handing
+ * the memory to another allocator.  Synchronises the device. */
+int pipnn_trim_pool(void);
+
 /* Statistics of the last successful pipnn_build / pipnn_build_into on the calling thread. */
 int pipnn_get_stats(pipnn_stats *out);
 

@@ -299,43 +299,60 @@ def knn(X, Q, k=10, metric=L2):
     return ids
 
 
-def knn_bytes(X, Q, k=10, chunk=256):
+def knn_bytes(X, Q, k=10, chunk=256, db_chunk=1 << 22):
     """Exact k nearest points of every query by (squared L2, id) for byte data (Def. 1), the same
-    result as knn() but through a float32 matrix product: u8 / i8 coordinates are integers of
+    result as knn() but through float32 matrix products: u8 / i8 coordinates are integers of
     magnitude <= 255, so every product and every partial sum of a d <= 128 dot product is an
     integer below 2^24 and exact in binary32 whatever the summation order; the distances
-    ||q||^2 + ||x||^2 - 2<q, x> are then formed exactly in int64.  Rows whose k-th and (k+1)-th
-    distances tie are resolved by id with an exact scan of that row."""
+    ||q||^2 + ||x||^2 - 2<q, x> are then formed exactly in int64.  The points are taken in blocks
+    of db_chunk; every block contributes its own exact k smallest by (distance, id), ties at the
+    k-th distance resolved by id, and the blocks' lists are merged by (distance, id)."""
     import torch
 
     X = np.ascontiguousarray(X)
     Q = np.ascontiguousarray(Q, dtype=X.dtype)
     if X.dtype not in (np.uint8, np.int8) or X.shape[1] > 128:
         raise ValueError("knn_bytes takes byte data with d <= 128")
-    Xf = torch.from_numpy(X.astype(np.float32))
-    nx = torch.from_numpy((X.astype(np.int64) ** 2).sum(1))
-    out = np.zeros((Q.shape[0], k), np.uint32)
-    for s in range(0, Q.shape[0], chunk):
-        q = Q[s:s + chunk]
-        dot = (torch.from_numpy(q.astype(np.float32)) @ Xf.T).to(torch.int64)
-        nq = torch.from_numpy((q.astype(np.int64) ** 2).sum(1))
-        D = nq[:, None] + nx[None, :] - 2 * dot
-        kk = min(k + 1, X.shape[0])
-        val, idx = torch.topk(D, kk, dim=1, largest=False, sorted=True)
-        val, idx = val.numpy(), idx.numpy()
-        Dn = None
-        for r in range(q.shape[0]):
-            if kk > k and val[r, k] == val[r, k - 1] or len(set(val[r, :k].tolist())) < k:
-                # ties inside or at the edge of the top k: order every candidate up to the k-th
-                # distance by (distance, id)
-                if Dn is None:
-                    Dn = D.numpy()
-                c = np.nonzero(Dn[r] <= val[r, k - 1])[0]
-                o = np.lexsort((c, Dn[r, c]))[:k]
-                out[s + r] = c[o]
-            else:
-                out[s + r] = idx[r, :k]
-    return out
+    n, nq = X.shape[0], Q.shape[0]
+    kk = min(k, n)
+    best_d = np.full((nq, 0), 0, np.int64)
+    best_i = np.full((nq, 0), 0, np.int64)
+    for b0 in range(0, n, db_chunk):
+        Xb = X[b0:b0 + db_chunk]
+        Xf = torch.from_numpy(Xb.astype(np.float32))
+        nx = torch.from_numpy((Xb.astype(np.int64) ** 2).sum(1))
+        cd = np.zeros((nq, min(kk, Xb.shape[0])), np.int64)
+        ci = np.zeros_like(cd)
+        for s in range(0, nq, chunk):
+            q = Q[s:s + chunk]
+            dot = (torch.from_numpy(q.astype(np.float32)) @ Xf.T).to(torch.int64)
+            nq_ = torch.from_numpy((q.astype(np.int64) ** 2).sum(1))
+            D = nq_[:, None] + nx[None, :] - 2 * dot
+            m = min(kk, Xb.shape[0])
+            val, idx = torch.topk(D, m, dim=1, largest=False, sorted=True)
+            val, idx = val.numpy(), idx.numpy()
+            Dn = None
+            for r in range(q.shape[0]):
+                th = val[r, m - 1]
+                # every candidate up to the m-th distance, ordered by (distance, id)
+                if m < Xb.shape[0] or len(set(val[r].tolist())) < m:
+                    if Dn is None:
+                        Dn = D.numpy()
+                    c = np.nonzero(Dn[r] <= th)[0]
+                    if len(c) > m or len(set(val[r].tolist())) < m:
+                        o = np.lexsort((c, Dn[r, c]))[:m]
+                        cd[s + r], ci[s + r] = Dn[r, c[o]], c[o]
+                        continue
+                cd[s + r], ci[s + r] = val[r], idx[r]
+                o = np.lexsort((ci[s + r], cd[s + r]))
+                cd[s + r], ci[s + r] = cd[s + r, o], ci[s + r, o]
+        ci += b0
+        alld = np.concatenate([best_d, cd], 1)
+        alli = np.concatenate([best_i, ci], 1)
+        o = np.lexsort((alli, alld), axis=1)[:, :kk]
+        best_d = np.take_along_axis(alld, o, 1)
+        best_i = np.take_along_axis(alli, o, 1)
+    return best_i.astype(np.uint32)
 
 
 def ceil_of_product(p, n):

@@ -1017,25 +1017,51 @@ int orc_knn(const void *X, uint64_t n, const void *Q, uint64_t nq, uint32_t d, i
     return err ? ORC_ENOMEM : ORC_OK;
 }
 
-/* The point nearest (double precision) to the mean of all points. */
+/* The point nearest (double precision) to the mean of all points.  The mean is summed in fixed
+ * chunks of 65,536 points whose partial sums are added in chunk order, so the result does not
+ * depend on the thread count; ties go to the smaller index. */
 uint32_t orc_medoid(const void *X, uint64_t n, uint32_t d, int dtype, int metric)
 {
+    (void)metric;
+    const uint64_t CH = 65536;
+    const uint64_t nch = (n + CH - 1) / CH;
+    double *part = (double *)calloc(nch * d, sizeof(double));
     double *mean = (double *)calloc(d, sizeof(double));
-    if (!mean) return 0;
-    for (uint64_t i = 0; i < n; i++)
-        for (uint32_t t = 0; t < d; t++) mean[t] += coord(row(X, i, d, dtype), t, dtype);
+    if (!part || !mean) {
+        free(part);
+        free(mean);
+        return 0;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < (int64_t)nch; c++) {
+        uint64_t lo = (uint64_t)c * CH, hi = lo + CH < n ? lo + CH : n;
+        for (uint64_t i = lo; i < hi; i++)
+            for (uint32_t t = 0; t < d; t++) part[(uint64_t)c * d + t] += coord(row(X, i, d, dtype), t, dtype);
+    }
+    for (uint64_t c = 0; c < nch; c++)
+        for (uint32_t t = 0; t < d; t++) mean[t] += part[c * d + t];
     for (uint32_t t = 0; t < d; t++) mean[t] /= (double)n;
     uint32_t best = 0;
     double bd = INFINITY;
-    for (uint64_t i = 0; i < n; i++) {
-        double s = 0.0;
-        for (uint32_t t = 0; t < d; t++) {
-            double df = coord(row(X, i, d, dtype), t, dtype) - mean[t];
-            s += df * df;
+#pragma omp parallel
+    {
+        uint32_t lb = 0;
+        double ld = INFINITY;
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < (int64_t)n; i++) {
+            double s = 0.0;
+            for (uint32_t t = 0; t < d; t++) {
+                double df = coord(row(X, (uint64_t)i, d, dtype), t, dtype) - mean[t];
+                s += df * df;
+            }
+            if (s < ld || (s == ld && (uint32_t)i < lb)) { ld = s; lb = (uint32_t)i; }
         }
-        (void)metric;
-        if (s < bd) { bd = s; best = (uint32_t)i; }
+#pragma omp critical
+        {
+            if (ld < bd || (ld == bd && lb < best)) { bd = ld; best = lb; }
+        }
     }
+    free(part);
     free(mean);
     return best;
 }

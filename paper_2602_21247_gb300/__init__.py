@@ -33,7 +33,7 @@ PIPNN_OK = 0
 EXPORTS = ("pipnn_set_stream", "pipnn_last_error", "pipnn_sketch", "pipnn_partition", "pipnn_leaves_free",
            "pipnn_leaf_pick", "pipnn_edges_free", "pipnn_hashprune", "pipnn_final_prune", "pipnn_build",
            "pipnn_free", "pipnn_build_into", "pipnn_get_stats", "pipnn_hashprune_noalloc", "pipnn_build_batched",
-           "pipnn_leaf_gram")
+           "pipnn_leaf_gram", "pipnn_trim_pool")
 
 
 class PipnnError(RuntimeError):
@@ -342,6 +342,11 @@ def pipnn_build_batched(points_list, bp: pipnn_params, seeds, metric=PIPNN_L2):
         for i in range(count):
             lib().pipnn_free(C.byref(outs[i]))
     return graphs
+
+
+def pipnn_trim_pool():
+    """Releases the device memory the library's pool keeps between builds."""
+    _check(lib().pipnn_trim_pool())
 
 
 def pipnn_get_stats() -> dict:

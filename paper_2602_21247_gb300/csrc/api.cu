@@ -551,6 +551,17 @@ int pipnn_build_batched(const void *const *points, const uint64_t *n, uint32_t c
     return PIPNN_OK;
 }
 
+int pipnn_trim_pool(void) {
+    clear_error();
+    int dev = 0;
+    PIPNN_CUDA(cudaGetDevice(&dev));
+    PIPNN_CUDA(cudaDeviceSynchronize());
+    cudaMemPool_t pool;
+    PIPNN_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    PIPNN_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return PIPNN_OK;
+}
+
 int pipnn_get_stats(pipnn_stats *out) {
     if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
     *out = g_stats;

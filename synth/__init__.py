@@ -126,6 +126,62 @@ def workload(name, n=None, n_queries=None):
                    normalize=(w["metric"] == IP), n_queries=nq, query_seed=w["query_seed"])
 
 
+def _centres(centers, d, dtype, seed):
+    """The mixture's centres, drawn exactly as mixture() draws them (float64, host)."""
+    rng_c = np.random.default_rng([seed, 0])
+    if dtype == F32:
+        return rng_c.standard_normal((centers, d))
+    if dtype == U8:
+        return rng_c.gamma(2.0, 20.0, size=(centers, d))
+    return 40.0 * rng_c.standard_normal((centers, d))
+
+
+def mixture_device(n, d, dtype, centers, sigma, seed, device="cuda", chunk=1 << 23, normalize=False):
+    """The same mixture recipes drawn with torch's generator on `device` (for workloads too large to
+    draw on the host in reasonable time, e.g. 100M x 128 int8).  Seeded and reproducible on one
+    kind of device; its values differ from mixture()'s numpy draws."""
+    import torch
+
+    def gen(tag):
+        g = torch.Generator(device=device)
+        g.manual_seed((int(seed) * 1000003 + tag) % (1 << 63))
+        return g
+
+    gx = gen(1)
+    c = torch.from_numpy(_centres(centers, d, dtype, seed)).to(device)
+    tdt = {F32: torch.float32, U8: torch.uint8, I8: torch.int8}[dtype]
+    out = torch.empty((n, d), dtype=tdt, device=device)
+    for s0 in range(0, n, chunk):
+        e = min(n, s0 + chunk)
+        lab = torch.randint(0, centers, (e - s0,), generator=gx, device=device)
+        v = c[lab] + sigma * torch.randn(e - s0, d, generator=gx, device=device, dtype=torch.float64)
+        if dtype == F32:
+            if normalize:
+                v = v / torch.linalg.norm(v, dim=1, keepdim=True)
+            out[s0:e] = v.to(torch.float32)
+        elif dtype == U8:
+            out[s0:e] = torch.round(torch.clamp(v, 0.0, 255.0)).to(torch.uint8)
+        else:
+            out[s0:e] = torch.clamp(torch.round(v), -127.0, 127.0).to(torch.int8)
+    return out
+
+
+def queries_device(n_queries, d, dtype, centers, sigma, seed, query_seed, device="cuda"):
+    """Queries from the same mixture as mixture_device(..., seed) (same centres), as a host array."""
+    import torch
+
+    if dtype not in (I8, F32):
+        raise ValueError("queries_device draws int8 and float32 mixtures")
+    c = torch.from_numpy(_centres(centers, d, dtype, seed)).to(device)
+    gq = torch.Generator(device=device)
+    gq.manual_seed((int(query_seed) * 1000003 + 2) % (1 << 63))
+    lab = torch.randint(0, centers, (n_queries,), generator=gq, device=device)
+    v = c[lab] + sigma * torch.randn(n_queries, d, generator=gq, device=device, dtype=torch.float64)
+    if dtype == I8:
+        return torch.clamp(torch.round(v), -127.0, 127.0).to(torch.int8).cpu().numpy()
+    return v.to(torch.float32).cpu().numpy()
+
+
 def multi_index_sizes(count=512, lo=2_000, hi=200_000, seed=1004):
     """Sizes of the batched multi-index workload: log-uniform in [lo, hi]."""
     rng = np.random.default_rng([seed, 3])

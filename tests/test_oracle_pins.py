@@ -533,6 +533,8 @@ def test_knn_bytes_equals_plain_knn_and_brute_force(dtype):
     want = oracle.knn(X, Q, 10)
     got = oracle.knn_bytes(X, Q, 10, chunk=16)
     assert np.array_equal(got, want)
+    # the points in blocks: every block's own top 10, merged by (distance, id)
+    assert np.array_equal(oracle.knn_bytes(X, Q, 10, chunk=16, db_chunk=77), want)
     D = ((Q[:, None, :].astype(np.int64) - X[None, :, :].astype(np.int64)) ** 2).sum(2)
     brute = np.lexsort((np.broadcast_to(np.arange(X.shape[0]), D.shape), D), axis=1)[:, :10]
     assert np.array_equal(got, brute)
