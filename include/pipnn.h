@@ -65,6 +65,9 @@ enum { PIPNN_L2 = 0, PIPNN_IP = 1 };
  *                   CUDA cores otherwise. */
 enum { PIPNN_LEAF_SIMT = 0, PIPNN_LEAF_TC = 1 };
 
+/* App. A.3 leaf-pick variants (pipnn_params.pick_direction, pipnn_leaf_pick's direction). */
+enum { PIPNN_PICK_BIDIRECTED = 0, PIPNN_PICK_DIRECTED = 1, PIPNN_PICK_INVERTED = 2 };
+
 /* Operand precision of the leaf Gram GEMM on the tensor cores (Sec. 4.2 forms the leaf's
  * all-pairs distances with a GEMM; the conclusion names quantised GEMMs as the next step).
  * Every precision gives the same picks -- those of the defining binary32 / exact-integer
@@ -121,6 +124,10 @@ typedef struct pipnn_params {
                                the history independence of Alg. 3 (Sec. 3) the graph does not
                                depend on the split.  0: as many members as the free device
                                memory holds (one wave whenever everything fits).              */
+    int32_t pick_direction; /* App. A.3 leaf-pick variant: PIPNN_PICK_BIDIRECTED (Sec. 4.2's
+                               choice: both edges of every picked pair), PIPNN_PICK_DIRECTED
+                               (only member -> neighbour: the neighbour enters the member's
+                               reservoir) or PIPNN_PICK_INVERTED (only neighbour -> member)  */
 } pipnn_params;
 
 /* Output graph: ids[v*R + j] for j < deg[v] are v's out-neighbours in prune order; the rest of
@@ -198,12 +205,12 @@ void pipnn_leaves_free(pipnn_leaves *leaves);
 /* A2-A4 -- for every leaf (offsets/members as produced by pipnn_partition, device, distinct
  * members), the k nearest other members of every member by (dissimilarity, id), emitted in both
  * directions (Sec. 4.2, App. A.3): 2 * |b| * min(k, |b|-1) edges per leaf, in no particular
- * order.  engine: PIPNN_LEAF_SIMT or PIPNN_LEAF_TC; prec: PIPNN_PREC_* (float data on the
+ * order; direction PIPNN_PICK_DIRECTED / _INVERTED keeps one edge of each pair (half as many).  engine: PIPNN_LEAF_SIMT or PIPNN_LEAF_TC; prec: PIPNN_PREC_* (float data on the
  * tensor cores needs BF16, FP8 or BF16X3; the edges are the same for every engine and precision).  Free
  * the result with pipnn_edges_free. */
 int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
                     const uint64_t *offsets, const uint32_t *members, uint64_t num_leaves,
-                    uint32_t k, int32_t engine, int32_t prec, pipnn_edges *out);
+                    uint32_t k, int32_t engine, int32_t prec, int32_t direction, pipnn_edges *out);
 void pipnn_edges_free(pipnn_edges *edges);
 
 /* The leaf dissimilarities as the reduced-precision tensor-core engine forms them (Sec. 4.2's

@@ -34,7 +34,8 @@ class Params(C.Structure):
     _fields_ = [("c_max", C.c_uint32), ("c_min", C.c_uint32), ("max_leaders", C.c_uint32),
                 ("p_samp", C.c_float), ("fanout", C.c_uint32 * 4), ("fanout_levels", C.c_uint32),
                 ("leaf_k", C.c_uint32), ("hash_bits", C.c_uint32), ("l_max", C.c_uint32),
-                ("R", C.c_uint32), ("alpha", C.c_float), ("final_prune", C.c_int32)]
+                ("R", C.c_uint32), ("alpha", C.c_float), ("final_prune", C.c_int32),
+                ("pick_direction", C.c_int32)]
 
 
 class _Leaves(C.Structure):
@@ -52,8 +53,11 @@ class _Stats(C.Structure):
                 ("candidates", C.c_uint64)]
 
 
+BIDIRECTED, DIRECTED, INVERTED = 0, 1, 2
+
+
 def params(c_max=1024, c_min=None, max_leaders=1000, p_samp=0.005, fanout=(2,), leaf_k=2,
-           hash_bits=12, l_max=64, R=64, alpha=1.2, final_prune=True) -> Params:
+           hash_bits=12, l_max=64, R=64, alpha=1.2, final_prune=True, pick_direction=BIDIRECTED) -> Params:
     p = Params()
     p.c_max = c_max
     p.c_min = c_max // 16 if c_min is None else c_min
@@ -68,6 +72,7 @@ def params(c_max=1024, c_min=None, max_leaders=1000, p_samp=0.005, fanout=(2,), 
     p.R = R
     p.alpha = alpha
     p.final_prune = 1 if final_prune else 0
+    p.pick_direction = pick_direction
     return p
 
 
@@ -89,7 +94,7 @@ def lib():
         L.orc_partition.argtypes = [vp, u64, u32, i32, i32, C.POINTER(Params), u64, C.POINTER(_Leaves)]
         L.orc_leaves_free.argtypes = [C.POINTER(_Leaves)]
         L.orc_leaves_free.restype = None
-        L.orc_leaf_pick.argtypes = [vp, u64, u32, i32, i32, vp, vp, u64, u32, C.POINTER(_Edges)]
+        L.orc_leaf_pick.argtypes = [vp, u64, u32, i32, i32, vp, vp, u64, u32, i32, C.POINTER(_Edges)]
         L.orc_edges_free.argtypes = [C.POINTER(_Edges)]
         L.orc_edges_free.restype = None
         for f in (L.orc_hashprune_stream, L.orc_hashprune_closed):
@@ -176,15 +181,16 @@ def partition(X, bp: Params, seed, metric=L2):
     return off, mem, levels
 
 
-def leaf_pick(X, off, mem, k=2, metric=L2):
-    """Bi-directed k-NN candidates (dst, src, dist) of every leaf."""
+def leaf_pick(X, off, mem, k=2, metric=L2, direction=BIDIRECTED):
+    """k-NN candidates (dst, src, dist) of every leaf: bi-directed (Sec. 4.2), or App. A.3's
+    directed (dst = the member, src = its neighbour) or inverted (the reverse) variant."""
     X = np.ascontiguousarray(X)
     n, d = X.shape
     off = np.ascontiguousarray(off, dtype=np.uint32)
     mem = np.ascontiguousarray(mem, dtype=np.uint32)
     out = _Edges()
     _check(lib().orc_leaf_pick(_p(X), n, d, _dtype_code(X), metric, _p(off), _p(mem),
-                               len(off) - 1, k, C.byref(out)), "leaf_pick")
+                               len(off) - 1, k, direction, C.byref(out)), "leaf_pick")
     try:
         cnt = out.count
         if cnt:
@@ -277,7 +283,7 @@ def build_replicated(X, bp: Params, H, seed, replicas, metric=L2):
     parts = []
     for r in range(replicas):
         off, mem, _ = partition(X, bp, replica_seed(seed, r), metric)
-        parts.append(leaf_pick(X, off, mem, k=bp.leaf_k, metric=metric))
+        parts.append(leaf_pick(X, off, mem, k=bp.leaf_k, metric=metric, direction=bp.pick_direction))
     dst, src, dist = (np.concatenate([p[i] for p in parts]) for i in range(3))
     res, cnt = hashprune_closed(dst, src, dist, S, n, bp.l_max)
     if bp.final_prune:

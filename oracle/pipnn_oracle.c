@@ -51,6 +51,7 @@ typedef struct {
     uint32_t leaf_k, hash_bits, l_max, R;
     float alpha;
     int32_t final_prune;
+    int32_t pick_direction; /* App. A.3: 0 bi-directed k-NN, 1 directed k-NN, 2 inverted k-NN */
 } orc_params;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -493,6 +494,7 @@ static int params_ok(const orc_params *bp)
     if (bp->hash_bits < 1 || bp->hash_bits > 16) return 0;
     if (bp->l_max < 1 || bp->l_max > 1024 || bp->R < 1 || bp->R > bp->l_max) return 0;
     if (!(bp->alpha >= 1.0f)) return 0;
+    if (bp->pick_direction < 0 || bp->pick_direction > 2) return 0;
     return 1;
 }
 
@@ -542,7 +544,9 @@ void orc_leaves_free(orc_leaves *l)
 /* ------------------------------------------------------------------------------------------ */
 /* Pick (Sec. 4.2, App. A.3): for every member i of a leaf, its k nearest other members by     */
 /* (dissimilarity, id); every picked pair (i, j) yields the candidates j -> reservoir(i) and   */
-/* i -> reservoir(j) ("bi-directed k-NN").  A leaf with repeated ids counts each id once.      */
+/* i -> reservoir(j) ("bi-directed k-NN").  App. A.3's variants keep one of the two: the       */
+/* directed k-NN the edge from i to its neighbour j (j -> reservoir(i)), the inverted k-NN the */
+/* edge to i from j (i -> reservoir(j)).  A leaf with repeated ids counts each id once.        */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
     uint32_t *dst, *src;
@@ -551,9 +555,10 @@ typedef struct {
 } orc_edges;
 
 int orc_leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const uint32_t *off,
-                  const uint32_t *mem, uint64_t nleaves, uint32_t k, orc_edges *out)
+                  const uint32_t *mem, uint64_t nleaves, uint32_t k, int direction, orc_edges *out)
 {
-    if (!out || !X || !off || !mem || k < 1 || k > 16) return ORC_EINVAL;
+    if (!out || !X || !off || !mem || k < 1 || k > 16 || direction < 0 || direction > 2) return ORC_EINVAL;
+    const uint64_t per_pick = direction == 0 ? 2 : 1;
     memset(out, 0, sizeof(*out));
     uint64_t *cnt = (uint64_t *)calloc(nleaves + 1, sizeof(uint64_t));
     uint32_t **uniq = (uint32_t **)calloc(nleaves ? nleaves : 1, sizeof(uint32_t *));
@@ -573,7 +578,7 @@ int orc_leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, 
         }
         usz[b] = u;
         uint64_t kk = u > 0 ? (u - 1 < k ? u - 1 : k) : 0;
-        cnt[b + 1] = cnt[b] + 2 * u * kk;
+        cnt[b + 1] = cnt[b] + per_pick * u * kk;
     }
     if (!err) {
         uint64_t total = cnt[nleaves];
@@ -607,8 +612,12 @@ int orc_leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, 
                     bd[pos] = dv; bid[pos] = id;
                 }
                 for (uint32_t t = 0; t < have; t++) {
-                    out->dst[w] = m[i]; out->src[w] = bid[t]; out->dist[w] = (float)bd[t]; w++;
-                    out->dst[w] = bid[t]; out->src[w] = m[i]; out->dist[w] = (float)bd[t]; w++;
+                    if (direction != 2) {  /* the edge from i to its neighbour */
+                        out->dst[w] = m[i]; out->src[w] = bid[t]; out->dist[w] = (float)bd[t]; w++;
+                    }
+                    if (direction != 1) {  /* the edge to i from its neighbour */
+                        out->dst[w] = bid[t]; out->src[w] = m[i]; out->dist[w] = (float)bd[t]; w++;
+                    }
                 }
             }
         }
@@ -941,7 +950,7 @@ int orc_build(const void *X, uint64_t n, uint32_t d, int dtype, int metric, cons
     if (!rc) rc = orc_partition(X, n, d, dtype, metric, bp, seed, &L);
     if (rc) { free(S); return rc; }
     orc_edges E;
-    rc = orc_leaf_pick(X, n, d, dtype, metric, L.off, L.mem, L.nleaves, bp->leaf_k, &E);
+    rc = orc_leaf_pick(X, n, d, dtype, metric, L.off, L.mem, L.nleaves, bp->leaf_k, bp->pick_direction, &E);
     if (st) {
         st->leaves = L.nleaves;
         st->leaf_members = L.nmem;

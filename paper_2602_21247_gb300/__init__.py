@@ -27,6 +27,7 @@ PIPNN_F32, PIPNN_U8, PIPNN_I8 = 0, 1, 2
 PIPNN_L2, PIPNN_IP = 0, 1
 PIPNN_LEAF_SIMT, PIPNN_LEAF_TC = 0, 1
 PIPNN_PREC_FP32, PIPNN_PREC_BF16, PIPNN_PREC_FP8, PIPNN_PREC_INT8, PIPNN_PREC_BF16X3 = 0, 1, 2, 3, 4
+PIPNN_PICK_BIDIRECTED, PIPNN_PICK_DIRECTED, PIPNN_PICK_INVERTED = 0, 1, 2
 PIPNN_OK = 0
 
 # symbols declared in include/pipnn.h
@@ -48,7 +49,8 @@ class pipnn_params(C.Structure):
                 ("leaf_k", C.c_uint32), ("hash_bits", C.c_uint32), ("l_max", C.c_uint32),
                 ("R", C.c_uint32), ("alpha", C.c_float), ("final_prune", C.c_int32),
                 ("dtype", C.c_int32), ("leaf_engine", C.c_int32), ("hyperplanes", C.c_void_p),
-                ("replicas", C.c_uint32), ("prec", C.c_int32), ("wave_members", C.c_uint64)]
+                ("replicas", C.c_uint32), ("prec", C.c_int32), ("wave_members", C.c_uint64),
+                ("pick_direction", C.c_int32)]
 
 
 class pipnn_graph(C.Structure):
@@ -92,7 +94,7 @@ def lib():
         L.pipnn_partition.argtypes = [vp, u64, u32, i32, C.POINTER(pipnn_params), u64, C.POINTER(pipnn_leaves)]
         L.pipnn_leaves_free.argtypes = [C.POINTER(pipnn_leaves)]
         L.pipnn_leaves_free.restype = None
-        L.pipnn_leaf_pick.argtypes = [vp, u64, u32, i32, i32, vp, vp, u64, u32, i32, i32, C.POINTER(pipnn_edges)]
+        L.pipnn_leaf_pick.argtypes = [vp, u64, u32, i32, i32, vp, vp, u64, u32, i32, i32, i32, C.POINTER(pipnn_edges)]
         L.pipnn_leaf_gram.argtypes = [vp, u64, u32, i32, vp, vp, u64, i32, vp]
         L.pipnn_edges_free.argtypes = [C.POINTER(pipnn_edges)]
         L.pipnn_edges_free.restype = None
@@ -153,7 +155,8 @@ def _take(ptr, count, typestr, view=None):
 
 def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.005, fanout=(2,), leaf_k=2,
            hash_bits=12, l_max=64, R=64, alpha=1.2, final_prune=True, leaf_engine=PIPNN_LEAF_SIMT,
-           hyperplanes=None, replicas=1, prec=PIPNN_PREC_FP32, wave_members=0) -> pipnn_params:
+           hyperplanes=None, replicas=1, prec=PIPNN_PREC_FP32, wave_members=0,
+           pick_direction=PIPNN_PICK_BIDIRECTED) -> pipnn_params:
     """BP of Alg. 4.  `hyperplanes` (hash_bits x d float32, numpy or torch) must stay alive for the call."""
     p = pipnn_params()
     p.c_max = c_max
@@ -175,6 +178,7 @@ def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.0
     p.replicas = replicas
     p.prec = prec
     p.wave_members = wave_members
+    p.pick_direction = pick_direction
     p._keep = hyperplanes
     return p
 
@@ -216,13 +220,13 @@ def pipnn_partition(points: torch.Tensor, bp: pipnn_params, seed: int, metric=PI
 
 
 def pipnn_leaf_pick(points: torch.Tensor, offsets: torch.Tensor, members: torch.Tensor, k=2, metric=PIPNN_L2,
-                    engine=PIPNN_LEAF_SIMT, prec=PIPNN_PREC_FP32):
+                    engine=PIPNN_LEAF_SIMT, prec=PIPNN_PREC_FP32, direction=PIPNN_PICK_BIDIRECTED):
     """A2-A4: returns (dst uint32, src uint32, dist float32) candidate edges."""
     n, d = points.shape
     out = pipnn_edges()
     pipnn_set_stream()
     _check(lib().pipnn_leaf_pick(_ptr(points), n, d, dtype_code(points), metric, _ptr(offsets), _ptr(members),
-                                 offsets.numel() - 1, k, engine, prec, C.byref(out)))
+                                 offsets.numel() - 1, k, engine, prec, direction, C.byref(out)))
     try:
         dst = _take(out.dst, out.count, "<i4", torch.uint32)
         src = _take(out.src, out.count, "<i4", torch.uint32)

@@ -16,7 +16,7 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
                      const pipnn_params *bp, uint64_t seed, pipnn_leaves *out);
 int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
               const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, int prec,
-              pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows);
+              int direction, pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows);
 int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
                     uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt);
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
@@ -88,6 +88,8 @@ int check_params(const pipnn_params *bp) {
         return set_error(PIPNN_EINVAL, "unknown leaf_engine %d", bp->leaf_engine);
     if (!bp->hyperplanes) return set_error(PIPNN_EINVAL, "hyperplanes is NULL");
     if (bp->replicas > 16) return set_error(PIPNN_EINVAL, "replicas above 16");
+    if (bp->pick_direction < PIPNN_PICK_BIDIRECTED || bp->pick_direction > PIPNN_PICK_INVERTED)
+        return set_error(PIPNN_EINVAL, "unknown pick_direction %d", bp->pick_direction);
     if (bp->prec < PIPNN_PREC_FP32 || bp->prec > PIPNN_PREC_BF16X3) return set_error(PIPNN_EINVAL, "unknown prec %d", bp->prec);
     if (bp->dtype == PIPNN_F32 && bp->prec == PIPNN_PREC_INT8)
         return set_error(PIPNN_EUNSUPPORTED, "PIPNN_PREC_INT8 takes byte data");
@@ -307,7 +309,8 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
                 uint32_t leaf_launches = 0;
                 uint64_t full_rows = 0;
                 rc = leaf_pick(X, n, d, dtype, metric, sqn_bytes, off_w, leaves.members + hoff[b0], Lw, bp->leaf_k,
-                               bp->leaf_engine, bp->prec, &edges, &leaf_ms, &leaf_launches, &full_rows);
+                               bp->leaf_engine, bp->prec, bp->pick_direction, &edges, &leaf_ms, &leaf_launches,
+                               &full_rows);
                 st.leaf_full_rows += full_rows;
                 st.ms_leaf_kernel += leaf_ms;
                 st.leaf_kernel_launches += leaf_launches;
@@ -453,7 +456,7 @@ void pipnn_leaves_free(pipnn_leaves *l) {
 
 int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric, const uint64_t *offsets,
                     const uint32_t *members, uint64_t num_leaves, uint32_t k, int32_t engine, int32_t prec,
-                    pipnn_edges *out) {
+                    int32_t direction, pipnn_edges *out) {
     if (!out) return set_error(PIPNN_EINVAL, "out is NULL");
     memset(out, 0, sizeof(*out));
     CallScope cs;
@@ -463,8 +466,8 @@ int pipnn_leaf_pick(const void *points, uint64_t n, uint32_t d, int32_t dtype, i
     if (k < 1 || k > 16) return set_error(PIPNN_EINVAL, "k outside 1..16");
     if (engine != PIPNN_LEAF_SIMT && engine != PIPNN_LEAF_TC) return set_error(PIPNN_EINVAL, "unknown engine");
     if (prec < PIPNN_PREC_FP32 || prec > PIPNN_PREC_BF16X3) return set_error(PIPNN_EINVAL, "unknown prec %d", prec);
-    return leaf_pick(points, n, d, dtype, metric, nullptr, offsets, members, num_leaves, k, engine, prec, out, nullptr,
-                     nullptr, nullptr);
+    return leaf_pick(points, n, d, dtype, metric, nullptr, offsets, members, num_leaves, k, engine, prec, direction,
+                     out, nullptr, nullptr, nullptr);
 }
 
 int pipnn_leaf_gram(const void *points, uint64_t n, uint32_t d, int32_t metric, const uint64_t *offsets,

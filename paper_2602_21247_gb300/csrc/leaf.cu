@@ -38,9 +38,22 @@ __global__ void leaf_sizes(const uint64_t *off, uint64_t L, uint32_t k, uint32_t
 }
 }  // namespace
 
+// App. A.3 variants: every engine writes the two edges of a picked pair at (2e, 2e + 1) --
+// member -> neighbour first -- so a directed or inverted pick keeps one parity.
+__global__ void keep_direction(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t half,
+                               uint32_t parity, uint32_t *od, uint32_t *os, float *ow) {
+    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < half; e += (uint64_t)gridDim.x * blockDim.x) {
+        od[e] = dst[2 * e + parity];
+        os[e] = src[2 * e + parity];
+        ow[e] = dist[2 * e + parity];
+    }
+}
+
 int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
               const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, int prec,
-              pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows) {
+              int direction, pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows) {
+    if (direction < PIPNN_PICK_BIDIRECTED || direction > PIPNN_PICK_INVERTED)
+        return set_error(PIPNN_EINVAL, "unknown pick direction %d", direction);
     if (full_rows) *full_rows = 0;
     if (engine == PIPNN_LEAF_TC && dtype == PIPNN_F32 && prec != PIPNN_PREC_BF16 && prec != PIPNN_PREC_FP8 &&
         prec != PIPNN_PREC_BF16X3)
@@ -123,6 +136,35 @@ int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, cons
         dev_free_raw(src);
         dev_free_raw(dist);
         return rc;
+    }
+    if (direction != PIPNN_PICK_BIDIRECTED) {
+        uint32_t *d2 = nullptr, *s2 = nullptr;
+        float *w2 = nullptr;
+        const uint64_t half = E / 2;
+        rc = dev_alloc_raw((void **)&d2, half * 4);
+        if (rc == PIPNN_OK) rc = dev_alloc_raw((void **)&s2, half * 4);
+        if (rc == PIPNN_OK) rc = dev_alloc_raw((void **)&w2, half * 4);
+        if (rc == PIPNN_OK && half) {
+            keep_direction<<<grid_for(half, 256), 256, 0, stream()>>>(dst, src, dist, half,
+                                                                      direction == PIPNN_PICK_DIRECTED ? 0u : 1u, d2,
+                                                                      s2, w2);
+            count_launch();
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "keep_direction: %s", cudaGetErrorString(e));
+        }
+        dev_free_raw(dst);
+        dev_free_raw(src);
+        dev_free_raw(dist);
+        if (rc != PIPNN_OK) {
+            dev_free_raw(d2);
+            dev_free_raw(s2);
+            dev_free_raw(w2);
+            return rc;
+        }
+        dst = d2;
+        src = s2;
+        dist = w2;
+        E = half;
     }
     out->dst = dst;
     out->src = src;

@@ -52,7 +52,8 @@ def test_params_struct_matches_header_layout():
     assert pk.pipnn_params.replicas.offset == 80
     assert pk.pipnn_params.prec.offset == 84
     assert pk.pipnn_params.wave_members.offset == 88
-    assert ctypes.sizeof(pk.pipnn_params) == 96
+    assert pk.pipnn_params.pick_direction.offset == 96
+    assert ctypes.sizeof(pk.pipnn_params) == 104
 
 
 def test_batched_build_argument_checks_need_no_gpu():

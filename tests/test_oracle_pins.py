@@ -538,3 +538,44 @@ def test_knn_bytes_equals_plain_knn_and_brute_force(dtype):
     D = ((Q[:, None, :].astype(np.int64) - X[None, :, :].astype(np.int64)) ** 2).sum(2)
     brute = np.lexsort((np.broadcast_to(np.arange(X.shape[0]), D.shape), D), axis=1)[:, :10]
     assert np.array_equal(got, brute)
+
+
+# --------------------------------------------------------------------------------------------
+# App. A.3 pick variants: directed, inverted and bi-directed k-NN
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_pick_directions(k):
+    X = synth.uniform_points(400, 16, synth.U8, lo=0, hi=6, seed=23)  # many ties
+    rng = np.random.default_rng(k)
+    sizes = [1, 2, 3, 40, 157, 199]
+    mem = np.concatenate([rng.choice(400, s, replace=False) for s in sizes]).astype(np.uint32)
+    off = np.cumsum([0] + sizes).astype(np.uint32)
+    fwd = oracle.leaf_pick(X, off, mem, k=k, direction=oracle.DIRECTED)
+    inv = oracle.leaf_pick(X, off, mem, k=k, direction=oracle.INVERTED)
+    bi = oracle.leaf_pick(X, off, mem, k=k)
+    # directed: exactly each member's k nearest other members by (distance, id), brute force
+    want = []
+    for b in range(len(sizes)):
+        m = mem[off[b]:off[b + 1]].astype(np.int64)
+        D = ((X[m][:, None, :].astype(np.int64) - X[m][None, :, :].astype(np.int64)) ** 2).sum(2)
+        for i in range(len(m)):
+            order = sorted((int(D[i, j]), int(m[j])) for j in range(len(m)) if j != i)
+            for dv, j in order[:k]:
+                want.append((int(m[i]), j, dv))
+    got = [(int(a), int(b_), int(c)) for a, b_, c in zip(*fwd)]
+    assert sorted(got) == sorted(want)  # as lists: a point in two leaves yields its edges twice
+    # inverted is directed with every edge reversed; bi-directed is the union of both, as lists
+    assert sorted(zip(inv[1].tolist(), inv[0].tolist(), inv[2].tolist())) == \
+        sorted(zip(fwd[0].tolist(), fwd[1].tolist(), fwd[2].tolist()))
+    both = sorted(zip(*[np.concatenate([f, i_]).tolist() for f, i_ in zip(fwd, inv)]))
+    assert both == sorted(zip(*[a.tolist() for a in bi]))
+
+
+def test_build_with_pick_directions_runs_and_differs():
+    X = synth.mixture(3000, 32, synth.U8, 20, 10.0, seed=24)
+    H = synth.hyperplanes(12, 32, seed=3)
+    graphs = [oracle.build(X, oracle.params(c_max=256, fanout=(3,), l_max=32, R=24, pick_direction=m), H, 5)
+              for m in (oracle.BIDIRECTED, oracle.DIRECTED, oracle.INVERTED)]
+    st = [g[2]["candidates"] for g in graphs]
+    assert st[0] == st[1] + st[2] and st[1] == st[2]
+    assert not np.array_equal(graphs[1][0], graphs[2][0])
