@@ -521,7 +521,11 @@ def main():
                              f"leaf_gram_tc_{args.workload}.md")
     if args.profile:
         if rank == 0:
-            print(json.dumps({"profile_run": True, "ms_per_step": ms, "phases_ms": phases(stats)}), flush=True)
+            st = stats[-1]
+            print(json.dumps({"profile_run": True, "ms_per_step": ms, "phases_ms": phases(stats),
+                              "leaf_pairs": st["leaf_pairs"], "leaf_members": st["leaf_members"],
+                              "leaves": st["leaves"], "candidates": st["candidates"],
+                              "waves": st["waves"]}), flush=True)
         return 0
 
     # end to end through the public call: pinned host input, host output, copies inside the region
