@@ -294,6 +294,14 @@ int pipnn_build_into(const void *points, uint64_t n, uint32_t d, int32_t metric,
  * the memory to another allocator.  Synchronises the device. */
 int pipnn_trim_pool(void);
 
+/* Failure injection for tests (no counterpart in the paper).  pipnn_debug_set_alloc_limit caps
+ * the device bytes the library may allocate from now on (0 lifts the cap); an allocation beyond
+ * it fails exactly as a failed cudaMallocAsync does (PIPNN_ENOMEM, nothing partial returned).
+ * pipnn_debug_wait_probe runs the engines' bounded device-side wait on an mbarrier that nothing
+ * completes: after limit_ns it must return PIPNN_ETIMEOUT, with the context still usable. */
+int pipnn_debug_set_alloc_limit(uint64_t bytes);
+int pipnn_debug_wait_probe(uint64_t limit_ns);
+
 /* Statistics of the last successful pipnn_build / pipnn_build_into on the calling thread. */
 int pipnn_get_stats(pipnn_stats *out);
 

@@ -34,7 +34,7 @@ PIPNN_OK = 0
 EXPORTS = ("pipnn_set_stream", "pipnn_last_error", "pipnn_sketch", "pipnn_partition", "pipnn_leaves_free",
            "pipnn_leaf_pick", "pipnn_edges_free", "pipnn_hashprune", "pipnn_final_prune", "pipnn_build",
            "pipnn_free", "pipnn_build_into", "pipnn_get_stats", "pipnn_hashprune_noalloc", "pipnn_build_batched",
-           "pipnn_leaf_gram", "pipnn_trim_pool")
+           "pipnn_leaf_gram", "pipnn_trim_pool", "pipnn_debug_set_alloc_limit", "pipnn_debug_wait_probe")
 
 
 class PipnnError(RuntimeError):
@@ -108,6 +108,8 @@ def lib():
         L.pipnn_build_batched.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_uint64), u32, u32, i32,
                                           C.POINTER(pipnn_params), C.POINTER(C.c_uint64), C.POINTER(pipnn_graph)]
         L.pipnn_get_stats.argtypes = [C.POINTER(pipnn_stats)]
+        L.pipnn_debug_set_alloc_limit.argtypes = [u64]
+        L.pipnn_debug_wait_probe.argtypes = [u64]
         _lib = L
     return _lib
 
@@ -346,6 +348,17 @@ def pipnn_build_batched(points_list, bp: pipnn_params, seeds, metric=PIPNN_L2):
         for i in range(count):
             lib().pipnn_free(C.byref(outs[i]))
     return graphs
+
+
+def pipnn_debug_set_alloc_limit(nbytes):
+    """Caps the device bytes the library may allocate (0 lifts the cap): failure injection."""
+    _check(lib().pipnn_debug_set_alloc_limit(int(nbytes)))
+
+
+def pipnn_debug_wait_probe(limit_ns):
+    """The engines' bounded wait on an mbarrier nothing completes; raises PipnnError(-4) after
+    limit_ns."""
+    _check(lib().pipnn_debug_wait_probe(int(limit_ns)))
 
 
 def pipnn_trim_pool():

@@ -13,7 +13,7 @@ void set_device_error_word(unsigned *p);
 int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float *H, uint32_t m, float *S,
                   void *sqnorm);
 int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out);
+                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out, uint16_t *level0_code);
 int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
               const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, int prec,
               int direction, pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows);
@@ -21,7 +21,8 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
                     uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt);
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                 const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, int engine,
-                uint32_t *adj, uint32_t *deg);
+                uint32_t *adj, uint32_t *deg, const uint32_t *order);
+int order_by_code(const uint16_t *code, uint64_t n, uint32_t *order, Workspace &ws);
 int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, uint32_t *adj,
                     uint32_t *deg);
 int leaf_gram_tcf(const float *X, uint32_t d, int metric, int prec, const uint64_t *off, const uint32_t *mem,
@@ -252,12 +253,16 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     PIPNN_TRY(ws.zeros(&acc, 1));
     uint64_t *res = nullptr;
     uint32_t *cnt = nullptr;
+    // every point's nearest level-0 leader: the prune visits nodes grouped by it, so nodes whose
+    // candidates share rows are pruned together (a processing order only; results do not change)
+    uint16_t *code = nullptr;
+    PIPNN_TRY(ws.zeros(&code, n));
     for (uint32_t r = 0; r < replicas; r++) {
         const uint64_t seed_r = seed + (uint64_t)r * 0x9E3779B97F4A7C15ull;
         rt[r].mark(0);
         // A1
         pipnn_leaves leaves;
-        PIPNN_TRY(partition_points(X, n, d, dtype, metric, sqn_bytes, bp, seed_r, &leaves));
+        PIPNN_TRY(partition_points(X, n, d, dtype, metric, sqn_bytes, bp, seed_r, &leaves, r == 0 ? code : nullptr));
         rt[r].mark(1);
         st.levels = leaves.levels > st.levels ? leaves.levels : st.levels;
         st.leaves += leaves.num_leaves;
@@ -347,10 +352,13 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     uint32_t *adj = nullptr, *deg = nullptr;
     PIPNN_TRY(dev_alloc_raw((void **)&adj, n * bp->R * 4));
     rc = dev_alloc_raw((void **)&deg, n * 4);
+    uint32_t *order = nullptr;
+    if (rc == PIPNN_OK) rc = ws.alloc(&order, n);
+    if (rc == PIPNN_OK) rc = order_by_code(code, n, order, ws);
     if (rc == PIPNN_OK) {
         if (bp->final_prune)
             rc = final_prune(X, n, d, dtype, metric, sqn_bytes, res, cnt, bp->l_max, bp->R, bp->alpha, bp->leaf_engine,
-                             adj, deg);
+                             adj, deg, order);
         else
             rc = reservoir_graph(n, res, cnt, bp->l_max, bp->R, adj, deg);
     }
@@ -443,7 +451,7 @@ int pipnn_partition(const void *points, uint64_t n, uint32_t d, int32_t metric, 
     PIPNN_TRY(cs.init());
     PIPNN_TRY(check_params(bp));
     PIPNN_TRY(check_points(points, n, d, bp->dtype, metric));
-    return partition_points(points, n, d, bp->dtype, metric, nullptr, bp, seed, out);
+    return partition_points(points, n, d, bp->dtype, metric, nullptr, bp, seed, out, nullptr);
 }
 
 void pipnn_leaves_free(pipnn_leaves *l) {
@@ -510,7 +518,8 @@ int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype,
     if (l_max < 1 || l_max > 256 || R < 1 || R > l_max) return set_error(PIPNN_EINVAL, "need 1 <= R <= l_max <= 256");
     if (!(alpha >= 1.0f) || !std::isfinite(alpha)) return set_error(PIPNN_EINVAL, "alpha must be finite and >= 1");
     if (engine != PIPNN_LEAF_SIMT && engine != PIPNN_LEAF_TC) return set_error(PIPNN_EINVAL, "unknown engine %d", engine);
-    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, engine, adj, deg));
+    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, engine, adj, deg,
+                          nullptr));
     return check_device_error("final prune");
 }
 

@@ -276,6 +276,42 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
             __syncwarp();
             return out < l_max ? out : l_max;
         };
+        // incremental path: a reservoir that already holds slots (from an earlier batch or wave) is
+        // sorted with distinct hash buckets, so a short run of new slots is sorted on its own and
+        // merged into it by rank (a stable merge: old before new on equal keys), then walked; the
+        // walk keeps the first slot of each bucket, which also drops exact duplicates
+        if (cur > 0 && b - a <= 32 && cur + (b - a) <= (uint64_t)HP_BUF / 2) {
+            const uint32_t nn = (uint32_t)(b - a);
+            uint64_t nk[1] = {(uint32_t)lane < nn ? slots[a + lane] : ~0ull};
+            warp_sort_regs<1>(nk, lane);
+            // the old reservoir, in the upper half of the buffer for the new slots' rank search
+            uint64_t *old = buf + HP_BUF / 2;
+            for (uint32_t t = lane; t < cur; t += 32) old[t] = res[v * l_max + t];
+            __syncwarp();
+            // each old slot's position: its index plus the new slots strictly below it
+            for (uint32_t t = lane; t < cur; t += 32) {
+                const uint64_t x = old[t];
+                uint32_t below = 0;
+                for (uint32_t q = 0; q < nn; q++) below += __shfl_sync(0xffffffffu, nk[0], q) < x ? 1u : 0u;
+                buf[t + below] = x;
+            }
+            // each new slot's position: its rank plus the old slots at or below it (binary search)
+            if ((uint32_t)lane < nn) {
+                uint32_t lo = 0, hi = cur;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (old[mid] <= nk[0]) lo = mid + 1;
+                    else hi = mid;
+                }
+                buf[lane + lo] = nk[0];
+            }
+            __syncwarp();
+            cur = walk(cur + nn);
+            for (uint32_t t = lane; t < l_max; t += 32) res[v * l_max + t] = t < cur ? buf[t] : ~0ull;
+            if (lane == 0) cnt[v] = cur;
+            __syncwarp();
+            continue;
+        }
         // fast path: the distinct slots (old reservoir and new run) through the hash set, sorted
         // in registers when at most HP_DISTINCT; exact duplicates are interchangeable, so dropping
         // them leaves the walk's result unchanged.  (A valid slot is never all ones: its id is < n.)

@@ -61,6 +61,13 @@ unsigned *device_error_word();
 int check_device_error(const char *where);   // synchronises the stream
 
 // ---------------------------------------------------------------------------------------------
+// Failure injection on the host (pipnn_debug_set_alloc_limit): every device allocation of the
+// library is charged against an optional byte budget and fails with PIPNN_ENOMEM once the budget
+// is spent, exactly as a failing cudaMallocAsync would.
+// ---------------------------------------------------------------------------------------------
+bool alloc_budget_take(size_t bytes);
+
+// ---------------------------------------------------------------------------------------------
 // Stream-ordered device allocations released when the owning Workspace goes out of scope.
 // ---------------------------------------------------------------------------------------------
 class Workspace {
@@ -74,6 +81,9 @@ class Workspace {
         *p = nullptr;
         if (count == 0) count = 1;
         void *q = nullptr;
+        if (!alloc_budget_take(count * sizeof(T)))
+            return set_error(PIPNN_ENOMEM, "device allocation of %zu bytes refused: allocation budget spent",
+                             count * sizeof(T));
         cudaError_t e = cudaMallocAsync(&q, count * sizeof(T), stream());
         if (e != cudaSuccess) {
             cudaGetLastError();

@@ -787,6 +787,43 @@ __device__ __forceinline__ void defined_dis(const float *xi, const float *const 
     }
 }
 
+// The same chain reading four coordinates per load (d a multiple of four: every row starts on a
+// 16-byte boundary); the fused multiply-adds still run one coordinate at a time in index order.
+template <int MET, int NC>
+__device__ __forceinline__ void defined_dis4(const float *xi, const float *const (&xj)[NC], uint32_t d, uint32_t nc,
+                                             float (&acc)[NC]) {
+#pragma unroll
+    for (int p = 0; p < NC; p++) acc[p] = 0.0f;
+    for (uint32_t t = 0; t < d; t += 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(xi + t));
+#pragma unroll
+        for (int p = 0; p < NC; p++) {
+            if ((uint32_t)p < nc) {
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(xj[p] + t));
+                if (MET == PIPNN_L2) {
+                    float df = __fsub_rn(a.x, b.x);
+                    acc[p] = __fmaf_rn(df, df, acc[p]);
+                    df = __fsub_rn(a.y, b.y);
+                    acc[p] = __fmaf_rn(df, df, acc[p]);
+                    df = __fsub_rn(a.z, b.z);
+                    acc[p] = __fmaf_rn(df, df, acc[p]);
+                    df = __fsub_rn(a.w, b.w);
+                    acc[p] = __fmaf_rn(df, df, acc[p]);
+                } else {
+                    acc[p] = __fmaf_rn(a.x, b.x, acc[p]);
+                    acc[p] = __fmaf_rn(a.y, b.y, acc[p]);
+                    acc[p] = __fmaf_rn(a.z, b.z, acc[p]);
+                    acc[p] = __fmaf_rn(a.w, b.w, acc[p]);
+                }
+            }
+        }
+    }
+    if (MET == PIPNN_IP) {
+#pragma unroll
+        for (int p = 0; p < NC; p++) acc[p] = __fsub_rn(1.0f, acc[p]);
+    }
+}
+
 __device__ __forceinline__ uint64_t dis_key(float D, uint32_t id) { return ((uint64_t)f32_order(D) << 32) | id; }
 
 __device__ __forceinline__ void emit_pair(uint32_t *dst, uint32_t *src, float *dist, uint64_t w, uint32_t me,
@@ -802,10 +839,12 @@ __device__ __forceinline__ void emit_pair(uint32_t *dst, uint32_t *src, float *d
 }
 
 // One block per unit, one thread per row: the row's listed candidates, evaluated exactly.
+// vec4: d is a multiple of four and X starts on a 16-byte boundary (four coordinates per load).
 template <int MET, int KP>
-__global__ void __launch_bounds__(128) rerank_rows(const float *X, uint32_t d, const TcUnitF *units, uint64_t nunits,
-                                                   const uint32_t *members, const uint16_t *cand, const uint8_t *ccnt,
-                                                   uint32_t k, uint32_t *out_dst, uint32_t *out_src, float *out_dist) {
+__global__ void __launch_bounds__(128) rerank_rows(const float *X, uint32_t d, bool vec4, const TcUnitF *units,
+                                                   uint64_t nunits, const uint32_t *members, const uint16_t *cand,
+                                                   const uint8_t *ccnt, uint32_t k, uint32_t *out_dst,
+                                                   uint32_t *out_src, float *out_dist) {
     for (uint64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
         const TcUnitF un = units[u];
         const uint32_t row = un.row0 + threadIdx.x;
@@ -825,7 +864,8 @@ __global__ void __launch_bounds__(128) rerank_rows(const float *X, uint32_t d, c
             xj[p] = X + (uint64_t)id[p] * d;
         }
         float D[KP];
-        defined_dis<MET, KP>(xi, xj, d, c, D);
+        if (vec4) defined_dis4<MET, KP>(xi, xj, d, c, D);
+        else defined_dis<MET, KP>(xi, xj, d, c, D);
         uint64_t key[KP];
 #pragma unroll
         for (int p = 0; p < KP; p++) key[p] = (uint32_t)p < c ? dis_key(D[p], id[p]) : ~0ull;
@@ -847,7 +887,7 @@ __global__ void __launch_bounds__(128) rerank_rows(const float *X, uint32_t d, c
 // One warp per listed row: every other member of the leaf, evaluated exactly; each lane keeps
 // its 16 smallest (D, id), then the warp takes the kk smallest of all lanes.
 template <int MET>
-__global__ void __launch_bounds__(256) rerank_full(const float *X, uint32_t d, const TcUnitF *units,
+__global__ void __launch_bounds__(256) rerank_full(const float *X, uint32_t d, bool vec4, const TcUnitF *units,
                                                    const uint32_t *ovf, uint32_t novf, const uint32_t *members,
                                                    const uint32_t *simt_size, uint32_t k, uint32_t *out_dst,
                                                    uint32_t *out_src, float *out_dist) {
@@ -869,7 +909,8 @@ __global__ void __launch_bounds__(256) rerank_full(const float *X, uint32_t d, c
             const uint32_t id = members[un.off + jm];
             const float *xj[1] = {X + (uint64_t)id * d};
             float D[1];
-            defined_dis<MET, 1>(xi, xj, d, 1, D);
+            if (vec4) defined_dis4<MET, 1>(xi, xj, d, 1, D);
+            else defined_dis<MET, 1>(xi, xj, d, 1, D);
             const uint64_t key = dis_key(D[0], id);
             if (key < best[15]) {
                 best[15] = key;
@@ -1183,14 +1224,15 @@ int leaf_pick_tcf(const float *X, uint64_t n, uint32_t d, int metric, int prec, 
 
     // exact re-rank of the listed candidates, then the rows listed for a full evaluation
     const unsigned gr = grid_for(ntiles, 1, 152u * 16u);
+    const bool vec4 = (d & 3u) == 0 && (reinterpret_cast<uintptr_t>(X) & 15u) == 0;
     if (metric == PIPNN_L2) {
-        if (KP == 4) rerank_rows<PIPNN_L2, 4><<<gr, 128, 0, stream()>>>(X, d, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
-        else if (KP == 8) rerank_rows<PIPNN_L2, 8><<<gr, 128, 0, stream()>>>(X, d, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
-        else rerank_rows<PIPNN_L2, 16><<<gr, 128, 0, stream()>>>(X, d, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
+        if (KP == 4) rerank_rows<PIPNN_L2, 4><<<gr, 128, 0, stream()>>>(X, d, vec4, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
+        else if (KP == 8) rerank_rows<PIPNN_L2, 8><<<gr, 128, 0, stream()>>>(X, d, vec4, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
+        else rerank_rows<PIPNN_L2, 16><<<gr, 128, 0, stream()>>>(X, d, vec4, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
     } else {
-        if (KP == 4) rerank_rows<PIPNN_IP, 4><<<gr, 128, 0, stream()>>>(X, d, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
-        else if (KP == 8) rerank_rows<PIPNN_IP, 8><<<gr, 128, 0, stream()>>>(X, d, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
-        else rerank_rows<PIPNN_IP, 16><<<gr, 128, 0, stream()>>>(X, d, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
+        if (KP == 4) rerank_rows<PIPNN_IP, 4><<<gr, 128, 0, stream()>>>(X, d, vec4, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
+        else if (KP == 8) rerank_rows<PIPNN_IP, 8><<<gr, 128, 0, stream()>>>(X, d, vec4, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
+        else rerank_rows<PIPNN_IP, 16><<<gr, 128, 0, stream()>>>(X, d, vec4, units, ntiles, mem, cand, ccnt, k, out_dst, out_src, out_dist);
     }
     PIPNN_LAUNCH_CHECK();
     unsigned hovf = 0;
@@ -1201,10 +1243,10 @@ int leaf_pick_tcf(const float *X, uint64_t n, uint32_t d, int metric, int prec, 
         PIPNN_LAUNCH_CHECK();
         const unsigned gf = grid_for((uint64_t)hovf * 32, 256);
         if (metric == PIPNN_L2)
-            rerank_full<PIPNN_L2><<<gf, 256, 0, stream()>>>(X, d, units, ovf, hovf, mem, simt_size, k, out_dst, out_src,
+            rerank_full<PIPNN_L2><<<gf, 256, 0, stream()>>>(X, d, vec4, units, ovf, hovf, mem, simt_size, k, out_dst, out_src,
                                                             out_dist);
         else
-            rerank_full<PIPNN_IP><<<gf, 256, 0, stream()>>>(X, d, units, ovf, hovf, mem, simt_size, k, out_dst, out_src,
+            rerank_full<PIPNN_IP><<<gf, 256, 0, stream()>>>(X, d, vec4, units, ovf, hovf, mem, simt_size, k, out_dst, out_src,
                                                             out_dist);
         PIPNN_LAUNCH_CHECK();
         uint32_t *sg = nullptr, *sr = nullptr;

@@ -409,8 +409,15 @@ uint32_t fanout_at(const pipnn_params *bp, uint32_t depth) {
 }
 }  // namespace
 
+// Level 0: instance i is point i; its nearest leader's rank is its first assignment slot.
+__global__ void level0_code(const uint32_t *inst, const uint16_t *assign, uint64_t N, uint32_t F, uint16_t *code) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
+        code[inst[i]] = assign[i * F];
+}
+
+// level0_code (optional, n entries): receives every point's nearest level-0 leader (its rank).
 int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out) {
+                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out, uint16_t *level0_code_out) {
     memset(out, 0, sizeof(*out));
     Workspace leaf_ws;
     std::vector<LevelLeaves> levels;
@@ -545,6 +552,11 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
                                 bucket_cnt, tw));
         } else {
             PIPNN_TRY(launch_allpairs<MODE_ASSIGN>(dtype, metric, F, a, ntiles));
+        }
+
+        if (depth == 0 && level0_code_out) {
+            level0_code<<<grid_for(N, 256), 256, 0, stream()>>>(cur->inst, assign, N, F, level0_code_out);
+            PIPNN_LAUNCH_CHECK();
         }
 
         // 3. Merge plan

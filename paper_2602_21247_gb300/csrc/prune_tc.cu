@@ -67,6 +67,7 @@ struct PtArgs {
     float alpha2, inv_alpha2;
     uint32_t *adj, *deg;
     unsigned *err;
+    const uint32_t *order;  // processing order of the nodes (a permutation of 0..n-1), or null
 };
 
 // Tile info, info warp -> gathers, MMA, epilogue: row ids (a packed node's rows start at 32q; the
@@ -202,8 +203,13 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
         // ------------------------------------------------------------ tile info (one warp)
         // Prefetch: the reservoir row, count and norm of node j + P are copied (cp.async, no
         // registers in flight) into ring slot (j + P) % P while node j is compacted.
+        // node j of this CTA: position blockIdx.x + j * gridDim.x of the processing order
+        auto node_at = [&](uint32_t j) {
+            const uint64_t idx = blockIdx.x + (uint64_t)j * gridDim.x;
+            return idx < n ? (a.order ? (uint64_t)a.order[idx] : idx) : n;
+        };
         auto fetch = [&](uint32_t j) {
-            const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
+            const uint64_t v = node_at(j);
             if (v < n) {
                 const uint32_t slot = sbase + C::OFF_PRE + (j % C::P) * C::P_BYTES;
 #pragma unroll
@@ -248,7 +254,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
         };
         for (uint32_t j = 0; j < (uint32_t)C::P; j++) fetch(j);
         for (uint32_t j = 0; !stop; j++) {
-            const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
+            const uint64_t v = node_at(j);
             if (v >= n) break;
             cp_async_wait<C::P - 1>();  // node j's group (every later one may still be in flight)
             __syncwarp();
@@ -638,7 +644,7 @@ bool prune_tc_eligible(int dtype, uint32_t d, uint64_t n, uint32_t l_max) {
 
 int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t *sqn, const uint64_t *res,
                    const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha2, uint32_t *adj, uint32_t *deg,
-                   Workspace &ws) {
+                   const uint32_t *order, Workspace &ws) {
     if (!prune_tc_eligible(dtype, d, n, l_max))
         return set_error(PIPNN_EUNSUPPORTED, "the tensor-core prune takes byte data, d <= 128, l_max <= %u", PT_MAXC);
     if (R < 1 || R > l_max) return set_error(PIPNN_EINVAL, "R outside 1..l_max");
@@ -660,6 +666,7 @@ int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32
     a.adj = adj;
     a.deg = deg;
     a.err = device_error_word();
+    a.order = order;
     if (kp == 64) return launch_pt<1>(map, a);
     return launch_pt<2>(map, a);
 }

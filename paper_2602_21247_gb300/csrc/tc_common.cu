@@ -122,4 +122,43 @@ int encode_rows_map(CUtensorMap *map, const __nv_bfloat16 *base, uint64_t n, uin
     return PIPNN_OK;
 }
 
+namespace {
+// One warp waits, through the engines' bounded wait, on an mbarrier that nothing ever arrives on.
+__global__ void wait_probe_kernel(unsigned long long limit_ns, unsigned *err) {
+    __shared__ __align__(8) unsigned long long bar_storage;
+    __shared__ int abort_flag;
+    const uint32_t bar = tc::smem_u32(&bar_storage);
+    if (threadIdx.x == 0) {
+        tc::mbar_init(bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const bool ok = tc::mbar_wait_limit(bar, 0, &abort_flag, err, limit_ns);
+    (void)__all_sync(0xffffffffu, ok);
+}
+}  // namespace
+
 }  // namespace pipnn
+
+// Exercises the bounded device-side wait that every tensor-core engine uses: a wait on an
+// mbarrier that is never completed must give up after limit_ns and report PIPNN_ETIMEOUT, and the
+// context must stay usable.  Failure detection without a fault: no GPU state is harmed.
+extern "C" int pipnn_debug_wait_probe(uint64_t limit_ns) {
+    using namespace pipnn;
+    clear_error();
+    unsigned *err = nullptr;
+    if (!alloc_budget_take(4)) return set_error(PIPNN_ENOMEM, "allocation budget spent");
+    PIPNN_CUDA(cudaMallocAsync(&err, sizeof(unsigned), stream()));
+    cudaMemsetAsync(err, 0, sizeof(unsigned), stream());
+    wait_probe_kernel<<<1, 32, 0, stream()>>>(limit_ns, err);
+    cudaError_t e = cudaGetLastError();
+    unsigned h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream());
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream());
+    cudaFreeAsync(err, stream());
+    if (e != cudaSuccess) return set_error(PIPNN_ECUDA, "wait probe: %s", cudaGetErrorString(e));
+    if (h & DERR_TIMEOUT) return set_error(PIPNN_ETIMEOUT, "wait probe: the bounded wait gave up after %llu ns",
+                                           (unsigned long long)limit_ns);
+    return PIPNN_OK;
+}

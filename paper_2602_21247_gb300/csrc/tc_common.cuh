@@ -60,22 +60,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: false if the CTA aborted or the wait ran past WAIT_NS (then the CTA is marked
+// Bounded wait: false if the CTA aborted or the wait ran past limit_ns (then the CTA is marked
 // aborted and DERR_TIMEOUT is recorded).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, unsigned *err) {
+__device__ __forceinline__ bool mbar_wait_limit(uint32_t bar, uint32_t parity, volatile int *abort, unsigned *err,
+                                                unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (uint32_t i = 1;; i++) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 63) == 0) {
             if (*abort) return false;
-            if (globaltimer() - t0 > WAIT_NS) {
+            if (globaltimer() - t0 > limit_ns) {
                 *abort = 1;
                 atomicOr(err, DERR_TIMEOUT);
                 return false;
             }
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, unsigned *err) {
+    return mbar_wait_limit(bar, parity, abort, err, WAIT_NS);
 }
 
 __device__ __forceinline__ void fence_proxy_async() {

@@ -1,6 +1,8 @@
 // util.cu -- error state, stream, device error word, prefix sums and tile tables.
 #include "internal.cuh"
 
+#include <atomic>
+
 #include <cstring>
 
 namespace pipnn {
@@ -41,8 +43,23 @@ int check_device_error(const char *where) {
     return PIPNN_OK;
 }
 
+namespace {
+std::atomic<uint64_t> g_alloc_left{~0ull};  // bytes the budget still allows; ~0 = unlimited
+}  // namespace
+
+bool alloc_budget_take(size_t bytes) {
+    uint64_t left = g_alloc_left.load();
+    for (;;) {
+        if (left == ~0ull) return true;
+        if (left < bytes) return false;
+        if (g_alloc_left.compare_exchange_weak(left, left - bytes)) return true;
+    }
+}
+
 int dev_alloc_raw(void **p, size_t bytes) {
     *p = nullptr;
+    if (!alloc_budget_take(bytes))
+        return set_error(PIPNN_ENOMEM, "device allocation of %zu bytes refused: allocation budget spent", bytes);
     cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 1, stream());
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -201,6 +218,60 @@ int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t *out, uint64_t n, ui
     return PIPNN_OK;
 }
 
+namespace {
+constexpr uint32_t CODE_BINS = 1024;
+
+// Per block, a shared histogram of its chunk's codes, added once per bin to the global counts.
+__global__ void code_hist(const uint16_t *code, uint64_t n, uint64_t chunk, unsigned long long *hist) {
+    __shared__ unsigned h[CODE_BINS];
+    for (uint32_t b = threadIdx.x; b < CODE_BINS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const uint64_t lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[code[i] & (CODE_BINS - 1)], 1u);
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < CODE_BINS; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
+}
+
+// The same chunks again: each block reserves one range per bin from the bin cursors, then places
+// its points inside (the order inside a bin is any).
+__global__ void code_place(const uint16_t *code, uint64_t n, uint64_t chunk, unsigned long long *cursor,
+                           uint32_t *order) {
+    __shared__ unsigned h[CODE_BINS];
+    __shared__ unsigned long long base[CODE_BINS];
+    for (uint32_t b = threadIdx.x; b < CODE_BINS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const uint64_t lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[code[i] & (CODE_BINS - 1)], 1u);
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < CODE_BINS; b += blockDim.x) {
+        base[b] = h[b] ? atomicAdd(&cursor[b], (unsigned long long)h[b]) : 0ull;
+        h[b] = 0;
+    }
+    __syncthreads();
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint32_t b = code[i] & (CODE_BINS - 1);
+        order[base[b] + atomicAdd(&h[b], 1u)] = (uint32_t)i;
+    }
+}
+}  // namespace
+
+int order_by_code(const uint16_t *code, uint64_t n, uint32_t *order, Workspace &ws) {
+    if (n == 0) return PIPNN_OK;
+    unsigned long long *hist, *tot;
+    PIPNN_TRY(ws.zeros(&hist, CODE_BINS));
+    PIPNN_TRY(ws.alloc(&tot, 1));
+    const uint64_t chunk = 1ull << 16;
+    const uint64_t blocks = (n + chunk - 1) / chunk;
+    code_hist<<<(unsigned)blocks, 512, 0, stream()>>>(code, n, chunk, hist);
+    PIPNN_LAUNCH_CHECK();
+    PIPNN_TRY(exclusive_scan_u64(reinterpret_cast<uint64_t *>(hist), reinterpret_cast<uint64_t *>(hist), CODE_BINS,
+                                 reinterpret_cast<uint64_t *>(tot), ws));
+    code_place<<<(unsigned)blocks, 512, 0, stream()>>>(code, n, chunk, hist, order);
+    PIPNN_LAUNCH_CHECK();
+    return PIPNN_OK;
+}
+
 int make_tiles(const uint32_t *size, uint64_t groups, uint32_t tile, uint32_t **tile_grp,
                uint32_t **tile_row0, uint64_t *num_tiles, Workspace &ws) {
     *num_tiles = 0;
@@ -223,3 +294,8 @@ int make_tiles(const uint32_t *size, uint64_t groups, uint32_t tile, uint32_t **
 }
 
 }  // namespace pipnn
+
+extern "C" int pipnn_debug_set_alloc_limit(uint64_t bytes) {
+    pipnn::g_alloc_left.store(bytes ? bytes : ~0ull);
+    return PIPNN_OK;
+}
