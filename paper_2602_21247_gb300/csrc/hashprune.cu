@@ -288,12 +288,14 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
             uint64_t *old = buf + HP_BUF / 2;
             for (uint32_t t = lane; t < cur; t += 32) old[t] = res[v * l_max + t];
             __syncwarp();
-            // each old slot's position: its index plus the new slots strictly below it
-            for (uint32_t t = lane; t < cur; t += 32) {
-                const uint64_t x = old[t];
+            // each old slot's position: its index plus the new slots strictly below it (the loop
+            // is warp-uniform: every lane takes part in every shuffle)
+            for (uint32_t base = 0; base < cur; base += 32) {
+                const uint32_t t = base + lane;
+                const uint64_t x = t < cur ? old[t] : ~0ull;
                 uint32_t below = 0;
                 for (uint32_t q = 0; q < nn; q++) below += __shfl_sync(0xffffffffu, nk[0], q) < x ? 1u : 0u;
-                buf[t + below] = x;
+                if (t < cur) buf[t + below] = x;
             }
             // each new slot's position: its rank plus the old slots at or below it (binary search)
             if ((uint32_t)lane < nn) {
