@@ -56,7 +56,7 @@ def test_bounded_wait_gives_up_and_context_survives(limit_ms):
     check_build_equals_oracle(X, H)
 
 
-@pytest.mark.parametrize("cap_mb", [0.001, 1, 4, 16, 48])
+@pytest.mark.parametrize("cap_mb", [0.001, 0.1, 1, 2, 4])
 def test_allocation_failure_returns_nothing_and_next_build_succeeds(cap_mb):
     X, H = small_case()
     Xd = torch.from_numpy(X).cuda()
