@@ -275,10 +275,13 @@ int pipnn_build(const void *points, uint64_t n, uint32_t d, int32_t metric, cons
 void pipnn_free(pipnn_graph *graph);
 
 /* Alg. 4 for `count` independent indexes of one dimension d (independent point sets, each with
- * its own seed: points[i] holds n[i] rows, host or device), built one after another on the
- * library stream.  outs[i] receives index i's graph in device memory; free each with pipnn_free.
- * On an error no graph is returned: the graphs already built are freed, every outs[i] is zeroed
- * and the error of the failing index is reported.  pipnn_get_stats describes the last build. */
+ * its own seed: points[i] holds n[i] rows, host or device), in one pipeline: the indexes are laid
+ * out one after another and partitioned together -- every index with its own seed and with its
+ * point ids taken relative to it wherever the randomness of Alg. 5 sees them, so each index gets
+ * the leaves a separate build would -- and their leaves, HashPrune and prune share the launches of
+ * a single build.  outs[i] receives index i's graph (index-local ids) in device memory; free each
+ * with pipnn_free.  On an error no graph is returned (every outs[i] is zeroed).  pipnn_get_stats
+ * describes the whole batch. */
 int pipnn_build_batched(const void *const *points, const uint64_t *n, uint32_t count, uint32_t d, int32_t metric,
                         const pipnn_params *bp, const uint64_t *seeds, pipnn_graph *outs);
 

@@ -14,6 +14,9 @@ int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float 
                   void *sqnorm);
 int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                      const pipnn_params *bp, uint64_t seed, pipnn_leaves *out, uint16_t *level0_code);
+int partition_points_batch(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
+                           const pipnn_params *bp, const uint64_t *idx_off, const uint64_t *seeds, uint64_t count,
+                           pipnn_leaves *out, uint16_t *level0_code);
 int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
               const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, int prec,
               int direction, pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows);
@@ -196,10 +199,44 @@ void keep_pool_memory() {
     cudaGetLastError();
 }
 
-// graph_on_host: 0 device graph, 1 pinned host graph, 2 caller buffers (user_adj/user_deg)
+// Several independent indexes built by one pipeline (pipnn_build_batched).
+struct BatchDesc {
+    const void *const *points;  // per index, host or device
+    const uint64_t *n;          // per index
+    const uint64_t *seeds;      // per index
+    uint32_t count;
+    pipnn_graph *outs;          // per index, device graphs
+};
+
+// Rows lo .. lo + rows of the batch's graph as index-local ids (padding stays 0xFFFFFFFF).
+__global__ void local_rows(const uint32_t *adj, const uint32_t *deg, uint64_t lo, uint64_t rows, uint32_t R,
+                           uint32_t *out_adj, uint32_t *out_deg) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows * R; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = adj[lo * R + i];
+        out_adj[i] = v == 0xFFFFFFFFu ? v : v - (uint32_t)lo;
+        if (i % R == 0) out_deg[i / R] = deg[lo + i / R];
+    }
+}
+
+// graph_on_host: 0 device graph, 1 pinned host graph, 2 caller buffers (user_adj/user_deg),
+// 3 a batch (batch->outs, device graphs per index)
 int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pipnn_params *bp, uint64_t seed,
-               int graph_on_host, pipnn_graph *out, uint32_t *user_adj = nullptr, uint32_t *user_deg = nullptr) {
+               int graph_on_host, pipnn_graph *out, uint32_t *user_adj = nullptr, uint32_t *user_deg = nullptr,
+               const BatchDesc *batch = nullptr) {
     memset(out, 0, sizeof(*out));
+    // the indexes of the build: one, or a batch laid out one after another
+    std::vector<uint64_t> idx_off{0}, idx_seed;
+    if (batch) {
+        for (uint32_t i = 0; i < batch->count; i++) {
+            idx_off.push_back(idx_off.back() + batch->n[i]);
+            idx_seed.push_back(batch->seeds[i]);
+        }
+        n = idx_off.back();
+        points = batch->count ? batch->points[0] : nullptr;
+    } else {
+        idx_off.push_back(n);
+        idx_seed.push_back(seed);
+    }
     keep_pool_memory();
     PIPNN_TRY(check_params(bp));
     const int dtype = bp->dtype;
@@ -217,9 +254,17 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     const uint64_t launches0 = launch_count();
     tm.mark(0);
 
-    // inputs on the device
+    // inputs on the device (a batch: every index's points copied one after another)
     const void *X = points;
-    if (!is_device_ptr(points)) {
+    if (batch) {
+        char *dx = nullptr;
+        PIPNN_TRY(ws.alloc(&dx, n * d * elem_size(dtype)));
+        for (uint32_t i = 0; i < batch->count; i++)
+            if (batch->n[i])
+                PIPNN_CUDA(cudaMemcpyAsync(dx + idx_off[i] * d * elem_size(dtype), batch->points[i],
+                                           batch->n[i] * d * elem_size(dtype), cudaMemcpyDefault, stream()));
+        X = dx;
+    } else if (!is_device_ptr(points)) {
         void *dx = nullptr;
         PIPNN_TRY(ws.alloc((char **)&dx, n * d * elem_size(dtype)));
         PIPNN_CUDA(cudaMemcpyAsync(dx, points, n * d * elem_size(dtype), cudaMemcpyHostToDevice, stream()));
@@ -258,11 +303,13 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     uint16_t *code = nullptr;
     PIPNN_TRY(ws.zeros(&code, n));
     for (uint32_t r = 0; r < replicas; r++) {
-        const uint64_t seed_r = seed + (uint64_t)r * 0x9E3779B97F4A7C15ull;
+        std::vector<uint64_t> seed_r(idx_seed.size());
+        for (size_t i = 0; i < idx_seed.size(); i++) seed_r[i] = idx_seed[i] + (uint64_t)r * 0x9E3779B97F4A7C15ull;
         rt[r].mark(0);
-        // A1
+        // A1 (every index of a batch with its own seed, in one pass)
         pipnn_leaves leaves;
-        PIPNN_TRY(partition_points(X, n, d, dtype, metric, sqn_bytes, bp, seed_r, &leaves, r == 0 ? code : nullptr));
+        PIPNN_TRY(partition_points_batch(X, n, d, dtype, metric, sqn_bytes, bp, idx_off.data(), seed_r.data(),
+                                         idx_seed.size(), &leaves, r == 0 ? code : nullptr));
         rt[r].mark(1);
         st.levels = leaves.levels > st.levels ? leaves.levels : st.levels;
         st.leaves += leaves.num_leaves;
@@ -364,7 +411,37 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     }
     if (rc == PIPNN_OK) rc = check_device_error("final prune");
     tm.mark(5);
-    if (rc == PIPNN_OK && graph_on_host == 2) {
+    if (rc == PIPNN_OK && graph_on_host == 3) {
+        // per index, its rows with index-local ids
+        uint32_t i = 0;
+        for (; rc == PIPNN_OK && i < batch->count; i++) {
+            const uint64_t lo = idx_off[i], rows = batch->n[i];
+            pipnn_graph &g = batch->outs[i];
+            rc = dev_alloc_raw((void **)&g.ids, rows * bp->R * 4);
+            if (rc == PIPNN_OK) rc = dev_alloc_raw((void **)&g.deg, rows * 4);
+            if (rc == PIPNN_OK && rows) {
+                local_rows<<<grid_for(rows * bp->R, 256), 256, 0, stream()>>>(adj, deg, lo, rows, bp->R, g.ids, g.deg);
+                count_launch();
+                cudaError_t e = cudaGetLastError();
+                if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "graph split: %s", cudaGetErrorString(e));
+            }
+            g.n = rows;
+            g.R = bp->R;
+            g.on_device = 1;
+        }
+        if (rc == PIPNN_OK) rc = check_device_error("graph split");
+        dev_free_raw(adj);
+        dev_free_raw(deg);
+        adj = deg = nullptr;
+        if (rc != PIPNN_OK) {
+            for (uint32_t j = 0; j < batch->count; j++) {
+                dev_free_raw(batch->outs[j].ids);
+                dev_free_raw(batch->outs[j].deg);
+                memset(&batch->outs[j], 0, sizeof(pipnn_graph));
+            }
+            return rc;
+        }
+    } else if (rc == PIPNN_OK && graph_on_host == 2) {
         cudaError_t e = cudaMemcpyAsync(user_adj, adj, n * bp->R * 4, cudaMemcpyDefault, stream());
         if (e == cudaSuccess) e = cudaMemcpyAsync(user_deg, deg, n * 4, cudaMemcpyDefault, stream());
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream());
@@ -553,14 +630,17 @@ int pipnn_build_batched(const void *const *points, const uint64_t *n, uint32_t c
                         const pipnn_params *bp, const uint64_t *seeds, pipnn_graph *outs) {
     if (count && (!points || !n || !seeds || !outs)) return set_error(PIPNN_EINVAL, "points/n/seeds/outs are NULL");
     for (uint32_t i = 0; i < count; i++) memset(&outs[i], 0, sizeof(pipnn_graph));
+    if (count == 0) return PIPNN_OK;
+    uint64_t total = 0;
     for (uint32_t i = 0; i < count; i++) {
-        const int rc = build_impl(points[i], n[i], d, metric, bp, seeds[i], 0, &outs[i]);
-        if (rc != PIPNN_OK) {
-            for (uint32_t j = 0; j <= i; j++) pipnn_free(&outs[j]);
-            return rc;
-        }
+        if (n[i] == 0) return set_error(PIPNN_EINVAL, "index %u has no points", i);
+        if (!points[i]) return set_error(PIPNN_EINVAL, "points[%u] is NULL", i);
+        total += n[i];
     }
-    return PIPNN_OK;
+    if (total >= 0xFFFFFFFFull) return set_error(PIPNN_EINVAL, "the batch holds 2^32 - 1 points or more");
+    BatchDesc b{points, n, seeds, count, outs};
+    pipnn_graph whole;
+    return build_impl(points[0], total, d, metric, bp, 0, 3, &whole, nullptr, nullptr, &b);
 }
 
 int pipnn_trim_pool(void) {

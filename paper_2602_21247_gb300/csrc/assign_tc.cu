@@ -46,6 +46,7 @@ struct AsUnit {
 struct AsArgs {
     const AsUnit *units;
     const uint32_t *inst;       // instance -> point id
+    const uint32_t *pos;        // point id -> its row in the plan's copy (null: the id itself)
     const int32_t *inst_norm;   // instance -> exact squared norm of its point
     const int32_t *lead_norm;   // exact squared norm of every leader row
     uint32_t fanout;            // F <= KMAX; stride of assign
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     uint32_t r = q.un.row0 + 4 * lane + e;
                     r = r < q.un.nrows ? r : q.un.nrows - 1;
                     v[e] = a.inst[q.un.inst0 + r];
+                    if (a.pos) v[e] = a.pos[v[e]];
                 } else if (q.kind == 1) {
                     const uint32_t c = q.t * C::NMAX + 4 * lane + e;
                     v[e] = c < q.un.ncols ? (uint32_t)a.lead_norm[q.un.lead0 + c] : 0u;
@@ -582,6 +584,14 @@ int assign_tc_plan(const void *X, uint64_t n, uint32_t d, int dtype, Workspace &
     return PIPNN_OK;
 }
 
+int assign_tc_plan_reorder(const void *X, uint64_t n, uint32_t d, int dtype, const uint32_t *order, Workspace &ws,
+                           AssignTcPlan *plan) {
+    if (!plan->rows) return set_error(PIPNN_EINVAL, "no assignment plan to reorder");
+    if (!plan->pos) PIPNN_TRY(ws.alloc(&plan->pos, n ? n : 1));
+    PIPNN_TRY(inverse_order(order, n, plan->pos));
+    return stage_rows_bf16(X, d, plan->kp, dtype, order, n, plan->rows);
+}
+
 int assign_tc(const AssignTcPlan &plan, const void *X, uint32_t d, int dtype, const int32_t *sqnorm,
               const uint32_t *tile_grp, const uint32_t *tile_row0, uint64_t ntiles, const uint64_t *seg_start,
               const uint32_t *seg_size, const uint32_t *inst, const uint64_t *lead_off, const uint32_t *lead_cnt,
@@ -614,6 +624,7 @@ int assign_tc(const AssignTcPlan &plan, const void *X, uint32_t d, int dtype, co
     AsArgs a{};
     a.units = units;
     a.inst = inst;
+    a.pos = plan.pos;
     a.inst_norm = inorm;
     a.lead_norm = lnorm;
     a.fanout = F;

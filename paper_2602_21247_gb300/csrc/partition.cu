@@ -86,15 +86,17 @@ __global__ void seg_setup(uint64_t S, const uint32_t *seg_size, float p_samp, ui
     }
 }
 
+// The sample's randomness is that of the subproblem's own index: its seed and its points' ids
+// relative to the index (seg_base), so a batch of indexes draws what separate builds would.
 __global__ void collect_candidates(uint64_t N, const uint32_t *inst, const uint32_t *inst_seg,
                                    const uint64_t *seg_id, const unsigned long long *thr, const uint8_t *active,
                                    const uint64_t *cand_off, const uint64_t *cand_cap, uint32_t *ccnt,
-                                   uint64_t *cbuf, uint64_t seed) {
+                                   uint64_t *cbuf, const uint64_t *seg_seed, const uint32_t *seg_base) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t s = inst_seg[i];
         if (!active[s]) continue;
         uint32_t pt = inst[i];
-        uint32_t prio = leader_priority(seed, seg_id[s], pt);
+        uint32_t prio = leader_priority(seg_seed[s], seg_id[s], pt - seg_base[s]);
         if ((unsigned long long)prio < thr[s]) {
             uint32_t pos = atomicAdd(&ccnt[s], 1u);
             if (pos < cand_cap[s]) cbuf[cand_off[s] + pos] = ((uint64_t)prio << 32) | pt;
@@ -161,9 +163,10 @@ __global__ void __launch_bounds__(1024) sort_leaders(const uint64_t *cbuf, const
 // pass 0 counts output buckets; pass 1 writes them at ob_base[s].
 __global__ void merge_plan(uint64_t S, int pass, const uint32_t *seg_size, const uint64_t *seg_id,
                            const uint64_t *lead_off, const uint32_t *lead_cnt, const uint32_t *lead,
-                           const uint32_t *bucket_cnt, uint32_t c_min, uint32_t c_max, uint32_t depth, uint64_t seed,
-                           uint64_t *ob_count, const uint64_t *ob_base, uint32_t *rank_ob, uint32_t *ob_raw,
-                           uint8_t *ob_kind, uint64_t *ob_child) {
+                           const uint32_t *bucket_cnt, uint32_t c_min, uint32_t c_max, uint32_t depth,
+                           const uint64_t *seg_seed, const uint32_t *seg_base, uint64_t *ob_count,
+                           const uint64_t *ob_base, uint32_t *rank_ob, uint32_t *ob_raw, uint8_t *ob_kind,
+                           uint64_t *ob_child, uint32_t *ob_parent) {
     for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < S; s += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t lo = lead_off[s];
         const uint32_t l = lead_cnt[s], n_s = seg_size[s];
@@ -185,7 +188,10 @@ __global__ void merge_plan(uint64_t S, int pass, const uint32_t *seg_size, const
                     rank_ob[lo + r] = (uint32_t)ob;
                     ob_raw[ob] = c;
                     ob_kind[ob] = kind;
-                    ob_child[ob] = kind == OB_RECURSE ? child_identity(seed, seg_id[s], lead[lo + r]) : 0ull;
+                    ob_child[ob] = kind == OB_RECURSE
+                                       ? child_identity(seg_seed[s], seg_id[s], lead[lo + r] - seg_base[s])
+                                       : 0ull;
+                    ob_parent[ob] = (uint32_t)s;
                 }
                 continue;
             }
@@ -331,7 +337,9 @@ __global__ void emit_descriptors(uint64_t OB, const uint8_t *ob_kind, const uint
                                  const uint64_t *leaf_pos, const uint64_t *next_pos, const uint64_t *leaf_idx,
                                  const uint64_t *rec_idx, const uint64_t *guard_idx, uint64_t *leaf_start,
                                  uint32_t *leaf_size, uint64_t *nseg_start, uint32_t *nseg_size, uint64_t *nseg_id,
-                                 uint64_t *guard_pos, uint64_t *guard_size) {
+                                 uint64_t *guard_pos, uint64_t *guard_size, const uint32_t *ob_parent,
+                                 const uint64_t *seg_seed, const uint32_t *seg_base, uint64_t *nseg_seed,
+                                 uint32_t *nseg_base) {
     for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < OB; b += (uint64_t)gridDim.x * blockDim.x) {
         const uint8_t k = ob_kind[b];
         if (k == OB_LEAF || k == OB_MERGED) {
@@ -341,6 +349,8 @@ __global__ void emit_descriptors(uint64_t OB, const uint8_t *ob_kind, const uint
             nseg_start[rec_idx[b]] = next_pos[b];
             nseg_size[rec_idx[b]] = ob_fill[b];
             nseg_id[rec_idx[b]] = ob_child[b];
+            nseg_seed[rec_idx[b]] = seg_seed[ob_parent[b]];
+            nseg_base[rec_idx[b]] = seg_base[ob_parent[b]];
         } else {
             guard_pos[guard_idx[b]] = leaf_pos[b];
             guard_size[guard_idx[b]] = ob_fill[b];
@@ -398,6 +408,8 @@ struct Level {
     uint64_t *seg_start = nullptr;
     uint32_t *seg_size = nullptr;
     uint64_t *seg_id = nullptr;
+    uint64_t *seg_seed = nullptr;  // the seed of the subproblem's index
+    uint32_t *seg_base = nullptr;  // the first point id of the subproblem's index
     uint32_t *inst = nullptr;
     uint32_t *inst_seg = nullptr;
     std::unique_ptr<Workspace> ws{new Workspace()};
@@ -415,13 +427,43 @@ __global__ void level0_code(const uint32_t *inst, const uint16_t *assign, uint64
         code[inst[i]] = assign[i * F];
 }
 
+// Points of the `count` indexes of a batch: index i holds point ids idx_off[i] .. idx_off[i+1).
+__global__ void batch_level0(uint64_t count, const uint64_t *big_off, const uint64_t *big_start,
+                             const uint64_t *big_seed, uint32_t *seg_size, uint64_t *seg_start, uint64_t *seg_seed,
+                             uint32_t *seg_base) {
+    for (uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; s < count; s += (uint64_t)gridDim.x * blockDim.x) {
+        seg_size[s] = (uint32_t)(big_off[2 * s + 1] - big_off[2 * s]);
+        seg_start[s] = big_start[s];
+        seg_seed[s] = big_seed[s];
+        seg_base[s] = (uint32_t)big_off[2 * s];
+    }
+}
+
+// instance j of the level-0 segments: the points of the large indexes in order, and their segment
+__global__ void batch_instances(uint64_t count, const uint64_t *big_off, const uint64_t *big_start, uint32_t *inst,
+                                uint32_t *inst_seg) {
+    for (uint64_t s = blockIdx.x; s < count; s += gridDim.x) {
+        const uint64_t lo = big_off[2 * s], hi = big_off[2 * s + 1], at = big_start[s];
+        for (uint64_t q = threadIdx.x; q < hi - lo; q += blockDim.x) {
+            inst[at + q] = (uint32_t)(lo + q);
+            inst_seg[at + q] = (uint32_t)s;
+        }
+    }
+}
+
 // level0_code (optional, n entries): receives every point's nearest level-0 leader (its rank).
-int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out, uint16_t *level0_code_out) {
+// Alg. 5 over a batch of `count` independent indexes at once: index i holds the points
+// idx_off[i] .. idx_off[i+1) (host array) and is partitioned with seeds[i] (host array), with its
+// point ids taken relative to idx_off[i] wherever the randomness sees them, so every index gets the
+// leaves a separate partition of it would get (its members as global ids).
+int partition_points_batch(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
+                           const pipnn_params *bp, const uint64_t *idx_off, const uint64_t *seeds, uint64_t count,
+                           pipnn_leaves *out, uint16_t *level0_code_out) {
     memset(out, 0, sizeof(*out));
     Workspace leaf_ws;
     std::vector<LevelLeaves> levels;
     unsigned *err = device_error_word();
+    if (count == 0 || idx_off[count] != n) return set_error(PIPNN_EINVAL, "index offsets do not cover the points");
 
     // byte data needs exact squared norms for the dot-product form
     const int32_t *sqn = sqnorm_bytes;
@@ -436,35 +478,66 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
     Workspace tc_ws;
     AssignTcPlan tc_plan;
 
-    std::unique_ptr<Level> cur(new Level());
-    uint32_t nlevels = 0;
-    if (n <= bp->c_max) {
+    // level 0: an index of at most C_max points is one leaf; the others are the first subproblems
+    std::vector<uint64_t> small_start, big_off, big_start, big_seed;
+    std::vector<uint32_t> small_size;
+    uint64_t big_total = 0;
+    for (uint64_t i = 0; i < count; i++) {
+        const uint64_t lo = idx_off[i], hi = idx_off[i + 1];
+        if (hi < lo) return set_error(PIPNN_EINVAL, "index offsets decrease");
+        if (hi == lo) continue;
+        if (hi - lo <= bp->c_max) {
+            small_start.push_back(lo);
+            small_size.push_back((uint32_t)(hi - lo));
+        } else {
+            big_off.push_back(lo);
+            big_off.push_back(hi);
+            big_start.push_back(big_total);
+            big_seed.push_back(seeds[i]);
+            big_total += hi - lo;
+        }
+    }
+    if (!small_start.empty()) {
+        // the leaf storage of these leaves is the point ids themselves: mem = 0 .. n-1
         LevelLeaves lv{};
+        const uint64_t ns = small_start.size();
         PIPNN_TRY(leaf_ws.alloc(&lv.mem, n));
-        PIPNN_TRY(leaf_ws.alloc(&lv.start, 1));
-        PIPNN_TRY(leaf_ws.alloc(&lv.size, 1));
+        PIPNN_TRY(leaf_ws.alloc(&lv.start, ns));
+        PIPNN_TRY(leaf_ws.alloc(&lv.size, ns));
         iota_u32<<<grid_for(n, 256), 256, 0, stream()>>>(lv.mem, n);
         PIPNN_LAUNCH_CHECK();
-        uint64_t z = 0;
-        uint32_t nn = (uint32_t)n;
-        PIPNN_CUDA(cudaMemcpyAsync(lv.start, &z, 8, cudaMemcpyHostToDevice, stream()));
-        PIPNN_CUDA(cudaMemcpyAsync(lv.size, &nn, 4, cudaMemcpyHostToDevice, stream()));
+        PIPNN_CUDA(cudaMemcpyAsync(lv.start, small_start.data(), ns * 8, cudaMemcpyHostToDevice, stream()));
+        PIPNN_CUDA(cudaMemcpyAsync(lv.size, small_size.data(), ns * 4, cudaMemcpyHostToDevice, stream()));
         PIPNN_CUDA(cudaStreamSynchronize(stream()));
-        lv.count = 1;
+        lv.count = ns;
         levels.push_back(lv);
-        cur->S = 0;
-    } else {
+    }
+    std::unique_ptr<Level> cur(new Level());
+    uint32_t nlevels = 0;
+    const uint64_t nbig = big_start.size();
+    cur->S = nbig;
+    cur->N = big_total;
+    if (nbig) {
         Workspace &w = *cur->ws;
-        cur->S = 1;
-        cur->N = n;
-        PIPNN_TRY(w.zeros(&cur->seg_start, 1));
-        PIPNN_TRY(w.alloc(&cur->seg_size, 1));
-        PIPNN_TRY(w.zeros(&cur->seg_id, 1));
-        PIPNN_TRY(w.alloc(&cur->inst, n));
-        PIPNN_TRY(w.zeros(&cur->inst_seg, n));
-        uint32_t nn = (uint32_t)n;
-        PIPNN_CUDA(cudaMemcpyAsync(cur->seg_size, &nn, 4, cudaMemcpyHostToDevice, stream()));
-        iota_u32<<<grid_for(n, 256), 256, 0, stream()>>>(cur->inst, n);
+        uint64_t *dbig_off, *dbig_start, *dbig_seed;
+        PIPNN_TRY(w.alloc(&cur->seg_start, nbig));
+        PIPNN_TRY(w.alloc(&cur->seg_size, nbig));
+        PIPNN_TRY(w.zeros(&cur->seg_id, nbig));
+        PIPNN_TRY(w.alloc(&cur->seg_seed, nbig));
+        PIPNN_TRY(w.alloc(&cur->seg_base, nbig));
+        PIPNN_TRY(w.alloc(&cur->inst, big_total));
+        PIPNN_TRY(w.alloc(&cur->inst_seg, big_total));
+        PIPNN_TRY(w.alloc(&dbig_off, 2 * nbig));
+        PIPNN_TRY(w.alloc(&dbig_start, nbig));
+        PIPNN_TRY(w.alloc(&dbig_seed, nbig));
+        PIPNN_CUDA(cudaMemcpyAsync(dbig_off, big_off.data(), 2 * nbig * 8, cudaMemcpyHostToDevice, stream()));
+        PIPNN_CUDA(cudaMemcpyAsync(dbig_start, big_start.data(), nbig * 8, cudaMemcpyHostToDevice, stream()));
+        PIPNN_CUDA(cudaMemcpyAsync(dbig_seed, big_seed.data(), nbig * 8, cudaMemcpyHostToDevice, stream()));
+        batch_level0<<<grid_for(nbig, 256), 256, 0, stream()>>>(nbig, dbig_off, dbig_start, dbig_seed, cur->seg_size,
+                                                                 cur->seg_start, cur->seg_seed, cur->seg_base);
+        PIPNN_LAUNCH_CHECK();
+        batch_instances<<<grid_for(nbig, 1, 152u * 16u), 256, 0, stream()>>>(nbig, dbig_off, dbig_start, cur->inst,
+                                                                              cur->inst_seg);
         PIPNN_LAUNCH_CHECK();
         PIPNN_CUDA(cudaStreamSynchronize(stream()));
     }
@@ -509,7 +582,8 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         int tries = 0;
         for (;; tries++) {
             collect_candidates<<<grid_for(N, 256), 256, 0, stream()>>>(N, cur->inst, cur->inst_seg, cur->seg_id, thr,
-                                                                       active, cand_off, cand_cap, ccnt, cbuf, seed);
+                                                                       active, cand_off, cand_cap, ccnt, cbuf,
+                                                                       cur->seg_seed, cur->seg_base);
             PIPNN_LAUNCH_CHECK();
             PIPNN_CUDA(cudaMemsetAsync(nbad, 0, sizeof(unsigned), stream()));
             check_candidates<<<gs, 256, 0, stream()>>>(S, cur->seg_size, lead_cnt, cand_cap, ccnt, expect, thr, active,
@@ -554,9 +628,19 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
             PIPNN_TRY(launch_allpairs<MODE_ASSIGN>(dtype, metric, F, a, ntiles));
         }
 
-        if (depth == 0 && level0_code_out) {
-            level0_code<<<grid_for(N, 256), 256, 0, stream()>>>(cur->inst, assign, N, F, level0_code_out);
+        if (depth == 0 && (level0_code_out || tc_plan.rows)) {
+            // every point's nearest level-0 leader; the deeper levels' subproblems hold points near
+            // one another, so the TC plan's rows are restaged grouped by it (locality of the gathers)
+            uint16_t *code = level0_code_out;
+            if (!code) PIPNN_TRY(tc_ws.zeros(&code, n));
+            level0_code<<<grid_for(N, 256), 256, 0, stream()>>>(cur->inst, assign, N, F, code);
             PIPNN_LAUNCH_CHECK();
+            if (tc_plan.rows) {
+                uint32_t *order = nullptr;
+                PIPNN_TRY(tw.alloc(&order, n));
+                PIPNN_TRY(order_by_code(code, n, order, tw));
+                PIPNN_TRY(assign_tc_plan_reorder(X, n, d, dtype, order, tc_ws, &tc_plan));
+            }
         }
 
         // 3. Merge plan
@@ -564,8 +648,8 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         PIPNN_TRY(tw.alloc(&ob_count, S));
         PIPNN_TRY(tw.alloc(&ob_base, S));
         merge_plan<<<gs, 256, 0, stream()>>>(S, 0, cur->seg_size, cur->seg_id, lead_off, lead_cnt, lead, bucket_cnt,
-                                             bp->c_min, bp->c_max, depth, seed, ob_count, nullptr, nullptr, nullptr,
-                                             nullptr, nullptr);
+                                             bp->c_min, bp->c_max, depth, cur->seg_seed, cur->seg_base, ob_count,
+                                             nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
         PIPNN_LAUNCH_CHECK();
         PIPNN_TRY(exclusive_scan_u64(ob_count, ob_base, S, tot, tw));
         PIPNN_TRY(read_u64(tot, &OB));
@@ -577,9 +661,11 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         PIPNN_TRY(tw.zeros(&ob_fill, OB));
         PIPNN_TRY(tw.alloc(&ob_kind, OB));
         PIPNN_TRY(tw.alloc(&ob_child, OB));
+        uint32_t *ob_parent;
+        PIPNN_TRY(tw.alloc(&ob_parent, OB));
         merge_plan<<<gs, 256, 0, stream()>>>(S, 1, cur->seg_size, cur->seg_id, lead_off, lead_cnt, lead, bucket_cnt,
-                                             bp->c_min, bp->c_max, depth, seed, nullptr, ob_base, rank_ob, ob_raw,
-                                             ob_kind, ob_child);
+                                             bp->c_min, bp->c_max, depth, cur->seg_seed, cur->seg_base, nullptr,
+                                             ob_base, rank_ob, ob_raw, ob_kind, ob_child, ob_parent);
         PIPNN_LAUNCH_CHECK();
 
         uint64_t *leafsz, *nextsz, *is_leaf, *is_rec, *is_guard;
@@ -609,6 +695,8 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         PIPNN_TRY(nw.alloc(&next->seg_start, n_rec));
         PIPNN_TRY(nw.alloc(&next->seg_size, n_rec));
         PIPNN_TRY(nw.alloc(&next->seg_id, n_rec));
+        PIPNN_TRY(nw.alloc(&next->seg_seed, n_rec));
+        PIPNN_TRY(nw.alloc(&next->seg_base, n_rec));
         PIPNN_TRY(nw.alloc(&next->inst, N_next));
         PIPNN_TRY(nw.alloc(&next->inst_seg, N_next));
         LevelLeaves lv{};
@@ -635,7 +723,8 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         emit_descriptors<<<grid_for(OB, 256), 256, 0, stream()>>>(OB, ob_kind, ob_fill, ob_child, leafsz, nextsz,
                                                                   is_leaf, is_rec, is_guard, lstart_tmp, lsize_tmp,
                                                                   next->seg_start, next->seg_size, next->seg_id,
-                                                                  guard_pos, guard_size);
+                                                                  guard_pos, guard_size, ob_parent, cur->seg_seed,
+                                                                  cur->seg_base, next->seg_seed, next->seg_base);
         PIPNN_LAUNCH_CHECK();
 
         // 5. guard buckets: runs of members in id order
@@ -733,6 +822,12 @@ int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metri
         out->levels = nlevels;
     }
     return PIPNN_OK;
+}
+
+int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
+                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out, uint16_t *level0_code) {
+    const uint64_t off[2] = {0, n};
+    return partition_points_batch(X, n, d, dtype, metric, sqnorm_bytes, bp, off, &seed, 1, out, level0_code);
 }
 
 }  // namespace pipnn

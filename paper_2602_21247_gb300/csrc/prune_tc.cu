@@ -68,6 +68,7 @@ struct PtArgs {
     uint32_t *adj, *deg;
     unsigned *err;
     const uint32_t *order;  // processing order of the nodes (a permutation of 0..n-1), or null
+    const uint32_t *pos;    // with an order: the BF16 row of point v is row pos[v] (rows staged in order)
 };
 
 // Tile info, info warp -> gathers, MMA, epilogue: row ids (a packed node's rows start at 32q; the
@@ -589,6 +590,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                     const uint32_t row = 4 * lane + e;
                     y[e] = use ? ids[(row & 31) <= c ? row : node_row] : 0u;
                 }
+                if (a.pos && use) {
+#pragma unroll
+                    for (int e = 0; e < 4; e++) y[e] = a.pos[y[e]];
+                }
             } else {
                 const uint32_t rows = misc[M_NODE] + 1;
                 use = 4u * lane < rows;
@@ -596,6 +601,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 for (int e = 0; e < 4; e++) {
                     const uint32_t row = 4 * lane + e;
                     y[e] = use ? ids[row < rows ? row : rows - 1] : 0u;
+                }
+                if (a.pos && use) {
+#pragma unroll
+                    for (int e = 0; e < 4; e++) y[e] = a.pos[y[e]];
                 }
             }
             const unsigned um = __ballot_sync(0xffffffffu, use);
@@ -651,7 +660,14 @@ int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32
     const uint32_t kp = d <= 64 ? 64 : 128;
     __nv_bfloat16 *rows = nullptr;
     PIPNN_TRY(ws.alloc(&rows, n * kp));
-    PIPNN_TRY(stage_rows_bf16(X, d, kp, dtype, nullptr, n, rows));
+    // with a processing order the rows are staged in that order, so the rows one stretch of the
+    // order gathers lie together in memory (a few pages, not the whole array): row i is point order[i]
+    uint32_t *pos = nullptr;
+    if (order) {
+        PIPNN_TRY(ws.alloc(&pos, n));
+        PIPNN_TRY(inverse_order(order, n, pos));
+    }
+    PIPNN_TRY(stage_rows_bf16(X, d, kp, dtype, order, n, rows));
     CUtensorMap map;
     PIPNN_TRY(encode_rows_map(&map, rows, n, kp, true));
     PtArgs a{};
@@ -667,6 +683,7 @@ int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32
     a.deg = deg;
     a.err = device_error_word();
     a.order = order;
+    a.pos = pos;
     if (kp == 64) return launch_pt<1>(map, a);
     return launch_pt<2>(map, a);
 }

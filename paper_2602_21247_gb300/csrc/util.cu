@@ -256,6 +256,20 @@ __global__ void code_place(const uint16_t *code, uint64_t n, uint64_t chunk, uns
 }
 }  // namespace
 
+namespace {
+__global__ void inverse_order_kernel(const uint32_t *order, uint64_t n, uint32_t *pos) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        pos[order[i]] = (uint32_t)i;
+}
+}  // namespace
+
+int inverse_order(const uint32_t *order, uint64_t n, uint32_t *pos) {
+    if (n == 0) return PIPNN_OK;
+    inverse_order_kernel<<<grid_for(n, 256), 256, 0, stream()>>>(order, n, pos);
+    PIPNN_LAUNCH_CHECK();
+    return PIPNN_OK;
+}
+
 int order_by_code(const uint16_t *code, uint64_t n, uint32_t *order, Workspace &ws) {
     if (n == 0) return PIPNN_OK;
     unsigned long long *hist, *tot;
