@@ -109,6 +109,8 @@ def lib():
         L.orc_medoid.restype = u32
         L.orc_beam_search.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, vp, u64, u32, u32, u32,
                                       vp, vp]
+        L.orc_beam_search_as.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, vp, u64, u32, u32, u32,
+                                         i32, vp, vp]
         _lib = L
     return _lib
 
@@ -372,8 +374,25 @@ def medoid(X, metric=L2):
     return int(lib().orc_medoid(_p(X), X.shape[0], X.shape[1], _dtype_code(X), metric))
 
 
-def beam_search(X, adj, deg, Q, L, k=10, start=None, metric=L2):
-    """Alg. 1 for every query; returns (ids nq x k, number of distance evaluations)."""
+def knn_graph(X, adj, deg, L, k=10, start=None, metric=L2, defined=True):
+    """k-NN graph construction with the built index (Sec. 5): every point p queries the graph with
+    itself (Alg. 1, beam L, the k + 1 closest kept) and p's k nearest are the first k of those
+    other than p.  Returns (knn n x k, number of distance evaluations)."""
+    X = np.ascontiguousarray(X)
+    if k + 1 > L:
+        raise ValueError("need k + 1 <= L")
+    ids, nd = beam_search(X, adj, deg, X, L, k=k + 1, start=start, metric=metric, defined=defined)
+    out = np.full((X.shape[0], k), 0xFFFFFFFF, dtype=np.uint32)
+    for p in range(X.shape[0]):
+        row = [int(v) for v in ids[p] if int(v) != p][:k]
+        out[p, :len(row)] = row
+    return out, nd
+
+
+def beam_search(X, adj, deg, Q, L, k=10, start=None, metric=L2, defined=False):
+    """Alg. 1 for every query; returns (ids nq x k, number of distance evaluations).  Query
+    dissimilarities in double precision, or with defined=True as the build's defining binary32 /
+    exact-integer value."""
     X = np.ascontiguousarray(X)
     Q = np.ascontiguousarray(Q, dtype=X.dtype)
     adj = np.ascontiguousarray(adj, dtype=np.uint32)
@@ -381,9 +400,9 @@ def beam_search(X, adj, deg, Q, L, k=10, start=None, metric=L2):
     start = medoid(X, metric) if start is None else start
     ids = np.zeros((Q.shape[0], k), dtype=np.uint32)
     nd = np.zeros(1, dtype=np.uint64)
-    _check(lib().orc_beam_search(_p(X), X.shape[0], X.shape[1], _dtype_code(X), metric, _p(adj),
-                                 _p(deg), adj.shape[1], _p(Q), Q.shape[0], start, L, k, _p(ids),
-                                 _p(nd)), "beam_search")
+    _check(lib().orc_beam_search_as(_p(X), X.shape[0], X.shape[1], _dtype_code(X), metric, _p(adj),
+                                    _p(deg), adj.shape[1], _p(Q), Q.shape[0], start, L, k,
+                                    1 if defined else 0, _p(ids), _p(nd)), "beam_search")
     return ids, int(nd[0])
 
 

@@ -984,11 +984,18 @@ int orc_build(const void *X, uint64_t n, uint32_t d, int dtype, int metric, cons
 
 /* ------------------------------------------------------------------------------------------ */
 /* Evaluation: exact k-NN (Def. 1, ties to the smaller id), Alg. 1 BeamSearch, medoid start.  */
-/* Query-side dissimilarities are taken in double precision.                                   */
+/* Query-side dissimilarities are taken in double precision, or (defined = 1) as the defining    */
+/* binary32 / exact-integer value the build uses.                                              */
 /* ------------------------------------------------------------------------------------------ */
+static double qdis_as(const void *X, uint64_t i, const void *q, uint32_t d, int dtype, int metric, int defined)
+{
+    return defined ? dis_vec(row(X, i, d, dtype), q, d, dtype, metric)
+                   : dis_vec_f64(row(X, i, d, dtype), q, d, dtype, metric);
+}
+
 static double qdis(const void *X, uint64_t i, const void *q, uint32_t d, int dtype, int metric)
 {
-    return dis_vec_f64(row(X, i, d, dtype), q, d, dtype, metric);
+    return qdis_as(X, i, q, d, dtype, metric, 0);
 }
 
 int orc_knn(const void *X, uint64_t n, const void *Q, uint64_t nq, uint32_t d, int dtype, int metric,
@@ -1026,12 +1033,51 @@ int orc_knn(const void *X, uint64_t n, const void *Q, uint64_t nq, uint32_t d, i
     return err ? ORC_ENOMEM : ORC_OK;
 }
 
-/* The point nearest (double precision) to the mean of all points.  The mean is summed in fixed
+/* Byte data: the point nearest to the exact mean, found without rounding.  With S the exact
+ * coordinate sums, |x - S/n|^2 = |n x - S|^2 / n^2, so the argmin of the integer
+ * sum_t (n x_t - S_t)^2 (below 2^92 for any admissible n and d) is the point nearest to the mean;
+ * ties go to the smaller index. */
+static uint32_t medoid_bytes_exact(const void *X, uint64_t n, uint32_t d, int dtype)
+{
+    int64_t *S = (int64_t *)calloc(d, sizeof(int64_t));
+    if (!S) return 0;
+    for (uint64_t i = 0; i < n; i++)
+        for (uint32_t t = 0; t < d; t++) S[t] += (int64_t)coord(row(X, i, d, dtype), t, dtype);
+    uint32_t best = 0;
+    unsigned __int128 bv = 0;
+    int have = 0;
+#pragma omp parallel
+    {
+        uint32_t lb = 0;
+        unsigned __int128 lv = 0;
+        int lh = 0;
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < (int64_t)n; i++) {
+            unsigned __int128 v = 0;
+            for (uint32_t t = 0; t < d; t++) {
+                int64_t e = (int64_t)n * (int64_t)coord(row(X, (uint64_t)i, d, dtype), t, dtype) - S[t];
+                uint64_t a = e < 0 ? (uint64_t)(-e) : (uint64_t)e;
+                v += (unsigned __int128)a * a;
+            }
+            if (!lh || v < lv) { lv = v; lb = (uint32_t)i; lh = 1; }
+        }
+#pragma omp critical
+        {
+            if (lh && (!have || lv < bv || (lv == bv && lb < best))) { bv = lv; best = lb; have = 1; }
+        }
+    }
+    free(S);
+    return best;
+}
+
+/* The beam-search start: the point nearest to the mean of all points (ties to the smaller
+ * index).  Byte data: exact (above).  Float data: in double precision, the mean summed in fixed
  * chunks of 65,536 points whose partial sums are added in chunk order, so the result does not
- * depend on the thread count; ties go to the smaller index. */
+ * depend on the thread count. */
 uint32_t orc_medoid(const void *X, uint64_t n, uint32_t d, int dtype, int metric)
 {
     (void)metric;
+    if (dtype != ORC_F32) return medoid_bytes_exact(X, n, d, dtype);
     const uint64_t CH = 65536;
     const uint64_t nch = (n + CH - 1) / CH;
     double *part = (double *)calloc(nch * d, sizeof(double));
@@ -1078,9 +1124,20 @@ uint32_t orc_medoid(const void *X, uint64_t n, uint32_t d, int dtype, int metric
 /* Alg. 1: beam B (kept sorted by (distance, id)) and visited set V; visit the nearest unvisited
  * beam member, add its neighbours, trim the beam to the L closest.  Returns the k closest of the
  * final beam and the number of distance evaluations. */
+int orc_beam_search_as(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const uint32_t *adj,
+                       const uint32_t *deg, uint32_t R, const void *Q, uint64_t nq, uint32_t start,
+                       uint32_t L, uint32_t k, int defined, uint32_t *ids, uint64_t *ndist);
+
 int orc_beam_search(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const uint32_t *adj,
                     const uint32_t *deg, uint32_t R, const void *Q, uint64_t nq, uint32_t start,
                     uint32_t L, uint32_t k, uint32_t *ids, uint64_t *ndist)
+{
+    return orc_beam_search_as(X, n, d, dtype, metric, adj, deg, R, Q, nq, start, L, k, 0, ids, ndist);
+}
+
+int orc_beam_search_as(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const uint32_t *adj,
+                       const uint32_t *deg, uint32_t R, const void *Q, uint64_t nq, uint32_t start,
+                       uint32_t L, uint32_t k, int defined, uint32_t *ids, uint64_t *ndist)
 {
     if (!X || !adj || !deg || !Q || !ids || L < 1 || k < 1 || k > L || start >= n) return ORC_EINVAL;
     uint64_t total = 0;
@@ -1101,7 +1158,7 @@ int orc_beam_search(const void *X, uint64_t n, uint32_t d, int dtype, int metric
                 uint64_t nt = 0;
                 uint32_t nb = 1;
                 B[0].id = start;
-                B[0].d = qdis(X, start, q, d, dtype, metric);
+                B[0].d = qdis_as(X, start, q, d, dtype, metric, defined);
                 total++;
                 vis[start] = 1;
                 touched[nt++] = start;
@@ -1117,7 +1174,7 @@ int orc_beam_search(const void *X, uint64_t n, uint32_t d, int dtype, int metric
                         if (u >= n || vis[u]) continue;
                         vis[u] = 1;
                         if (nt < cap_t) touched[nt++] = u;
-                        double dv = qdis(X, u, q, d, dtype, metric);
+                        double dv = qdis_as(X, u, q, d, dtype, metric, defined);
                         total++;
                         if (nb == L && (dv > B[L - 1].d || (dv == B[L - 1].d && u > B[L - 1].id))) continue;
                         uint32_t pos = nb < L ? nb++ : L - 1;

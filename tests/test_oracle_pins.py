@@ -471,6 +471,53 @@ def test_knn_and_beam_search_exact_on_complete_graph():
     assert oracle.recall(ids, gt) == 1.0
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.uint8, np.int8])
+def test_beam_search_walks_a_path_graph(dtype):
+    """Alg. 1 worked by hand on ten points on a line (x_i = i, edges i <-> i +- 1), query at 7,
+    start 0.  L = 1 walks greedily 0 -> 7 and evaluates points 0 .. 8 (9 evaluations); L = 3 also
+    expands 8 and evaluates 9 (10 evaluations) and returns 7, then the tie 6 / 8 by id."""
+    X = np.zeros((10, 4), dtype=dtype)
+    X[:, 0] = np.arange(10)
+    adj = np.full((10, 2), 0xFFFFFFFF, np.uint32)
+    deg = np.zeros(10, np.uint32)
+    for i in range(10):
+        nb = [j for j in (i - 1, i + 1) if 0 <= j < 10]
+        adj[i, :len(nb)] = nb
+        deg[i] = len(nb)
+    Q = X[7:8].copy()
+    for defined in (False, True):
+        ids, nd = oracle.beam_search(X, adj, deg, Q, 1, k=1, start=0, defined=defined)
+        assert ids.tolist() == [[7]] and nd == 9
+        ids, nd = oracle.beam_search(X, adj, deg, Q, 3, k=3, start=0, defined=defined)
+        assert ids.tolist() == [[7, 6, 8]] and nd == 10
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.uint8, np.int8])
+def test_defined_beam_search_and_knn_graph_on_complete_graph(dtype):
+    """On the complete graph one expansion evaluates every point, so Alg. 1 returns the exact k
+    nearest by (dissimilarity, id), and the k-NN graph is the brute-force one without self.
+    Integer-valued data keeps the binary32 evaluation exact, so the brute force is in integers;
+    duplicated points plant exact ties."""
+    rng = np.random.default_rng(33)
+    n, d = 240, 6
+    lo, hi = (0, 12) if dtype == np.uint8 else (-6, 7)
+    X = rng.integers(lo, hi, size=(n, d)).astype(dtype)
+    X[100:110] = X[99]
+    adj = np.array([[j for j in range(n) if j != i] for i in range(n)], np.uint32)
+    deg = np.full(n, n - 1, np.uint32)
+    Xi = X.astype(np.int64)
+    D = ((Xi[:, None, :] - Xi[None, :, :]) ** 2).sum(2)
+    order = np.lexsort((np.broadcast_to(np.arange(n), (n, n)), D), axis=1)
+    Q = X[[5, 99, 104, 200]]
+    ids, _ = oracle.beam_search(X, adj, deg, Q, 20, k=12, start=17, defined=True)
+    for r, qi in enumerate([5, 99, 104, 200]):
+        assert ids[r].tolist() == order[qi, :12].tolist()
+    knn, _ = oracle.knn_graph(X, adj, deg, 20, k=10, start=17)
+    for p in range(n):
+        want = [int(j) for j in order[p] if j != p][:10]
+        assert knn[p].tolist() == want
+
+
 def test_invalid_parameters_rejected():
     X = synth.uniform_points(100, 8, synth.U8, seed=25)
     for kw in (dict(c_max=1), dict(hash_bits=17), dict(R=65, l_max=64), dict(leaf_k=0)):
@@ -520,6 +567,37 @@ def test_medoid_is_point_nearest_to_mean(dtype):
     # a planted exact centre: the mean of a symmetric set is one of its points
     Y = np.array([[0, 0], [2, 0], [-2, 0], [0, 2], [0, -2], [1, 1], [-1, -1]], np.float32)
     assert oracle.medoid(Y) == 0
+
+
+@pytest.mark.parametrize("dtype", [synth.U8, synth.I8])
+def test_byte_medoid_is_exact(dtype):
+    """Byte data: the start is the point nearest to the exact rational mean, checked with Python
+    integers, including a near tie (mirrored points around a mean just off the lattice) and an
+    exact tie (broken towards the smaller index)."""
+    X = synth.mixture(700, 16, dtype, 5, 10.0, seed=32)
+    n = X.shape[0]
+    Xi = [[int(v) for v in r] for r in X]
+    S = [sum(r[t] for r in Xi) for t in range(16)]
+    val = [sum((n * r[t] - S[t]) ** 2 for t in range(16)) for r in Xi]
+    assert oracle.medoid(X) == min(range(n), key=lambda i: (val[i], i))
+    # exact tie: two mirrored points around an integer mean, the rest symmetric too
+    npdt = np.uint8 if dtype == synth.U8 else np.int8
+    lo, hi = (0, 200) if dtype == synth.U8 else (-100, 100)
+    mid = (lo + hi) // 2
+    Y = np.array([[mid + 3, mid], [mid - 3, mid], [mid, mid + 3], [mid, mid - 3],
+                  [lo, lo], [hi, hi], [lo, hi], [hi, lo]], dtype=npdt)
+    assert oracle.medoid(Y) == 0
+    # near tie: the mean is just off the lattice point between the mirrored candidates
+    Z = np.zeros((1000, 2), dtype=npdt)
+    Z[:, :] = mid
+    Z[0] = (mid + 1, mid)
+    Z[1] = (mid - 1, mid)
+    Z[2] = (mid + 1, mid)   # mean x = mid + 1/1000: point 0/2 (x = mid + 1) nearer than point 1
+    Z[3:] = (mid + 5, mid + 5)
+    Zi = [[int(v) for v in r] for r in Z]
+    S = [sum(r[t] for r in Zi) for t in range(2)]
+    val = [sum((1000 * r[t] - S[t]) ** 2 for t in range(2)) for r in Zi]
+    assert oracle.medoid(Z) == min(range(1000), key=lambda i: (val[i], i))
 
 
 @pytest.mark.parametrize("dtype", [synth.U8, synth.I8])
