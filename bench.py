@@ -163,7 +163,47 @@ def cpu_baseline(X, H, w, name, n_sample):
 RECALL_L = (16, 32, 64, 128)
 
 
-def recall_gate(X, H, w, adj_gpu, deg_gpu, n_queries):
+KNN_L = (16, 32, 64)
+
+
+def knn_graph_block(pk, Xd, X, adj, deg, steps, n_sample=2000):
+    """The k-NN graph application of Sec. 5 on the built graph: every point runs Alg. 1 on the GPU
+    with itself as the query and keeps its 10 nearest others (pipnn_knn_graph), timed with CUDA
+    events for several beam widths; recall@10 against the exact 10-NN (without self) of a sample of
+    points; the GPU start (pipnn_medoid) checked against the oracle's."""
+    import oracle
+    import torch
+
+    start = pk.pipnn_medoid(Xd)
+    start_o = oracle.medoid(X)
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(X.shape[0], n_sample, replace=False))
+    t = time.perf_counter()
+    gt = oracle.knn_bytes(X, X[sample], 11)
+    t_gt = time.perf_counter() - t
+    gt10 = [[int(j) for j in r if j != p][:10] for r, p in zip(gt, sample)]
+    rows = []
+    for L in KNN_L:
+        pk.pipnn_knn_graph(Xd, adj, deg, L, k=10, start=start)
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            knn, nd = pk.pipnn_knn_graph(Xd, adj, deg, L, k=10, start=start)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        kh = knn.view(torch.int32).cpu().numpy().view(np.uint32)[sample]
+        rec = float(np.mean([len(set(a.tolist()) & set(b)) / 10 for a, b in zip(kh, gt10)]))
+        m = statistics.mean(ms)
+        rows.append({"L": L, "ms": m, "points_per_s": X.shape[0] / (m / 1e3), "recall_at_10": rec,
+                     "evaluations_per_point": nd / X.shape[0]})
+    return {"k": 10, "start": "medoid (exact, GPU)", "start_equals_oracle": bool(start == start_o),
+            "sample": f"recall over {n_sample} random points against exact 10-NN without self ({t_gt:.1f} s)",
+            "runs": rows}
+
+
+def recall_gate(X, H, w, adj_gpu, deg_gpu, n_queries, Xd=None, pk=None):
     """The metric's gate, measured outside the timed region: the oracle builds the same graph
     (Alg. 4 on the same points, parameters and seed); both graphs are searched with the oracle's
     beam search (Alg. 1) from the medoid at every beam width L for the workload's queries, and
@@ -184,16 +224,26 @@ def recall_gate(X, H, w, adj_gpu, deg_gpu, n_queries):
     gt = oracle.knn_bytes(X, Q, 10)
     t_gt = time.perf_counter() - t
     start = oracle.medoid(X)
-    rec_g, rec_o = [], []
+    rec_g, rec_o, same_search = [], [], []
     for L in RECALL_L:
         ids_g, _ = oracle.beam_search(X, adj_gpu, deg_gpu, Q, L, start=start)
         ids_o, _ = oracle.beam_search(X, adj_o, deg_o, Q, L, start=start)
         rec_g.append(oracle.recall(ids_g, gt))
         rec_o.append(oracle.recall(ids_o, gt))
+        if pk is not None:
+            # the GPU's Alg. 1 on the GPU graph returns the oracle's results query for query
+            import torch
+
+            adj_t = torch.from_numpy(adj_gpu.view(np.int32)).cuda().view(torch.uint32)
+            deg_t = torch.from_numpy(deg_gpu.view(np.int32)).cuda().view(torch.uint32)
+            ids_d, _ = pk.pipnn_beam_search(Xd, adj_t, deg_t, torch.from_numpy(Q).cuda(), L, k=10, start=start)
+            same_search.append(bool(np.array_equal(ids_d.view(torch.int32).cpu().numpy().view(np.uint32), ids_g)))
     gate = all(g >= o - 0.003 for g, o in zip(rec_g, rec_o))
     rec = {"k": 10, "L": list(RECALL_L), "gpu": rec_g, "oracle": rec_o, "gate_pp": 0.3, "pass": gate,
            "graph_identical_to_oracle": identical, "rows_differing": rows_differ, "queries": int(Q.shape[0]),
            "start": "medoid", "ground_truth": f"exact 10-NN by (L2, id) ({t_gt:.1f} s)"}
+    if same_search:
+        rec["gpu_beam_search_identical_to_oracle"] = same_search
     return rec, cpu
 
 
@@ -364,7 +414,7 @@ def phases(stats):
             for k in ("ms_sketch", "ms_partition", "ms_leaf", "ms_hashprune", "ms_prune")}
 
 
-def context_block(pk, steps, warmup, engine, n_queries, cpu_sample, recall=True):
+def context_block(pk, steps, warmup, engine, n_queries, cpu_sample, recall=True, knn=True):
     """The 1M-point bigann-like-u8 build (the configuration the oracle can build inside a run):
     points/s, and the recall gate against the oracle's graph of the same points."""
     import torch
@@ -386,9 +436,13 @@ def context_block(pk, steps, warmup, engine, n_queries, cpu_sample, recall=True)
     if recall:
         adj_g = adj.cpu().numpy().view(np.uint32)
         deg_g = deg.cpu().numpy().view(np.uint32)
-        out["recall"], out["cpu_baseline"] = recall_gate(X, H, w, adj_g, deg_g, n_queries)
+        out["recall"], out["cpu_baseline"] = recall_gate(X, H, w, adj_g, deg_g, n_queries, Xd, pk)
     else:
         out["cpu_baseline"] = cpu_baseline(X, H, w, CONTEXT, cpu_sample)
+    if knn:
+        import torch
+
+        out["knn_graph"] = knn_graph_block(pk, Xd, X, adj.view(torch.uint32), deg.view(torch.uint32), steps)
     del Xd, adj, deg
     return out
 
@@ -472,6 +526,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true", help="skip the recall measurements")
     ap.add_argument("--no-context", action="store_true", help="skip the 1M bigann-like-u8 block")
+    ap.add_argument("--no-knn", action="store_true", help="skip the k-NN graph application in that block")
     ap.add_argument("--no-precision-modes", action="store_true",
                     help="skip the float workload built at every leaf precision")
     ap.add_argument("--queries", type=int, default=None, help="queries of the recall measurement")
@@ -580,7 +635,8 @@ def main():
         if world == 1 and not args.no_context and args.workload != CONTEXT:
             line["bigann_like_u8"] = context_block(pk, min(args.steps, 10), min(args.warmup, 3), args.engine,
                                                    args.queries or synth.WORKLOADS[CONTEXT]["queries"],
-                                                   CONTEXT_CPU_SAMPLE, recall=not args.no_recall)
+                                                   CONTEXT_CPU_SAMPLE, recall=not args.no_recall,
+                                                   knn=not args.no_knn)
             pk.pipnn_trim_pool()
             torch.cuda.empty_cache()
         if world == 1 and not args.no_precision_modes:

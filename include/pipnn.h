@@ -291,6 +291,38 @@ int pipnn_build_batched(const void *const *points, const uint64_t *n, uint32_t c
 int pipnn_build_into(const void *points, uint64_t n, uint32_t d, int32_t metric, const pipnn_params *bp,
                      uint64_t seed, uint32_t *adj, uint32_t *deg);
 
+/* Search start for byte data (u8 / i8): the point nearest to the mean of all points, found
+ * exactly as the argmin of the integer sum_t (n x_t - S_t)^2 with S the exact coordinate sums
+ * (ties to the smaller index).  The paper does not name a start node for Alg. 1; this is the
+ * medoid reading.  points: device, n x d row-major.  Float data: PIPNN_EUNSUPPORTED (the caller
+ * passes its own start).  Synchronises the stream. */
+int pipnn_medoid(const void *points, uint64_t n, uint32_t d, int32_t dtype, uint32_t *medoid);
+
+/* Alg. 1 (BeamSearch) for nq queries at once: from `start`, repeatedly expand the nearest
+ * unvisited node of the beam, evaluate its not yet evaluated out-neighbours, keep the L nearest
+ * by (dissimilarity, id); stop when every beam node is visited; return the k nearest.  The
+ * dissimilarity is the defining one of Sec. 2 (binary32 fused multiply-add chain in index order
+ * for float data, 1 - <x, q> for PIPNN_IP; exact integer squared L2 for byte data), so the result
+ * equals a sequential Alg. 1 on the same values.
+ *   points: device, n x d (dtype); adj: device, n x R uint32 rows, the first deg[v] entries of row
+ *   v are v's out-neighbours (other entries ignored; ids >= n are an error); deg: device, n
+ *   uint32; queries: device, nq x d of the same dtype; ids: device, nq x k uint32, written
+ *   completely (0xFFFFFFFF where the beam holds fewer than k nodes).  1 <= k <= L <= 512,
+ *   1 <= R <= 1024, start < n.  ndist (host, may be NULL) receives the number of dissimilarity
+ *   evaluations (each node evaluated at least once per query it reaches; a node may be evaluated
+ *   twice when a query's evaluated-id set outgrows its table).  Synchronises the stream. */
+int pipnn_beam_search(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
+                      const uint32_t *adj, const uint32_t *deg, uint32_t R, const void *queries, uint64_t nq,
+                      uint32_t start, uint32_t L, uint32_t k, uint32_t *ids, uint64_t *ndist);
+
+/* k-NN graph construction with a built index (Sec. 5): every point p runs Alg. 1 with itself as
+ * the query (beam L) and its row of knn (device, n x k uint32) receives the first k beam nodes
+ * other than p (0xFFFFFFFF where fewer exist).  start = 0xFFFFFFFF takes pipnn_medoid's start
+ * (byte data only).  1 <= k < L <= 512.  Other arguments as pipnn_beam_search. */
+int pipnn_knn_graph(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
+                    const uint32_t *adj, const uint32_t *deg, uint32_t R, uint32_t start, uint32_t L,
+                    uint32_t k, uint32_t *knn, uint64_t *ndist);
+
 /* Returns to the driver the device memory the library's stream-ordered pool keeps for reuse
  * between builds (the pool otherwise holds its high-water mark, so that repeated builds of one
  * size allocate nothing new).  Call it between builds of very different sizes, or before handing

@@ -34,7 +34,8 @@ PIPNN_OK = 0
 EXPORTS = ("pipnn_set_stream", "pipnn_last_error", "pipnn_sketch", "pipnn_partition", "pipnn_leaves_free",
            "pipnn_leaf_pick", "pipnn_edges_free", "pipnn_hashprune", "pipnn_final_prune", "pipnn_build",
            "pipnn_free", "pipnn_build_into", "pipnn_get_stats", "pipnn_hashprune_noalloc", "pipnn_build_batched",
-           "pipnn_leaf_gram", "pipnn_trim_pool", "pipnn_debug_set_alloc_limit", "pipnn_debug_wait_probe")
+           "pipnn_leaf_gram", "pipnn_trim_pool", "pipnn_debug_set_alloc_limit", "pipnn_debug_wait_probe",
+           "pipnn_medoid", "pipnn_beam_search", "pipnn_knn_graph")
 
 
 class PipnnError(RuntimeError):
@@ -110,6 +111,11 @@ def lib():
         L.pipnn_get_stats.argtypes = [C.POINTER(pipnn_stats)]
         L.pipnn_debug_set_alloc_limit.argtypes = [u64]
         L.pipnn_debug_wait_probe.argtypes = [u64]
+        L.pipnn_medoid.argtypes = [vp, u64, u32, i32, C.POINTER(C.c_uint32)]
+        L.pipnn_beam_search.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, vp, u64, u32, u32, u32, vp,
+                                        C.POINTER(C.c_uint64)]
+        L.pipnn_knn_graph.argtypes = [vp, u64, u32, i32, i32, vp, vp, u32, u32, u32, u32, vp,
+                                      C.POINTER(C.c_uint64)]
         _lib = L
     return _lib
 
@@ -359,6 +365,44 @@ def pipnn_debug_wait_probe(limit_ns):
     """The engines' bounded wait on an mbarrier nothing completes; raises PipnnError(-4) after
     limit_ns."""
     _check(lib().pipnn_debug_wait_probe(int(limit_ns)))
+
+
+def pipnn_medoid(points) -> int:
+    """The search start for byte data: the point nearest to the exact mean (device points)."""
+    n, d = points.shape
+    out = C.c_uint32(0)
+    pipnn_set_stream()
+    _check(lib().pipnn_medoid(_ptr(points), n, d, dtype_code(points), C.byref(out)))
+    return int(out.value)
+
+
+def pipnn_beam_search(points, adj, deg, queries, L, k=10, start=None, metric=PIPNN_L2):
+    """Alg. 1 for every row of queries (device tensors).  start None: pipnn_medoid's start (byte
+    data).  Returns (ids nq x k uint32 on the device, number of dissimilarity evaluations)."""
+    n, d = points.shape
+    nq = queries.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device=points.device).view(torch.uint32)
+    nd = C.c_uint64(0)
+    if start is None:
+        start = pipnn_medoid(points)
+    pipnn_set_stream()
+    _check(lib().pipnn_beam_search(_ptr(points), n, d, dtype_code(points), metric, _ptr(adj), _ptr(deg),
+                                   adj.shape[1], _ptr(queries), nq, int(start), L, k, _ptr(ids), C.byref(nd)))
+    return ids, int(nd.value)
+
+
+def pipnn_knn_graph(points, adj, deg, L, k=10, start=None, metric=PIPNN_L2):
+    """k-NN graph construction with the built graph (Sec. 5): every point queries with itself.
+    start None: pipnn_medoid's start (byte data).  Returns (knn n x k uint32 on the device,
+    number of dissimilarity evaluations)."""
+    n, d = points.shape
+    knn = torch.empty((n, k), dtype=torch.int32, device=points.device).view(torch.uint32)
+    nd = C.c_uint64(0)
+    pipnn_set_stream()
+    _check(lib().pipnn_knn_graph(_ptr(points), n, d, dtype_code(points), metric, _ptr(adj), _ptr(deg),
+                                 adj.shape[1], 0xFFFFFFFF if start is None else int(start), L, k, _ptr(knn),
+                                 C.byref(nd)))
+    return knn, int(nd.value)
 
 
 def pipnn_trim_pool():

@@ -30,6 +30,10 @@ int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32
                     uint32_t *deg);
 int leaf_gram_tcf(const float *X, uint32_t d, int metric, int prec, const uint64_t *off, const uint32_t *mem,
                   uint64_t L, float *gram, Workspace &ws);
+int medoid_bytes(const void *X, uint64_t n, uint32_t d, int dtype, uint32_t *medoid_host, Workspace &ws);
+int beam_search_batch(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const uint32_t *adj,
+                      const uint32_t *deg, uint32_t R, const void *Q, uint64_t nq, uint32_t start, uint32_t L,
+                      uint32_t k, int exclude_self, uint32_t *ids, uint64_t *ndist_host, Workspace &ws);
 
 namespace {
 thread_local pipnn_stats g_stats;
@@ -641,6 +645,58 @@ int pipnn_build_batched(const void *const *points, const uint64_t *n, uint32_t c
     BatchDesc b{points, n, seeds, count, outs};
     pipnn_graph whole;
     return build_impl(points[0], total, d, metric, bp, 0, 3, &whole, nullptr, nullptr, &b);
+}
+
+int pipnn_medoid(const void *points, uint64_t n, uint32_t d, int32_t dtype, uint32_t *medoid) {
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    PIPNN_TRY(check_points(points, n, d, dtype, PIPNN_L2));
+    if (!medoid) return set_error(PIPNN_EINVAL, "medoid is NULL");
+    if (!is_device_ptr(points)) return set_error(PIPNN_EINVAL, "points must be a device pointer");
+    PIPNN_TRY(medoid_bytes(points, n, d, dtype, medoid, cs.ws));
+    return check_device_error("medoid");
+}
+
+static int search_common(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
+                         const uint32_t *adj, const uint32_t *deg, uint32_t R, const void *queries, uint64_t nq,
+                         uint32_t *start, uint32_t L, uint32_t k, int exclude_self, uint32_t *ids, uint64_t *ndist,
+                         const char *what) {
+    if (ndist) *ndist = 0;
+    CallScope cs;
+    PIPNN_TRY(cs.init());
+    PIPNN_TRY(check_points(points, n, d, dtype, metric));
+    if (!adj || !deg || !ids || !queries) return set_error(PIPNN_EINVAL, "%s: NULL array", what);
+    if (!is_device_ptr(points) || !is_device_ptr(adj) || !is_device_ptr(deg) || !is_device_ptr(queries) ||
+        !is_device_ptr(ids))
+        return set_error(PIPNN_EINVAL, "%s: points, adj, deg, queries and the output must be device pointers", what);
+    if (R < 1 || R > 1024) return set_error(PIPNN_EINVAL, "%s: R outside 1..1024", what);
+    if (L < 1 || L > 512) return set_error(PIPNN_EINVAL, "%s: L outside 1..512", what);
+    if (k < 1 || k + (exclude_self ? 1u : 0u) > L)
+        return set_error(PIPNN_EINVAL, exclude_self ? "%s: need 1 <= k < L" : "%s: need 1 <= k <= L", what);
+    if (*start == 0xFFFFFFFFu) PIPNN_TRY(medoid_bytes(points, n, d, dtype, start, cs.ws));
+    if (*start >= n) return set_error(PIPNN_EINVAL, "%s: start %u is not a point", what, *start);
+    PIPNN_TRY(beam_search_batch(points, n, d, dtype, metric, adj, deg, R, queries, nq, *start, L, k, exclude_self,
+                                ids, ndist, cs.ws));
+    return check_device_error(what);
+}
+
+int pipnn_beam_search(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric, const uint32_t *adj,
+                      const uint32_t *deg, uint32_t R, const void *queries, uint64_t nq, uint32_t start, uint32_t L,
+                      uint32_t k, uint32_t *ids, uint64_t *ndist) {
+    if (nq == 0) {
+        if (ndist) *ndist = 0;
+        return PIPNN_OK;
+    }
+    if (start == 0xFFFFFFFFu) return set_error(PIPNN_EINVAL, "beam search: start %u is not a point", start);
+    return search_common(points, n, d, dtype, metric, adj, deg, R, queries, nq, &start, L, k, 0, ids, ndist,
+                         "beam search");
+}
+
+int pipnn_knn_graph(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric, const uint32_t *adj,
+                    const uint32_t *deg, uint32_t R, uint32_t start, uint32_t L, uint32_t k, uint32_t *knn,
+                    uint64_t *ndist) {
+    return search_common(points, n, d, dtype, metric, adj, deg, R, points, n, &start, L, k, 1, knn, ndist,
+                         "k-NN graph");
 }
 
 int pipnn_trim_pool(void) {
