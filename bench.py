@@ -166,6 +166,49 @@ RECALL_L = (16, 32, 64, 128)
 KNN_L = (16, 32, 64)
 
 
+def multi_index_block(pk, steps):
+    """The multi-index workload: 512 independent float indexes (sizes log-uniform in 2,000 ..
+    200,000, 128-d, L2; C_max 1024, l_max 64, R 48, fanout [2]) built by one batched pipeline
+    (pipnn_build_batched), timed with CUDA events, against a loop of one pipnn_build per index
+    over the same points; every batched graph is checked equal to its single build."""
+    import torch
+
+    sizes = synth.multi_index_sizes()
+    d = 128
+    pts = [synth.mixture_device(int(s), d, synth.F32, max(10, int(s) // 200), 0.3, 10000 + i)
+           for i, s in enumerate(sizes)]
+    H = torch.from_numpy(synth.hyperplanes(12, d)).cuda()
+    bp = pk.params(dtype=pk.PIPNN_F32, hyperplanes=H, leaf_engine=pk.PIPNN_LEAF_TC, prec=pk.PIPNN_PREC_BF16X3,
+                   c_max=1024, l_max=64, R=48, fanout=(2,))
+    seeds = [synth.BUILD_SEED] * len(sizes)
+    total = int(sizes.sum())
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    pk.pipnn_build_batched(pts, bp, seeds)
+    ms_b = []
+    for _ in range(steps):
+        graphs, ms = timed(lambda: pk.pipnn_build_batched(pts, bp, seeds))
+        ms_b.append(ms)
+    pk.pipnn_build(pts[0], bp, seeds[0])
+    serial, ms_s = timed(lambda: [pk.pipnn_build(p, bp, sd) for p, sd in zip(pts, seeds)])
+    same = all(torch.equal(ga, sa) and torch.equal(gd, sd_) for (ga, gd), (sa, sd_) in zip(graphs, serial))
+    mb = statistics.mean(ms_b)
+    return {"indexes": len(sizes), "points": total, "d": d, "dtype": "f32", "metric": "L2", "c_max": 1024,
+            "l_max": 64, "R": 48, "fanout": [2], "leaf_engine": "tc", "prec": "bf16x3",
+            "batched": {"ms": mb, "points_per_s": total / (mb / 1e3), "steps": steps},
+            "serial_loop": {"ms": ms_s, "points_per_s": total / (ms_s / 1e3)},
+            "speedup": ms_s / mb, "batched_graphs_equal_single_builds": bool(same),
+            "data": "synthetic: index i drawn with seed 10000 + i, max(10, n_i / 200) centres, sigma 0.3"}
+
+
 def knn_graph_block(pk, Xd, X, adj, deg, steps, n_sample=2000):
     """The k-NN graph application of Sec. 5 on the built graph: every point runs Alg. 1 on the GPU
     with itself as the query and keeps its 10 nearest others (pipnn_knn_graph), timed with CUDA
@@ -527,6 +570,7 @@ def main():
     ap.add_argument("--no-recall", action="store_true", help="skip the recall measurements")
     ap.add_argument("--no-context", action="store_true", help="skip the 1M bigann-like-u8 block")
     ap.add_argument("--no-knn", action="store_true", help="skip the k-NN graph application in that block")
+    ap.add_argument("--no-multi-index", action="store_true", help="skip the 512-index batched block")
     ap.add_argument("--no-precision-modes", action="store_true",
                     help="skip the float workload built at every leaf precision")
     ap.add_argument("--queries", type=int, default=None, help="queries of the recall measurement")
@@ -637,6 +681,10 @@ def main():
                                                    args.queries or synth.WORKLOADS[CONTEXT]["queries"],
                                                    CONTEXT_CPU_SAMPLE, recall=not args.no_recall,
                                                    knn=not args.no_knn)
+            pk.pipnn_trim_pool()
+            torch.cuda.empty_cache()
+        if world == 1 and not args.no_multi_index:
+            line["multi_index"] = multi_index_block(pk, min(args.steps, 3))
             pk.pipnn_trim_pool()
             torch.cuda.empty_cache()
         if world == 1 and not args.no_precision_modes:

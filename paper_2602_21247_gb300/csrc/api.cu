@@ -13,19 +13,18 @@ void set_device_error_word(unsigned *p);
 int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float *H, uint32_t m, float *S,
                   void *sqnorm);
 int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out, uint16_t *level0_code);
+                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out);
 int partition_points_batch(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                            const pipnn_params *bp, const uint64_t *idx_off, const uint64_t *seeds, uint64_t count,
-                           pipnn_leaves *out, uint16_t *level0_code);
+                           pipnn_leaves *out);
 int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
               const uint64_t *off, const uint32_t *mem, uint64_t L, uint32_t k, int engine, int prec,
               int direction, pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows);
 int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
-                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt);
+                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt, int padded);
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                 const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, int engine,
-                uint32_t *adj, uint32_t *deg, const uint32_t *order);
-int order_by_code(const uint16_t *code, uint64_t n, uint32_t *order, Workspace &ws);
+                uint32_t *adj, uint32_t *deg);
 int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, uint32_t *adj,
                     uint32_t *deg);
 int leaf_gram_tcf(const float *X, uint32_t d, int metric, int prec, const uint64_t *off, const uint32_t *mem,
@@ -302,10 +301,6 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     PIPNN_TRY(ws.zeros(&acc, 1));
     uint64_t *res = nullptr;
     uint32_t *cnt = nullptr;
-    // every point's nearest level-0 leader: the prune visits nodes grouped by it, so nodes whose
-    // candidates share rows are pruned together (a processing order only; results do not change)
-    uint16_t *code = nullptr;
-    PIPNN_TRY(ws.zeros(&code, n));
     for (uint32_t r = 0; r < replicas; r++) {
         std::vector<uint64_t> seed_r(idx_seed.size());
         for (size_t i = 0; i < idx_seed.size(); i++) seed_r[i] = idx_seed[i] + (uint64_t)r * 0x9E3779B97F4A7C15ull;
@@ -313,7 +308,7 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
         // A1 (every index of a batch with its own seed, in one pass)
         pipnn_leaves leaves;
         PIPNN_TRY(partition_points_batch(X, n, d, dtype, metric, sqn_bytes, bp, idx_off.data(), seed_r.data(),
-                                         idx_seed.size(), &leaves, r == 0 ? code : nullptr));
+                                         idx_seed.size(), &leaves));
         rt[r].mark(1);
         st.levels = leaves.levels > st.levels ? leaves.levels : st.levels;
         st.leaves += leaves.num_leaves;
@@ -375,7 +370,7 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
             }
             if (rc == PIPNN_OK) {
                 note_peak(&st);
-                rc = hashprune_merge(edges.dst, edges.src, edges.dist, edges.count, S, m, n, bp->l_max, res, cnt);
+                rc = hashprune_merge(edges.dst, edges.src, edges.dist, edges.count, S, m, n, bp->l_max, res, cnt, 1);
                 wt.mark(2);
             }
             dev_free_raw(edges.dst);
@@ -403,13 +398,10 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     uint32_t *adj = nullptr, *deg = nullptr;
     PIPNN_TRY(dev_alloc_raw((void **)&adj, n * bp->R * 4));
     rc = dev_alloc_raw((void **)&deg, n * 4);
-    uint32_t *order = nullptr;
-    if (rc == PIPNN_OK) rc = ws.alloc(&order, n);
-    if (rc == PIPNN_OK) rc = order_by_code(code, n, order, ws);
     if (rc == PIPNN_OK) {
         if (bp->final_prune)
             rc = final_prune(X, n, d, dtype, metric, sqn_bytes, res, cnt, bp->l_max, bp->R, bp->alpha, bp->leaf_engine,
-                             adj, deg, order);
+                             adj, deg);
         else
             rc = reservoir_graph(n, res, cnt, bp->l_max, bp->R, adj, deg);
     }
@@ -532,7 +524,7 @@ int pipnn_partition(const void *points, uint64_t n, uint32_t d, int32_t metric, 
     PIPNN_TRY(cs.init());
     PIPNN_TRY(check_params(bp));
     PIPNN_TRY(check_points(points, n, d, bp->dtype, metric));
-    return partition_points(points, n, d, bp->dtype, metric, nullptr, bp, seed, out, nullptr);
+    return partition_points(points, n, d, bp->dtype, metric, nullptr, bp, seed, out);
 }
 
 void pipnn_leaves_free(pipnn_leaves *l) {
@@ -586,7 +578,7 @@ int pipnn_hashprune(const uint32_t *dst, const uint32_t *src, const float *dist,
     if (count && (!dst || !src || !dist)) return set_error(PIPNN_EINVAL, "candidate arrays are NULL");
     if (!sketch || !reservoir || !count_inout) return set_error(PIPNN_EINVAL, "sketch/reservoir/count are NULL");
     if (n == 0 || n >= 0xFFFFFFFFull) return set_error(PIPNN_EINVAL, "n outside 1..2^32-2");
-    return hashprune_merge(dst, src, dist, count, sketch, m, n, l_max, reservoir, count_inout);
+    return hashprune_merge(dst, src, dist, count, sketch, m, n, l_max, reservoir, count_inout, 0);
 }
 
 int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype, int32_t metric,
@@ -599,8 +591,7 @@ int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype,
     if (l_max < 1 || l_max > 256 || R < 1 || R > l_max) return set_error(PIPNN_EINVAL, "need 1 <= R <= l_max <= 256");
     if (!(alpha >= 1.0f) || !std::isfinite(alpha)) return set_error(PIPNN_EINVAL, "alpha must be finite and >= 1");
     if (engine != PIPNN_LEAF_SIMT && engine != PIPNN_LEAF_TC) return set_error(PIPNN_EINVAL, "unknown engine %d", engine);
-    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, engine, adj, deg,
-                          nullptr));
+    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, engine, adj, deg));
     return check_device_error("final prune");
 }
 

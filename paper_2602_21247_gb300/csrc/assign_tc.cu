@@ -46,7 +46,6 @@ struct AsUnit {
 struct AsArgs {
     const AsUnit *units;
     const uint32_t *inst;       // instance -> point id
-    const uint32_t *pos;        // point id -> its row in the plan's copy (null: the id itself)
     const int32_t *inst_norm;   // instance -> exact squared norm of its point
     const int32_t *lead_norm;   // exact squared norm of every leader row
     uint32_t fanout;            // F <= KMAX; stride of assign
@@ -190,119 +189,113 @@ __global__ void __launch_bounds__(THREADS, 1)
                          : "memory");
         }
         fence_proxy_async();
-        // job stream: per unit one A job (gather of its instance rows), then one B job per 128
-        // leaders.  The next job's ids or norms are loaded while the current one is issued.
-        struct Job {
-            uint32_t kind;  // 0 A, 1 B, 2 end
-            uint32_t i, u, t, nct;
-            AsUnit un;
+        // Per unit i of this CTA (u = blockIdx.x + i gridDim.x): one A job (the gather of its
+        // instance rows), then one B job per 128 leaders.  The loads a job depends on are requested
+        // ahead, so the producer never waits on a chain of its own loads: unit descriptors two
+        // units ahead, instance ids (the rows of the copy) one unit ahead, and the leader norms of
+        // the next B job (of this unit or the next) during the current one.
+        const uint32_t G = gridDim.x;
+        auto desc = [&](uint32_t i) {
+            const uint64_t u = blockIdx.x + (uint64_t)i * G;
+            AsUnit x{};  // nrows = 0: past the last unit
+            if (u < nunits) x = a.units[u];
+            return x;
         };
-        auto unit_job = [&](uint32_t i, uint32_t u) {
-            Job q;
-            q.kind = 2;
-            if (u >= nunits) return q;
-            q.un = a.units[u];
-            q.kind = 0;
-            q.i = i;
-            q.u = u;
-            q.t = 0;
-            q.nct = (q.un.ncols + C::NMAX - 1) / C::NMAX;
-            return q;
-        };
-        auto next_job = [&](const Job &c) {
-            Job q = c;
-            if (c.kind == 0) {
-                q.kind = 1;
-                q.t = 0;
-                return q;
-            }
-            if (c.t + 1 < c.nct) {
-                q.t = c.t + 1;
-                return q;
-            }
-            return unit_job(c.i + 1, c.u + gridDim.x);
-        };
-        auto load_vals = [&](const Job &q, uint32_t (&v)[4]) {
+        auto inst_ids = [&](const AsUnit &un, uint32_t (&v)[4]) {
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                v[e] = 0u;
-                if (q.kind == 0) {
-                    // rows past the subproblem repeat its last instance; their results are unused
-                    uint32_t r = q.un.row0 + 4 * lane + e;
-                    r = r < q.un.nrows ? r : q.un.nrows - 1;
-                    v[e] = a.inst[q.un.inst0 + r];
-                    if (a.pos) v[e] = a.pos[v[e]];
-                } else if (q.kind == 1) {
-                    const uint32_t c = q.t * C::NMAX + 4 * lane + e;
-                    v[e] = c < q.un.ncols ? (uint32_t)a.lead_norm[q.un.lead0 + c] : 0u;
-                }
+                // rows past the subproblem repeat its last instance; their results are unused
+                uint32_t r = un.row0 + 4 * lane + e;
+                r = r < un.nrows ? r : un.nrows - 1;
+                v[e] = un.nrows ? a.inst[un.inst0 + r] : 0u;
             }
         };
-        Job cur = unit_job(0, blockIdx.x);
-        uint32_t v[4];
-        load_vals(cur, v);
-        uint32_t j = 0;
-        while (cur.kind != 2) {
-            const Job nxt = next_job(cur);
-            uint32_t nv[4];
-            load_vals(nxt, nv);
-            bool ok;
-            if (cur.kind == 0) {
-                const uint32_t ua = cur.i & 1;
-                ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + ua), ((cur.i >> 1) & 1) ^ 1, abort, a.err));
-                if (ok) {
-                    const uint32_t fb = bar(C::BAR_FULL_A + ua);
-                    if (lane == 0) mbar_arrive_tx(fb, KB * REGION);
-                    __syncwarp();
-                    // lane L fetches tile rows 4L..4L+3 of every K block
-                    const uint32_t dst = sbase + C::OFF_A0 + ua * KB * REGION + lane * 4 * 128;
+        auto lead_norms = [&](const AsUnit &un, uint32_t t, uint32_t (&v)[4]) {
 #pragma unroll
-                    for (int kb = 0; kb < KB; kb++)
-                        tma_gather4(dst + kb * REGION, &xmap, kb * 64, (int32_t)v[0], (int32_t)v[1], (int32_t)v[2],
-                                    (int32_t)v[3], fb);
-                }
-            } else {
+            for (int e = 0; e < 4; e++) {
+                const uint32_t c = t * C::NMAX + 4 * lane + e;
+                v[e] = (un.nrows && c < un.ncols) ? (uint32_t)a.lead_norm[un.lead0 + c] : 0u;
+            }
+        };
+        AsUnit d0 = desc(0), d1 = desc(1), d2 = desc(2);
+        uint32_t rows0[4], rows1[4], nrm[4];
+        inst_ids(d0, rows0);
+        inst_ids(d1, rows1);
+        lead_norms(d0, 0, nrm);
+        uint32_t j = 0;
+        bool ok = true;
+        for (uint32_t i = 0; ok && blockIdx.x + (uint64_t)i * G < nunits; i++) {
+            // A job: lane L fetches tile rows 4L..4L+3 of every K block
+            const uint32_t ua = i & 1;
+            ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + ua), ((i >> 1) & 1) ^ 1, abort, a.err));
+            if (!ok) break;
+            {
+                const uint32_t fb = bar(C::BAR_FULL_A + ua);
+                if (lane == 0) mbar_arrive_tx(fb, KB * REGION);
+                __syncwarp();
+                const uint32_t dst = sbase + C::OFF_A0 + ua * KB * REGION + lane * 4 * 128;
+#pragma unroll
+                for (int kb = 0; kb < KB; kb++)
+                    tma_gather4(dst + kb * REGION, &xmap, kb * 64, (int32_t)rows0[0], (int32_t)rows0[1],
+                                (int32_t)rows0[2], (int32_t)rows0[3], fb);
+            }
+            uint32_t rows2[4];
+            const AsUnit d3 = desc(i + 3);
+            inst_ids(d2, rows2);
+            // B jobs
+            const uint32_t nct = (d0.ncols + C::NMAX - 1) / C::NMAX;
+            for (uint32_t t = 0; t < nct; t++, j++) {
+                uint32_t nn[4];
+                if (t + 1 < nct) lead_norms(d0, t + 1, nn);
+                else lead_norms(d1, 0, nn);
                 const uint32_t st = j % C::S;
                 ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY + st), ((j / C::S) & 1) ^ 1, abort, a.err));
-                if (ok) {
+                if (!ok) break;
 #pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const uint32_t r = 4 * lane + e;
-                        const uint2 pc = neg_half_norm_pieces(v[e]);
-                        const uint32_t nb = sbase + C::OFF_BN + r * 128;
-                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st) ^ (r & 7)) << 4)),
-                                     "r"(pc.x), "r"(pc.y), "r"(0u), "r"(0u)
-                                     : "memory");
-                        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st + 1) ^ (r & 7)) << 4)),
-                                     "r"(0u), "r"(0u), "r"(0u), "r"(0u)
-                                     : "memory");
-                    }
-                    fence_proxy_async();
-                    const uint32_t fb = bar(C::BAR_FULL + st);
-                    if (lane == 0) {
-                        mbar_arrive_tx(fb, KB * REGION);
-                        const uint32_t dst = sbase + C::OFF_B0 + st * KB * REGION;
-                        const int32_t y = (int32_t)(cur.un.lead0 + (uint64_t)cur.t * C::NMAX);
-#pragma unroll
-                        for (int kb = 0; kb < KB; kb++) tma_load_tile(dst + kb * REGION, &lmap, kb * 64, y, fb);
-                    } else {
-                        mbar_arrive(fb);
-                    }
+                for (int e = 0; e < 4; e++) {
+                    const uint32_t r = 4 * lane + e;
+                    const uint2 pc = neg_half_norm_pieces(nrm[e]);
+                    const uint32_t nb = sbase + C::OFF_BN + r * 128;
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st) ^ (r & 7)) << 4)),
+                                 "r"(pc.x), "r"(pc.y), "r"(0u), "r"(0u)
+                                 : "memory");
+                    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(nb + (((2 * st + 1) ^ (r & 7)) << 4)),
+                                 "r"(0u), "r"(0u), "r"(0u), "r"(0u)
+                                 : "memory");
                 }
-                j++;
-            }
-            if (!ok) break;
-            cur = nxt;
+                fence_proxy_async();
+                const uint32_t fb = bar(C::BAR_FULL + st);
+                if (lane == 0) {
+                    mbar_arrive_tx(fb, KB * REGION);
+                    const uint32_t dst = sbase + C::OFF_B0 + st * KB * REGION;
+                    const int32_t y = (int32_t)(d0.lead0 + (uint64_t)t * C::NMAX);
 #pragma unroll
-            for (int e = 0; e < 4; e++) v[e] = nv[e];
+                    for (int kb = 0; kb < KB; kb++) tma_load_tile(dst + kb * REGION, &lmap, kb * 64, y, fb);
+                } else {
+                    mbar_arrive(fb);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; e++) nrm[e] = nn[e];
+            }
+            d0 = d1;
+            d1 = d2;
+            d2 = d3;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                rows0[e] = rows1[e];
+                rows1[e] = rows2[e];
+            }
         }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t j = 0, issued_j = 0;
             bool any = false, stop = false;
+            // the next unit's leader count is requested one unit ahead
+            uint32_t nc_next = blockIdx.x < nunits ? a.units[blockIdx.x].ncols : 0u;
             for (uint32_t i = 0, u = blockIdx.x; u < nunits && !stop; i++, u += gridDim.x) {
-                const uint32_t ncols = a.units[u].ncols;
+                const uint32_t ncols = nc_next;
+                nc_next = u + gridDim.x < nunits ? a.units[u + gridDim.x].ncols : 0u;
                 const uint32_t ua = i & 1;
                 if (!mbar_wait(bar(C::BAR_FULL_A + ua), (i >> 1) & 1, abort, a.err)) break;
                 const uint32_t aB = sbase + C::OFF_A0 + ua * KB * REGION;
@@ -352,8 +345,21 @@ __global__ void __launch_bounds__(THREADS, 1)
         float2 *mv = reinterpret_cast<float2 *>(smem + C::OFF_MV);
         uint32_t j = 0;
         bool failed = false;
+        // unit descriptors are requested two units ahead and the row's instance norm one unit
+        // ahead, so no unit starts with a wait on a chain of loads
+        auto desc = [&](uint64_t u) {
+            AsUnit x{};
+            if (u < nunits) x = a.units[u];
+            return x;
+        };
+        auto row_norm = [&](const AsUnit &x) {
+            return (KMAX <= 4 && x.row0 + r < x.nrows) ? a.inst_norm[x.inst0 + x.row0 + r] : 0;
+        };
+        AsUnit un = desc(blockIdx.x), un1 = desc(blockIdx.x + (uint64_t)gridDim.x);
+        int32_t nrm = row_norm(un);
         for (uint32_t i = 0, u = blockIdx.x; u < nunits; i++, u += gridDim.x) {
-            const AsUnit un = a.units[u];
+            const AsUnit un2 = desc(u + 2 * (uint64_t)gridDim.x);
+            const int32_t nrm1 = row_norm(un1);
             const bool row_ok = un.row0 + r < un.nrows;
             // F <= 4: the KMAX smallest (D << 32 | rank), D = n_x - 2 w the squared distance
             uint64_t RK[KMAX];
@@ -361,7 +367,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if constexpr (KMAX <= 4) {
 #pragma unroll
                 for (int p = 0; p < KMAX; p++) RK[p] = ~0ull;
-                nb23 = (float)(row_ok ? a.inst_norm[un.inst0 + un.row0 + r] : 0) + 8388608.0f;  // n_x + 2^23
+                nb23 = (float)(row_ok ? nrm : 0) + 8388608.0f;  // n_x + 2^23
             }
             // KMAX - F padding entries (+inf) in front, then the F live ones
             float kv[KMAX];
@@ -501,7 +507,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             failed = named_barrier_or(1, EPI_WARPS * 32, failed || *abort);
             if (failed) break;
             const uint32_t nu = u + gridDim.x;
-            if (nu >= nunits || a.units[nu].seg != un.seg) {
+            if (nu >= nunits || un1.seg != un.seg) {
                 for (uint32_t c = et; c < un.ncols && c < AS_HIST; c += EPI_WARPS * 32) {
                     const uint32_t h = hist[c];
                     if (h) {
@@ -510,6 +516,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
             }
+            un = un1;
+            un1 = un2;
+            nrm = nrm1;
         }
     }
 
@@ -584,14 +593,6 @@ int assign_tc_plan(const void *X, uint64_t n, uint32_t d, int dtype, Workspace &
     return PIPNN_OK;
 }
 
-int assign_tc_plan_reorder(const void *X, uint64_t n, uint32_t d, int dtype, const uint32_t *order, Workspace &ws,
-                           AssignTcPlan *plan) {
-    if (!plan->rows) return set_error(PIPNN_EINVAL, "no assignment plan to reorder");
-    if (!plan->pos) PIPNN_TRY(ws.alloc(&plan->pos, n ? n : 1));
-    PIPNN_TRY(inverse_order(order, n, plan->pos));
-    return stage_rows_bf16(X, d, plan->kp, dtype, order, n, plan->rows);
-}
-
 int assign_tc(const AssignTcPlan &plan, const void *X, uint32_t d, int dtype, const int32_t *sqnorm,
               const uint32_t *tile_grp, const uint32_t *tile_row0, uint64_t ntiles, const uint64_t *seg_start,
               const uint32_t *seg_size, const uint32_t *inst, const uint64_t *lead_off, const uint32_t *lead_cnt,
@@ -624,7 +625,6 @@ int assign_tc(const AssignTcPlan &plan, const void *X, uint32_t d, int dtype, co
     AsArgs a{};
     a.units = units;
     a.inst = inst;
-    a.pos = plan.pos;
     a.inst_norm = inorm;
     a.lead_norm = lnorm;
     a.fanout = F;

@@ -209,9 +209,10 @@ __device__ __forceinline__ void warp_bitonic_sort(uint64_t *buf, uint32_t P, int
     }
 }
 
+// padded: rows past cnt[v] already hold 0xFF..FF (a node without new slots is then left alone)
 __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_t m, uint32_t l_max,
                                                          const uint64_t *start, const uint64_t *slots,
-                                                         uint64_t *res, uint32_t *cnt) {
+                                                         uint64_t *res, uint32_t *cnt, int padded) {
     extern __shared__ __align__(16) unsigned char hp_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bm_words = m >= 5 ? (1u << (m - 5)) : 1u;
@@ -246,8 +247,10 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
             n_b = start[v + stride];
         }
         if (a == b) {
-            // no new candidates: the reservoir is unchanged (normalise the padding)
-            for (uint32_t t = cur + lane; t < l_max; t += 32) res[v * l_max + t] = ~0ull;
+            // no new candidates: the reservoir is unchanged (normalise the padding unless the
+            // caller keeps it)
+            if (!padded)
+                for (uint32_t t = cur + lane; t < l_max; t += 32) res[v * l_max + t] = ~0ull;
             continue;
         }
         // walk buf[0 .. nb) ascending, keep the first slot of every unseen hash bucket (compacted
@@ -462,7 +465,7 @@ size_t hashprune_smem_bytes(uint32_t m) {
 }
 
 int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
-                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt) {
+                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt, int padded) {
     if (m < 1 || m > 16) return set_error(PIPNN_EINVAL, "hash_bits %u outside 1..16", m);
     if (l_max < 1 || l_max > 256) return set_error(PIPNN_EINVAL, "l_max %u outside 1..256", l_max);
     Workspace ws;
@@ -492,7 +495,8 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
     }
     size_t smem = hashprune_smem_bytes(m);
     PIPNN_CUDA(cudaFuncSetAttribute(hp_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    hp_merge<<<grid_for(n, HP_WARPS, 152u * 8u), HP_WARPS * 32, smem, stream()>>>(n, m, l_max, start, slots, res, cnt);
+    hp_merge<<<grid_for(n, HP_WARPS, 152u * 8u), HP_WARPS * 32, smem, stream()>>>(n, m, l_max, start, slots, res, cnt,
+                                                                                   padded);
     PIPNN_LAUNCH_CHECK();
     return check_device_error("hashprune");
 }
@@ -610,7 +614,8 @@ int hashprune_noalloc_impl(const uint32_t *dst, const uint32_t *src, const float
     }
     const size_t smem = hashprune_smem_bytes(m);
     PIPNN_CUDA(cudaFuncSetAttribute(hp_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    hp_merge<<<grid_for(n, HP_WARPS, 152u * 8u), HP_WARPS * 32, smem, stream()>>>(n, m, l_max, start, slots, res, cnt);
+    hp_merge<<<grid_for(n, HP_WARPS, 152u * 8u), HP_WARPS * 32, smem, stream()>>>(n, m, l_max, start, slots, res, cnt,
+                                                                                   0);
     PIPNN_LAUNCH_CHECK();
     return check_device_error("hashprune (static scratch)");
 }

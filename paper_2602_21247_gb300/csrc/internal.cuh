@@ -131,10 +131,6 @@ int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t *out, uint64_t n, ui
                                uint64_t *scratch);
 // copy one device value to the host (synchronises the stream)
 int read_u64(const uint64_t *dev, uint64_t *host);
-// a permutation of 0..n-1 grouping equal codes (codes below 1024; order inside a group is any)
-int order_by_code(const uint16_t *code, uint64_t n, uint32_t *order, Workspace &ws);
-// pos[order[i]] = i
-int inverse_order(const uint32_t *order, uint64_t n, uint32_t *pos);
 
 // Tiles: for groups of sizes size[g], tile t covers rows [row0, row0 + tile) of group grp[t].
 // Produces tile_grp/tile_row0 arrays of total ceil(size/tile) entries; total on host.

@@ -421,12 +421,6 @@ uint32_t fanout_at(const pipnn_params *bp, uint32_t depth) {
 }
 }  // namespace
 
-// Level 0: instance i is point i; its nearest leader's rank is its first assignment slot.
-__global__ void level0_code(const uint32_t *inst, const uint16_t *assign, uint64_t N, uint32_t F, uint16_t *code) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < N; i += (uint64_t)gridDim.x * blockDim.x)
-        code[inst[i]] = assign[i * F];
-}
-
 // Points of the `count` indexes of a batch: index i holds point ids idx_off[i] .. idx_off[i+1).
 __global__ void batch_level0(uint64_t count, const uint64_t *big_off, const uint64_t *big_start,
                              const uint64_t *big_seed, uint32_t *seg_size, uint64_t *seg_start, uint64_t *seg_seed,
@@ -451,14 +445,13 @@ __global__ void batch_instances(uint64_t count, const uint64_t *big_off, const u
     }
 }
 
-// level0_code (optional, n entries): receives every point's nearest level-0 leader (its rank).
 // Alg. 5 over a batch of `count` independent indexes at once: index i holds the points
 // idx_off[i] .. idx_off[i+1) (host array) and is partitioned with seeds[i] (host array), with its
 // point ids taken relative to idx_off[i] wherever the randomness sees them, so every index gets the
 // leaves a separate partition of it would get (its members as global ids).
 int partition_points_batch(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                            const pipnn_params *bp, const uint64_t *idx_off, const uint64_t *seeds, uint64_t count,
-                           pipnn_leaves *out, uint16_t *level0_code_out) {
+                           pipnn_leaves *out) {
     memset(out, 0, sizeof(*out));
     Workspace leaf_ws;
     std::vector<LevelLeaves> levels;
@@ -626,21 +619,6 @@ int partition_points_batch(const void *X, uint64_t n, uint32_t d, int dtype, int
                                 bucket_cnt, tw));
         } else {
             PIPNN_TRY(launch_allpairs<MODE_ASSIGN>(dtype, metric, F, a, ntiles));
-        }
-
-        if (depth == 0 && (level0_code_out || tc_plan.rows)) {
-            // every point's nearest level-0 leader; the deeper levels' subproblems hold points near
-            // one another, so the TC plan's rows are restaged grouped by it (locality of the gathers)
-            uint16_t *code = level0_code_out;
-            if (!code) PIPNN_TRY(tc_ws.zeros(&code, n));
-            level0_code<<<grid_for(N, 256), 256, 0, stream()>>>(cur->inst, assign, N, F, code);
-            PIPNN_LAUNCH_CHECK();
-            if (tc_plan.rows) {
-                uint32_t *order = nullptr;
-                PIPNN_TRY(tw.alloc(&order, n));
-                PIPNN_TRY(order_by_code(code, n, order, tw));
-                PIPNN_TRY(assign_tc_plan_reorder(X, n, d, dtype, order, tc_ws, &tc_plan));
-            }
         }
 
         // 3. Merge plan
@@ -825,9 +803,9 @@ int partition_points_batch(const void *X, uint64_t n, uint32_t d, int dtype, int
 }
 
 int partition_points(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
-                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out, uint16_t *level0_code) {
+                     const pipnn_params *bp, uint64_t seed, pipnn_leaves *out) {
     const uint64_t off[2] = {0, n};
-    return partition_points_batch(X, n, d, dtype, metric, sqnorm_bytes, bp, off, &seed, 1, out, level0_code);
+    return partition_points_batch(X, n, d, dtype, metric, sqnorm_bytes, bp, off, &seed, 1, out);
 }
 
 }  // namespace pipnn

@@ -14,7 +14,7 @@ int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float 
 bool prune_tc_eligible(int dtype, uint32_t d, uint64_t n, uint32_t l_max);
 int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t *sqn, const uint64_t *res,
                    const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha2, uint32_t *adj, uint32_t *deg,
-                   const uint32_t *order, Workspace &ws);
+                   Workspace &ws);
 
 namespace {
 constexpr int PR_WARPS = 8;
@@ -456,7 +456,7 @@ __global__ void reservoir_to_graph(uint64_t n, const uint64_t *res, const uint32
 
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                 const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, int engine,
-                uint32_t *adj, uint32_t *deg, const uint32_t *order) {
+                uint32_t *adj, uint32_t *deg) {
     if (l_max > PR_MAX) return set_error(PIPNN_EINVAL, "l_max %u exceeds %d", l_max, PR_MAX);
     Workspace ws;
     const int32_t *sqn = sqnorm_bytes;
@@ -469,7 +469,7 @@ int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, co
     const float alpha2 = (float)((double)alpha * (double)alpha);
     if (n == 0) return PIPNN_OK;
     if (engine == PIPNN_LEAF_TC && prune_tc_eligible(dtype, d, n, l_max))
-        return final_prune_tc(X, n, d, dtype, sqn, res, cnt, l_max, R, alpha2, adj, deg, order, ws);
+        return final_prune_tc(X, n, d, dtype, sqn, res, cnt, l_max, R, alpha2, adj, deg, ws);
     const PruneSmem L = prune_smem_layout(dtype, d, l_max);
     const size_t budget = 200 * 1024;
     if (L.per_warp <= budget) {

@@ -67,8 +67,6 @@ struct PtArgs {
     float alpha2, inv_alpha2;
     uint32_t *adj, *deg;
     unsigned *err;
-    const uint32_t *order;  // processing order of the nodes (a permutation of 0..n-1), or null
-    const uint32_t *pos;    // with an order: the BF16 row of point v is row pos[v] (rows staged in order)
 };
 
 // Tile info, info warp -> gathers, MMA, epilogue: row ids (a packed node's rows start at 32q; the
@@ -93,7 +91,7 @@ struct PtCfg {
     static constexpr int W_DX = 0, W_HN = 128, W_ORDER = 256, W_BYTES = 288;
     static constexpr int OFF_WARP = OFF_GROUP + PT_GROUPS * G_BYTES;
     // the info warp's prefetch ring: per node its reservoir row (up to 128 slots), count and norm
-    static constexpr int P = 8;                                       // nodes in flight
+    static constexpr int P = 16;                                      // nodes in flight (<= 32)
     static constexpr int P_KEYS = 0, P_CNT = 1024, P_NRM = 1028, P_BYTES = 1040;
     static constexpr int OFF_PRE = OFF_WARP + PT_EPI_WARPS * W_BYTES;
     static constexpr int OFF_BAR = OFF_PRE + P * P_BYTES;
@@ -204,10 +202,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
         // ------------------------------------------------------------ tile info (one warp)
         // Prefetch: the reservoir row, count and norm of node j + P are copied (cp.async, no
         // registers in flight) into ring slot (j + P) % P while node j is compacted.
-        // node j of this CTA: position blockIdx.x + j * gridDim.x of the processing order
+        // node j of this CTA: blockIdx.x + j * gridDim.x (n past the last)
         auto node_at = [&](uint32_t j) {
-            const uint64_t idx = blockIdx.x + (uint64_t)j * gridDim.x;
-            return idx < n ? (a.order ? (uint64_t)a.order[idx] : idx) : n;
+            const uint64_t v = blockIdx.x + (uint64_t)j * gridDim.x;
+            return v < n ? v : n;
         };
         auto fetch = [&](uint32_t j) {
             const uint64_t v = node_at(j);
@@ -566,59 +564,68 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
         }
     } else {
         // ------------------------------------------------------------ row gathers (two warps)
-        for (uint32_t k = warp - PT_GATHER_WARP0;; k += PT_GATHERERS) {
-            const uint32_t ua = k % C::A, ib = k % C::I;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_CFULL + ib), (k / C::I) & 1, abort, a.err))) break;
+        // Warp g gathers the rows of tiles g, g + 2, ...: lane L rows 4L .. 4L + 3 if any of them
+        // is in use.  A tile's row ids are read one own tile ahead (while the current tile waits
+        // for its A buffer); no tile past an end marker is read (none may exist).
+        struct Rows {
+            uint32_t y[4];
+            bool use;
+            uint32_t kind;
+        };
+        auto prepare = [&](uint32_t k, Rows &t) {
+            const uint32_t ib = k % C::I;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_CFULL + ib), (k / C::I) & 1, abort, a.err)))
+                return false;
             const unsigned char *in = info(ib);
             const uint32_t *ids = reinterpret_cast<const uint32_t *>(in + I_IDS);
             const uint32_t *misc = reinterpret_cast<const uint32_t *>(in + I_MISC);
-            const uint32_t kind = misc[M_KIND];
-            if (kind == TK_END) break;
-            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + ua), ((k / C::A) & 1) ^ 1, abort, a.err)))
-                break;
-            // lane L gathers rows 4L .. 4L + 3 if any of them is in use
-            uint32_t y[4];
-            bool use;
-            if (kind == TK_PACK) {
+            t.kind = misc[M_KIND];
+            t.use = false;
+            if (t.kind == TK_END) return true;
+            if (t.kind == TK_PACK) {
                 const uint32_t q = (uint32_t)lane >> 3;
                 const uint32_t nodes = misc[M_NODES];
                 const uint32_t c = q < nodes ? misc[M_NODE + 3 * q] : 0u;
                 const uint32_t node_row = 32 * q + c;  // the node itself
-                use = q < nodes && 4 * ((uint32_t)lane & 7) <= c;
+                t.use = q < nodes && 4 * ((uint32_t)lane & 7) <= c;
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
                     const uint32_t row = 4 * lane + e;
-                    y[e] = use ? ids[(row & 31) <= c ? row : node_row] : 0u;
-                }
-                if (a.pos && use) {
-#pragma unroll
-                    for (int e = 0; e < 4; e++) y[e] = a.pos[y[e]];
+                    t.y[e] = t.use ? ids[(row & 31) <= c ? row : node_row] : 0u;
                 }
             } else {
                 const uint32_t rows = misc[M_NODE] + 1;
-                use = 4u * lane < rows;
+                t.use = 4u * lane < rows;
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
                     const uint32_t row = 4 * lane + e;
-                    y[e] = use ? ids[row < rows ? row : rows - 1] : 0u;
-                }
-                if (a.pos && use) {
-#pragma unroll
-                    for (int e = 0; e < 4; e++) y[e] = a.pos[y[e]];
+                    t.y[e] = t.use ? ids[row < rows ? row : rows - 1] : 0u;
                 }
             }
-            const unsigned um = __ballot_sync(0xffffffffu, use);
+            return true;
+        };
+        uint32_t k = warp - PT_GATHER_WARP0;
+        Rows cur, nxt;
+        bool live = prepare(k, cur) && (cur.kind == TK_END || prepare(k + PT_GATHERERS, nxt));
+        while (live && cur.kind != TK_END) {
+            const uint32_t ua = k % C::A;
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + ua), ((k / C::A) & 1) ^ 1, abort, a.err)))
+                break;
+            const unsigned um = __ballot_sync(0xffffffffu, cur.use);
             const uint32_t fb = bar(C::BAR_FULL_A + ua);
             if (lane == 0) mbar_arrive_tx(fb, __popc(um) * 512u * KB);
             __syncwarp();
-            if (use) {
+            if (cur.use) {
                 const uint32_t dst = sbase + C::OFF_A0 + ua * KB * REGION + lane * 4 * 128;
 #pragma unroll
                 for (int kb = 0; kb < KB; kb++)
-                    tma_gather4(dst + kb * REGION, &xmap, kb * 64, (int32_t)y[0], (int32_t)y[1], (int32_t)y[2],
-                                (int32_t)y[3], fb);
+                    tma_gather4(dst + kb * REGION, &xmap, kb * 64, (int32_t)cur.y[0], (int32_t)cur.y[1],
+                                (int32_t)cur.y[2], (int32_t)cur.y[3], fb);
             }
             if (lane != 0) mbar_arrive(fb);
+            cur = nxt;
+            k += PT_GATHERERS;
+            if (cur.kind != TK_END) live = prepare(k + PT_GATHERERS, nxt);
         }
     }
 
@@ -653,21 +660,14 @@ bool prune_tc_eligible(int dtype, uint32_t d, uint64_t n, uint32_t l_max) {
 
 int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t *sqn, const uint64_t *res,
                    const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha2, uint32_t *adj, uint32_t *deg,
-                   const uint32_t *order, Workspace &ws) {
+                   Workspace &ws) {
     if (!prune_tc_eligible(dtype, d, n, l_max))
         return set_error(PIPNN_EUNSUPPORTED, "the tensor-core prune takes byte data, d <= 128, l_max <= %u", PT_MAXC);
     if (R < 1 || R > l_max) return set_error(PIPNN_EINVAL, "R outside 1..l_max");
     const uint32_t kp = d <= 64 ? 64 : 128;
     __nv_bfloat16 *rows = nullptr;
     PIPNN_TRY(ws.alloc(&rows, n * kp));
-    // with a processing order the rows are staged in that order, so the rows one stretch of the
-    // order gathers lie together in memory (a few pages, not the whole array): row i is point order[i]
-    uint32_t *pos = nullptr;
-    if (order) {
-        PIPNN_TRY(ws.alloc(&pos, n));
-        PIPNN_TRY(inverse_order(order, n, pos));
-    }
-    PIPNN_TRY(stage_rows_bf16(X, d, kp, dtype, order, n, rows));
+    PIPNN_TRY(stage_rows_bf16(X, d, kp, dtype, nullptr, n, rows));
     CUtensorMap map;
     PIPNN_TRY(encode_rows_map(&map, rows, n, kp, true));
     PtArgs a{};
@@ -682,8 +682,6 @@ int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32
     a.adj = adj;
     a.deg = deg;
     a.err = device_error_word();
-    a.order = order;
-    a.pos = pos;
     if (kp == 64) return launch_pt<1>(map, a);
     return launch_pt<2>(map, a);
 }

@@ -288,7 +288,6 @@ struct AssignTcPlan {
     __nv_bfloat16 *rows = nullptr;
     CUtensorMap map;
     uint32_t kp = 0;
-    uint32_t *pos = nullptr;
 };
 
 // True if a level with fanout F can run on the tensor-core assignment engine: byte data,
@@ -296,12 +295,6 @@ struct AssignTcPlan {
 bool assign_tc_eligible(int dtype, uint32_t d, uint64_t n, uint32_t F);
 
 int assign_tc_plan(const void *X, uint64_t n, uint32_t d, int dtype, Workspace &ws, AssignTcPlan *plan);
-
-// Restages the plan's rows in `order` (a permutation of the points: row i is point order[i]), so
-// that the instances of a deeper subproblem -- points near one another -- gather rows that lie
-// together in memory instead of across the whole array.
-int assign_tc_plan_reorder(const void *X, uint64_t n, uint32_t d, int dtype, const uint32_t *order, Workspace &ws,
-                           AssignTcPlan *plan);
 
 // One level's assignment: for every instance of every subproblem, the min(F, L) nearest of the
 // subproblem's L leaders by (squared distance, rank), written to assign[instance * F + slot], and

@@ -218,74 +218,6 @@ int exclusive_scan_u64_scratch(const uint64_t *in, uint64_t *out, uint64_t n, ui
     return PIPNN_OK;
 }
 
-namespace {
-constexpr uint32_t CODE_BINS = 1024;
-
-// Per block, a shared histogram of its chunk's codes, added once per bin to the global counts.
-__global__ void code_hist(const uint16_t *code, uint64_t n, uint64_t chunk, unsigned long long *hist) {
-    __shared__ unsigned h[CODE_BINS];
-    for (uint32_t b = threadIdx.x; b < CODE_BINS; b += blockDim.x) h[b] = 0;
-    __syncthreads();
-    const uint64_t lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[code[i] & (CODE_BINS - 1)], 1u);
-    __syncthreads();
-    for (uint32_t b = threadIdx.x; b < CODE_BINS; b += blockDim.x)
-        if (h[b]) atomicAdd(&hist[b], (unsigned long long)h[b]);
-}
-
-// The same chunks again: each block reserves one range per bin from the bin cursors, then places
-// its points inside (the order inside a bin is any).
-__global__ void code_place(const uint16_t *code, uint64_t n, uint64_t chunk, unsigned long long *cursor,
-                           uint32_t *order) {
-    __shared__ unsigned h[CODE_BINS];
-    __shared__ unsigned long long base[CODE_BINS];
-    for (uint32_t b = threadIdx.x; b < CODE_BINS; b += blockDim.x) h[b] = 0;
-    __syncthreads();
-    const uint64_t lo = blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[code[i] & (CODE_BINS - 1)], 1u);
-    __syncthreads();
-    for (uint32_t b = threadIdx.x; b < CODE_BINS; b += blockDim.x) {
-        base[b] = h[b] ? atomicAdd(&cursor[b], (unsigned long long)h[b]) : 0ull;
-        h[b] = 0;
-    }
-    __syncthreads();
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const uint32_t b = code[i] & (CODE_BINS - 1);
-        order[base[b] + atomicAdd(&h[b], 1u)] = (uint32_t)i;
-    }
-}
-}  // namespace
-
-namespace {
-__global__ void inverse_order_kernel(const uint32_t *order, uint64_t n, uint32_t *pos) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        pos[order[i]] = (uint32_t)i;
-}
-}  // namespace
-
-int inverse_order(const uint32_t *order, uint64_t n, uint32_t *pos) {
-    if (n == 0) return PIPNN_OK;
-    inverse_order_kernel<<<grid_for(n, 256), 256, 0, stream()>>>(order, n, pos);
-    PIPNN_LAUNCH_CHECK();
-    return PIPNN_OK;
-}
-
-int order_by_code(const uint16_t *code, uint64_t n, uint32_t *order, Workspace &ws) {
-    if (n == 0) return PIPNN_OK;
-    unsigned long long *hist, *tot;
-    PIPNN_TRY(ws.zeros(&hist, CODE_BINS));
-    PIPNN_TRY(ws.alloc(&tot, 1));
-    const uint64_t chunk = 1ull << 16;
-    const uint64_t blocks = (n + chunk - 1) / chunk;
-    code_hist<<<(unsigned)blocks, 512, 0, stream()>>>(code, n, chunk, hist);
-    PIPNN_LAUNCH_CHECK();
-    PIPNN_TRY(exclusive_scan_u64(reinterpret_cast<uint64_t *>(hist), reinterpret_cast<uint64_t *>(hist), CODE_BINS,
-                                 reinterpret_cast<uint64_t *>(tot), ws));
-    code_place<<<(unsigned)blocks, 512, 0, stream()>>>(code, n, chunk, hist, order);
-    PIPNN_LAUNCH_CHECK();
-    return PIPNN_OK;
-}
-
 int make_tiles(const uint32_t *size, uint64_t groups, uint32_t tile, uint32_t **tile_grp,
                uint32_t **tile_row0, uint64_t *num_tiles, Workspace &ws) {
     *num_tiles = 0;
