@@ -452,6 +452,23 @@ def leaf_roofline(stats, d, engine, kernel_file, profile_file):
             "ms_per_build": ms / len(stats), "launches_per_build": launches / len(stats)}
 
 
+def prune_roofline(stats, w, n):
+    """The final prune's kernel (A6) against the measured HBM copy bandwidth: per build, every
+    reservoir slot read (8 B) with its candidate's vector gathered in the stored element type, the
+    node's own vector, count, adjacency row and degree -- over the kernel's launch time."""
+    elem = 4 if w["dtype"] == synth.F32 else 1
+    d, R = w["d"], w["R"]
+    bytes_ = [s["reservoir_slots"] * (8 + d * elem) + n * (d * elem + 4 + R * 4 + 4) for s in stats]
+    ms = sum(s["ms_prune_kernel"] for s in stats)
+    peaks, kind = measured_peaks()
+    achieved = sum(bytes_) / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    return {"kernel": "final RobustPrune (prune_tc_kernel)" if w["dtype"] != synth.F32 else "final RobustPrune",
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{kind} HBM copy", "traffic": None,
+            "algorithmic_bytes_per_build": sum(bytes_) / len(stats), "ms_per_build": ms / len(stats),
+            "reservoir_slots_per_build": sum(s["reservoir_slots"] for s in stats) / len(stats)}
+
+
 def phases(stats):
     return {k: statistics.mean(s[k] for s in stats)
             for k in ("ms_sketch", "ms_partition", "ms_leaf", "ms_hashprune", "ms_prune")}
@@ -475,7 +492,8 @@ def context_block(pk, steps, warmup, engine, n_queries, cpu_sample, recall=True,
     ms = statistics.mean(times)
     out = {"config": config_dict(CONTEXT, w, engine, n), "value": n / (ms / 1e3), "unit": "points/s",
            "ms_per_step": ms, "steps": steps, "phases_ms": phases(stats),
-           "roofline": leaf_roofline(stats, w["d"], engine, "leaf_tc.cu", "leaf_gram_tc_bigann-like-u8.md")}
+           "roofline": leaf_roofline(stats, w["d"], engine, "leaf_tc.cu", "leaf_gram_tc_bigann-like-u8.md"),
+           "roofline_prune": prune_roofline(stats, w, n)}
     if recall:
         adj_g = adj.cpu().numpy().view(np.uint32)
         deg_g = deg.cpu().numpy().view(np.uint32)
@@ -655,7 +673,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": DTYPE_NAME[w["dtype"]], "data": "synthetic",
-                "config": config_dict(args.workload, w, args.engine, n), "roofline": roofline, "e2e": e2e,
+                "config": config_dict(args.workload, w, args.engine, n), "roofline": roofline,
+                "roofline_prune": prune_roofline(stats, w, n), "e2e": e2e,
                 "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks,
                 "phases_ms": phases(stats), "leaves": st["leaves"], "candidates": st["candidates"],
                 "waves_per_build": st["waves"], "peak_device_bytes": st["peak_device_bytes"]}

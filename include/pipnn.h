@@ -177,6 +177,11 @@ typedef struct pipnn_stats {
     uint64_t peak_device_bytes;  /* device memory in use (total minus free, so including memory
                                     the allocators hold in reserve) at the fullest point the
                                     build sampled: after the partition and inside every wave  */
+    float ms_prune_kernel;       /* duration of the final prune's kernel launch (A6, without
+                                    the staging of its operand rows)                           */
+    uint32_t pad2_;
+    uint64_t reservoir_slots;    /* sum over nodes of the final reservoir sizes: the candidates
+                                    the final prune reads                                       */
 } pipnn_stats;
 
 /* Sets the CUDA stream (a cudaStream_t, or NULL for the default stream) used by later calls. */

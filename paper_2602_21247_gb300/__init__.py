@@ -75,7 +75,8 @@ class pipnn_stats(C.Structure):
                 ("leaves", C.c_uint64), ("leaf_members", C.c_uint64), ("candidates", C.c_uint64),
                 ("leaf_pairs", C.c_double), ("leaf_pairs_executed", C.c_double),
                 ("kernel_launches", C.c_uint64), ("leaf_full_rows", C.c_uint64), ("waves", C.c_uint32),
-                ("pad_", C.c_uint32), ("peak_device_bytes", C.c_uint64)]
+                ("pad_", C.c_uint32), ("peak_device_bytes", C.c_uint64), ("ms_prune_kernel", C.c_float),
+                ("pad2_", C.c_uint32), ("reservoir_slots", C.c_uint64)]
 
 
 _lib = None

@@ -24,7 +24,8 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
                     uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt, int padded);
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                 const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, int engine,
-                uint32_t *adj, uint32_t *deg);
+                uint32_t *adj, uint32_t *deg, float *ms_kernel);
+int reservoir_total(const uint32_t *cnt, uint64_t n, uint32_t l_max, uint64_t *total);
 int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, uint32_t *adj,
                     uint32_t *deg);
 int leaf_gram_tcf(const float *X, uint32_t d, int metric, int prec, const uint64_t *off, const uint32_t *mem,
@@ -401,12 +402,13 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
     if (rc == PIPNN_OK) {
         if (bp->final_prune)
             rc = final_prune(X, n, d, dtype, metric, sqn_bytes, res, cnt, bp->l_max, bp->R, bp->alpha, bp->leaf_engine,
-                             adj, deg);
+                             adj, deg, &st.ms_prune_kernel);
         else
             rc = reservoir_graph(n, res, cnt, bp->l_max, bp->R, adj, deg);
     }
     if (rc == PIPNN_OK) rc = check_device_error("final prune");
     tm.mark(5);
+    if (rc == PIPNN_OK) rc = reservoir_total(cnt, n, bp->l_max, &st.reservoir_slots);
     if (rc == PIPNN_OK && graph_on_host == 3) {
         // per index, its rows with index-local ids
         uint32_t i = 0;
@@ -591,7 +593,8 @@ int pipnn_final_prune(const void *points, uint64_t n, uint32_t d, int32_t dtype,
     if (l_max < 1 || l_max > 256 || R < 1 || R > l_max) return set_error(PIPNN_EINVAL, "need 1 <= R <= l_max <= 256");
     if (!(alpha >= 1.0f) || !std::isfinite(alpha)) return set_error(PIPNN_EINVAL, "alpha must be finite and >= 1");
     if (engine != PIPNN_LEAF_SIMT && engine != PIPNN_LEAF_TC) return set_error(PIPNN_EINVAL, "unknown engine %d", engine);
-    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, engine, adj, deg));
+    PIPNN_TRY(final_prune(points, n, d, dtype, metric, nullptr, reservoir, count, l_max, R, alpha, engine, adj, deg,
+                          nullptr));
     return check_device_error("final prune");
 }
 

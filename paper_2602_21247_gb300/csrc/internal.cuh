@@ -118,6 +118,32 @@ class Workspace {
 int dev_alloc_raw(void **p, size_t bytes);   // outside any workspace (library-owned outputs)
 void dev_free_raw(void *p);
 
+// CUDA-event time of the launches issued on the library stream between construction and stop()
+// (nothing is recorded when out is null or the events cannot be made).
+struct LaunchTimer {
+    float *out;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    explicit LaunchTimer(float *o) : out(o) {
+        if (!out) return;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            cudaGetLastError();
+            out = nullptr;
+            return;
+        }
+        cudaEventRecord(e0, stream());
+    }
+    void stop() {
+        if (!out) return;
+        cudaEventRecord(e1, stream());
+        if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(out, e0, e1);
+        else cudaGetLastError();
+    }
+    ~LaunchTimer() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 // ---------------------------------------------------------------------------------------------
 // Small device utilities
 // ---------------------------------------------------------------------------------------------

@@ -14,7 +14,7 @@ int sketch_points(const void *X, uint64_t n, uint32_t d, int dtype, const float 
 bool prune_tc_eligible(int dtype, uint32_t d, uint64_t n, uint32_t l_max);
 int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t *sqn, const uint64_t *res,
                    const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha2, uint32_t *adj, uint32_t *deg,
-                   Workspace &ws);
+                   float *ms_kernel, Workspace &ws);
 
 namespace {
 constexpr int PR_WARPS = 8;
@@ -456,7 +456,7 @@ __global__ void reservoir_to_graph(uint64_t n, const uint64_t *res, const uint32
 
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                 const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, int engine,
-                uint32_t *adj, uint32_t *deg) {
+                uint32_t *adj, uint32_t *deg, float *ms_kernel) {
     if (l_max > PR_MAX) return set_error(PIPNN_EINVAL, "l_max %u exceeds %d", l_max, PR_MAX);
     Workspace ws;
     const int32_t *sqn = sqnorm_bytes;
@@ -469,7 +469,7 @@ int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, co
     const float alpha2 = (float)((double)alpha * (double)alpha);
     if (n == 0) return PIPNN_OK;
     if (engine == PIPNN_LEAF_TC && prune_tc_eligible(dtype, d, n, l_max))
-        return final_prune_tc(X, n, d, dtype, sqn, res, cnt, l_max, R, alpha2, adj, deg, ws);
+        return final_prune_tc(X, n, d, dtype, sqn, res, cnt, l_max, R, alpha2, adj, deg, ms_kernel, ws);
     const PruneSmem L = prune_smem_layout(dtype, d, l_max);
     const size_t budget = 200 * 1024;
     if (L.per_warp <= budget) {
@@ -478,6 +478,7 @@ int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, co
         const size_t smem = wpb * L.per_warp;
         const unsigned grid = grid_for(n, wpb, 152u * 64u);
         unsigned *err = device_error_word();
+        LaunchTimer lt(ms_kernel);
 #define PIPNN_PRS(DT, MET)                                                                                   \
     do {                                                                                                     \
         PIPNN_CUDA(cudaFuncSetAttribute(robust_prune_smem<DT, MET>,                                           \
@@ -491,9 +492,11 @@ int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, co
         else PIPNN_PRS(PIPNN_I8, PIPNN_L2);
 #undef PIPNN_PRS
         PIPNN_LAUNCH_CHECK();
+        lt.stop();
         return PIPNN_OK;
     }
     const unsigned grid = grid_for(n, PR_WARPS, 152u * 16u);
+    LaunchTimer lt(ms_kernel);
 #define PIPNN_PR(DT, MET) \
     robust_prune<DT, MET><<<grid, PR_WARPS * 32, 0, stream()>>>(X, n, d, sqn, res, cnt, l_max, R, alpha2, adj, deg, \
                                                                 device_error_word())
@@ -503,7 +506,29 @@ int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, co
     else PIPNN_PR(PIPNN_I8, PIPNN_L2);
 #undef PIPNN_PR
     PIPNN_LAUNCH_CHECK();
+    lt.stop();
     return PIPNN_OK;
+}
+
+namespace {
+__global__ void sum_counts(const uint32_t *cnt, uint64_t n, uint32_t l_max, unsigned long long *out) {
+    unsigned long long s = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        s += cnt[i] < l_max ? cnt[i] : l_max;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+}  // namespace
+
+int reservoir_total(const uint32_t *cnt, uint64_t n, uint32_t l_max, uint64_t *total) {
+    Workspace ws;
+    unsigned long long *d = nullptr;
+    PIPNN_TRY(ws.zeros(&d, 1));
+    if (n) {
+        sum_counts<<<grid_for(n, 256, 152u * 8u), 256, 0, stream()>>>(cnt, n, l_max, d);
+        PIPNN_LAUNCH_CHECK();
+    }
+    return read_u64(reinterpret_cast<uint64_t *>(d), total);
 }
 
 int reservoir_graph(uint64_t n, const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, uint32_t *adj,

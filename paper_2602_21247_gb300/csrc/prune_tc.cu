@@ -660,7 +660,7 @@ bool prune_tc_eligible(int dtype, uint32_t d, uint64_t n, uint32_t l_max) {
 
 int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t *sqn, const uint64_t *res,
                    const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha2, uint32_t *adj, uint32_t *deg,
-                   Workspace &ws) {
+                   float *ms_kernel, Workspace &ws) {
     if (!prune_tc_eligible(dtype, d, n, l_max))
         return set_error(PIPNN_EUNSUPPORTED, "the tensor-core prune takes byte data, d <= 128, l_max <= %u", PT_MAXC);
     if (R < 1 || R > l_max) return set_error(PIPNN_EINVAL, "R outside 1..l_max");
@@ -682,8 +682,10 @@ int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32
     a.adj = adj;
     a.deg = deg;
     a.err = device_error_word();
-    if (kp == 64) return launch_pt<1>(map, a);
-    return launch_pt<2>(map, a);
+    LaunchTimer lt(ms_kernel);
+    PIPNN_TRY(kp == 64 ? launch_pt<1>(map, a) : launch_pt<2>(map, a));
+    lt.stop();
+    return PIPNN_OK;
 }
 
 }  // namespace pipnn
