@@ -21,7 +21,10 @@
 // ~20), so nodes with at most 31 valid candidates are packed four to a 128-row tile: node q owns
 // rows 32q .. 32q + c_q (its candidates, then itself), i.e. exactly TMEM lane quarter q, and the
 // columns it needs are the same 32.  The 128 x 128 Gram of a packed tile costs the tensor cores
-// little; only its four diagonal 32 x 32 blocks are read.  A larger node gets a tile of its own.
+// little; only its four diagonal 32 x 32 blocks are read.  Nodes with 32 .. 63 candidates (most of
+// them in builds of 100M points, whose reservoirs fill further) go two to a tile: node h owns rows
+// and columns 64h .. 64h + c_h, TMEM lane quarters 2h and 2h + 1, and the group's two warps on
+// those quarters handle it.  A larger node gets a tile of its own.
 //
 // Persistent CTA (one per SM, 16 warps):
 //   warps 0-11   epilogue: three groups of four warps (one per TMEM lane quarter) take turns on
@@ -54,9 +57,10 @@ constexpr int PT_GATHERERS = 2;
 constexpr int PT_THREADS = 16 * 32;
 constexpr uint32_t PT_MAXC = 127;            // candidates per node (+ the node)
 constexpr uint32_t PT_SMALL = 31;            // packed nodes: at most this many valid candidates
+constexpr uint32_t PT_MEDIUM = 63;           // two to a tile: at most this many
 constexpr uint32_t PT_ENDS = PT_GROUPS > PT_GATHERERS ? PT_GROUPS : PT_GATHERERS;  // end markers
 
-enum : uint32_t { TK_PACK = 1, TK_LARGE = 2, TK_END = 3 };
+enum : uint32_t { TK_PACK = 1, TK_LARGE = 2, TK_END = 3, TK_MED = 4 };
 
 struct PtArgs {
     const uint64_t *res;   // n x l_max reservoir slots
@@ -83,10 +87,11 @@ struct PtCfg {
     static constexpr int OFF_A0 = 0;
     static constexpr int OFF_INFO = OFF_A0 + A * KB * REGION;
     static constexpr int OFF_STAGE = OFF_INFO + I * I_BYTES;          // the info warp's packed tile
+    static constexpr int OFF_STAGE2 = OFF_STAGE + I_BYTES;            // and its two-node tile
     // per group (large nodes): column masks 128 x 4 u32, ids 128, order 128 u8, D(x, .) 128,
     // n / 2 128 floats
     static constexpr int G_MASK = 0, G_IDS = 2048, G_ORDER = 2560, G_DX = 2688, G_HN = 3200, G_BYTES = 3712;
-    static constexpr int OFF_GROUP = OFF_STAGE + I_BYTES;
+    static constexpr int OFF_GROUP = OFF_STAGE2 + I_BYTES;
     // per epilogue warp (packed nodes): D(x, .) 32, n / 2 32 floats, order 32 u8
     static constexpr int W_DX = 0, W_HN = 128, W_ORDER = 256, W_BYTES = 288;
     static constexpr int OFF_WARP = OFF_GROUP + PT_GROUPS * G_BYTES;
@@ -223,9 +228,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             }
             cp_async_commit();  // one group per node, empty past the end
         };
-        unsigned char *stage = smem + C::OFF_STAGE;
-        uint32_t *stage_misc = reinterpret_cast<uint32_t *>(stage + I_MISC);
-        uint32_t tile = 0, packed = 0;  // tiles written; nodes in the staged packed tile
+        unsigned char *stage = smem + C::OFF_STAGE, *stage2 = smem + C::OFF_STAGE2;
+        uint32_t tile = 0, packed = 0, paired = 0;  // tiles written; nodes in the two staged tiles
         bool stop = false;
         // the next tile slot; false if the kernel aborted
         auto acquire = [&]() {
@@ -237,20 +241,22 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             mbar_arrive(bar(C::BAR_CFULL + tile % C::I));
             tile++;
         };
-        auto flush_packed = [&]() {
+        auto flush_staged = [&](unsigned char *st, uint32_t kind, uint32_t &count) {
             if (lane == 0) {
-                stage_misc[M_KIND] = TK_PACK;
-                stage_misc[M_NODES] = packed;
+                reinterpret_cast<uint32_t *>(st + I_MISC)[M_KIND] = kind;
+                reinterpret_cast<uint32_t *>(st + I_MISC)[M_NODES] = count;
             }
             __syncwarp();
             if (!acquire()) return false;
-            const uint4 *srcv = reinterpret_cast<const uint4 *>(stage);
+            const uint4 *srcv = reinterpret_cast<const uint4 *>(st);
             uint4 *dstv = reinterpret_cast<uint4 *>(info(tile % C::I));
             for (int q = lane; q < I_BYTES / 16; q += 32) dstv[q] = srcv[q];
             publish();
-            packed = 0;
+            count = 0;
             return true;
         };
+        auto flush_packed = [&]() { return flush_staged(stage, TK_PACK, packed); };
+        auto flush_paired = [&]() { return flush_staged(stage2, TK_MED, paired); };
         for (uint32_t j = 0; j < (uint32_t)C::P; j++) fetch(j);
         for (uint32_t j = 0; !stop; j++) {
             const uint64_t v = node_at(j);
@@ -289,6 +295,9 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             if (cc <= PT_SMALL) {
                 dst = stage;
                 row0 = 32 * packed;
+            } else if (cc <= PT_MEDIUM) {
+                dst = stage2;
+                row0 = 64 * paired;
             } else {
                 // a large node: its own tile, written straight into the ring
                 if (!acquire()) {
@@ -310,11 +319,11 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             }
             if (lane == 0) {
                 ids[row0 + cc] = (uint32_t)v;
-                const uint32_t q = cc <= PT_SMALL ? packed : 0;
+                const uint32_t q = cc <= PT_SMALL ? packed : cc <= PT_MEDIUM ? paired : 0;
                 misc[M_NODE + 3 * q + 0] = cc;
                 misc[M_NODE + 3 * q + 1] = (uint32_t)v;
                 misc[M_NODE + 3 * q + 2] = (uint32_t)pnv;
-                if (cc > PT_SMALL) {
+                if (cc > PT_MEDIUM) {
                     misc[M_KIND] = TK_LARGE;
                     misc[M_NODES] = 1;
                 }
@@ -322,12 +331,16 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             if (cc <= PT_SMALL) {
                 __syncwarp();
                 if (++packed == 4 && !flush_packed()) stop = true;
+            } else if (cc <= PT_MEDIUM) {
+                __syncwarp();
+                if (++paired == 2 && !flush_paired()) stop = true;
             } else {
                 publish();
             }
         }
         cp_async_wait<0>();  // no copy outlives the warp's loop
         if (!stop && packed > 0 && !flush_packed()) stop = true;
+        if (!stop && paired > 0 && !flush_paired()) stop = true;
         // one end marker for every consumer that walks the tiles in a stride
         for (uint32_t e = 0; e < PT_ENDS && !stop; e++) {
             if (!acquire()) break;
@@ -354,7 +367,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                     break;
                 }
                 fence_after();
-                const uint32_t ncol = kind == TK_PACK ? 128u : ((misc[M_NODE] + 1 + 15) & ~15u);
+                const uint32_t ncol = kind != TK_LARGE ? 128u : ((misc[M_NODE] + 1 + 15) & ~15u);
                 const uint32_t idesc = idesc_bf16(128, ncol);
                 const uint32_t aB = sbase + C::OFF_A0 + ua * KB * REGION;
                 const uint32_t d = tmem + tb * 128;
@@ -455,6 +468,118 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 fence_before();
                 mbar_arrive(bar(C::BAR_TEMPTY + tb));
                 mbar_arrive(bar(C::BAR_IEMPTY + ib));
+                continue;
+            }
+
+            if (kind == TK_MED) {
+                // ---- two nodes: node h by the warps on lane quarters 2h and 2h + 1, rows and
+                // columns 64h .. 64h + c_h; the pair meets at its own named barrier
+                uint32_t *gmask = reinterpret_cast<uint32_t *>(gs + C::G_MASK);
+                uint32_t *gids = reinterpret_cast<uint32_t *>(gs + C::G_IDS);
+                unsigned char *gorder = gs + C::G_ORDER;
+                uint32_t *dx = reinterpret_cast<uint32_t *>(gs + C::G_DX);
+                float *hn = reinterpret_cast<float *>(gs + C::G_HN);
+                const uint32_t h = (uint32_t)quarter >> 1;
+                const uint32_t base = 64 * h, lr = r - base;
+                const uint32_t pair_id = 1 + PT_GROUPS + 2 * grp + h;
+                const bool mine = h < misc[M_NODES];
+                uint32_t c = 0;
+                uint64_t v = 0;
+                if (mine) {
+                    c = misc[M_NODE + 3 * h + 0];
+                    v = misc[M_NODE + 3 * h + 1];
+                    const float nx = (float)(int32_t)misc[M_NODE + 3 * h + 2];
+                    uint32_t DX = 0;
+                    float theta = 0.0f;
+                    bool bad = false;
+                    {
+                        uint32_t g[32];
+                        tmem_ld32(trow + quarter * 32, g);
+                        const float nr = __uint_as_float(pick32(g, lane));  // diagonal: exact integer
+                        hn[r] = 0.5f * nr;
+                        const uint32_t xc = base + c;  // the node's column
+                        tmem_ld32(trow + (xc & ~31u), g);
+                        if (lr < c) {
+                            const float gx = __uint_as_float(pick32(g, xc & 31u));
+                            const float dxf = __fmaf_rn(-2.0f, gx, nr + nx);
+                            DX = (uint32_t)dxf;
+                            const uint32_t T = removal_threshold(DX, a.alpha2, a.inv_alpha2);
+                            theta = (nr - (float)T) * 0.5f;
+                            dx[r] = DX;
+                            bad = bf16_key(dxf) != bkey[r] || (lr > 0 && bkey[r - 1] > bkey[r]);
+                        }
+                    }
+                    const bool full = named_barrier_or(pair_id, 64, bad);
+                    if (lr < c) {
+                        gorder[base + candidate_rank(lr, c, DX, ids[r], dx + base, ids + base, bkey + base, full)] =
+                            (unsigned char)lr;
+                        gids[r] = ids[r];
+                    }
+                    uint32_t mw[2] = {0u, 0u};
+#pragma unroll
+                    for (uint32_t qq = 0; qq < 2; qq++) {
+                        if (qq * 32 < c) {
+                            uint32_t g[32];
+                            tmem_ld32(trow + (2 * h + qq) * 32, g);
+                            const float4 *h4 = reinterpret_cast<const float4 *>(hn + base + qq * 32);
+                            uint32_t m = 0;
+#pragma unroll
+                            for (int j4 = 0; j4 < 8; j4++) {
+                                const float4 hv = h4[j4];
+                                m |= __fsub_rn(__uint_as_float(g[4 * j4 + 0]), hv.x) > theta ? (1u << (4 * j4 + 0)) : 0u;
+                                m |= __fsub_rn(__uint_as_float(g[4 * j4 + 1]), hv.y) > theta ? (1u << (4 * j4 + 1)) : 0u;
+                                m |= __fsub_rn(__uint_as_float(g[4 * j4 + 2]), hv.z) > theta ? (1u << (4 * j4 + 2)) : 0u;
+                                m |= __fsub_rn(__uint_as_float(g[4 * j4 + 3]), hv.w) > theta ? (1u << (4 * j4 + 3)) : 0u;
+                            }
+                            const uint32_t live = c - qq * 32;
+                            if (live < 32) m &= (1u << live) - 1u;
+                            if (lr / 32 == qq) m &= ~(1u << (lr & 31));
+                            mw[qq] = m;
+                        }
+                    }
+                    if (lr < c) reinterpret_cast<uint2 *>(gmask)[r] = make_uint2(mw[0], mw[1]);
+                }
+                fence_before();
+                mbar_arrive(bar(C::BAR_TEMPTY + tb));
+                mbar_arrive(bar(C::BAR_IEMPTY + ib));
+                if (mine) {
+                    named_barrier_or(pair_id, 64, false);  // masks, order and ids of the pair complete
+                    if ((uint32_t)quarter == 2 * h) {
+                        // the walk, as for a large node, over at most 63 ranks
+                        const uint2 *mask = reinterpret_cast<const uint2 *>(gmask) + base;
+                        uint32_t A0 = 0, A1 = 0, e = 0;
+                        uint32_t out[2] = {0xFFFFFFFFu, 0xFFFFFFFFu};
+                        for (uint32_t b = 0; b * 32 < c && e < R; b++) {
+                            const uint32_t i = b * 32 + lane;
+                            const bool valid = i < c;
+                            const uint32_t tl = valid ? gorder[base + i] : 0u;
+                            const uint2 cm = valid ? mask[tl] : make_uint2(0, 0);
+                            unsigned U = __ballot_sync(0xffffffffu, valid && ((cm.x & A0) | (cm.y & A1)) == 0u);
+                            while (U != 0u && e < R) {
+                                const uint32_t u = __ffs(U) - 1;
+                                const uint32_t t = __shfl_sync(0xffffffffu, tl, u);
+                                const uint32_t wd = t >> 5, bit = 1u << (t & 31);
+                                A0 |= wd == 0 ? bit : 0u;
+                                A1 |= wd == 1 ? bit : 0u;
+                                const uint32_t id = gids[base + t];
+                                const uint32_t o = e >> 5;
+                                const bool slot = (e & 31) == (uint32_t)lane;
+                                out[0] = (slot && o == 0) ? id : out[0];
+                                out[1] = (slot && o == 1) ? id : out[1];
+                                e++;
+                                const uint32_t mwd = wd == 0 ? cm.x : cm.y;
+                                U &= ~__ballot_sync(0xffffffffu, (mwd >> (t & 31)) & 1u) & ~(1u << u);
+                            }
+                        }
+                        for (uint32_t p = lane; p < R; p += 32) {
+                            const uint32_t o = p >> 5;
+                            a.adj[v * R + p] = p < e ? (o == 0 ? out[0] : o == 1 ? out[1] : 0xFFFFFFFFu) : 0xFFFFFFFFu;
+                        }
+                        if (lane == 0) a.deg[v] = e;
+                    }
+                }
+                // the group's arrays are rewritten by its next tile only after this barrier
+                if (named_barrier_or(bar_id, 128, *abort != 0)) break;
                 continue;
             }
 
@@ -592,6 +717,17 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 for (int e = 0; e < 4; e++) {
                     const uint32_t row = 4 * lane + e;
                     t.y[e] = t.use ? ids[(row & 31) <= c ? row : node_row] : 0u;
+                }
+            } else if (t.kind == TK_MED) {
+                const uint32_t h = (uint32_t)lane >> 4;
+                const uint32_t nodes = misc[M_NODES];
+                const uint32_t c = h < nodes ? misc[M_NODE + 3 * h] : 0u;
+                const uint32_t node_row = 64 * h + c;  // the node itself
+                t.use = h < nodes && 4 * ((uint32_t)lane & 15) <= c;
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const uint32_t row = 4 * lane + e;
+                    t.y[e] = t.use ? ids[(row & 63) <= c ? row : node_row] : 0u;
                 }
             } else {
                 const uint32_t rows = misc[M_NODE] + 1;

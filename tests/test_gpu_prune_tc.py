@@ -100,3 +100,23 @@ def test_tc_prune_small_counts_clipping_and_huge_alpha():
     cnt[full] = 1000  # above l_max (only where the reservoir is full): clipped to l_max
     check(X, res, cnt, 24, 1.2)
     check(X, res, cnt, 48, 1e18)
+
+
+@pytest.mark.parametrize("n", [4001, 4002])
+def test_tc_prune_every_tile_kind(n):
+    """Reservoirs filled from 400 random candidates per node and cut to sizes spread over
+    0 .. l_max, so that nodes go four to a tile (up to 31 candidates), two to a tile (32 .. 63) and
+    alone (64 and more), in every interleaving, with a lone node left over in the last two-node
+    tile when their number is odd."""
+    X = synth.mixture(n, 128, synth.U8, 8, 10.0, seed=78)
+    rng = np.random.default_rng(n)
+    dst = np.repeat(np.arange(n, dtype=np.uint32), 400)
+    src = rng.integers(0, n, size=dst.size).astype(np.uint32)
+    Xi = X.astype(np.int64)
+    dist = ((Xi[dst] - Xi[src]) ** 2).sum(1).astype(np.float32)
+    S, _ = oracle.sketch(X, synth.hyperplanes(12, X.shape[1], seed=8))
+    res, cnt = oracle.hashprune_closed(dst, src, dist, S, n, 96)
+    cnt = np.minimum(cnt, rng.integers(0, 97, size=n)).astype(cnt.dtype)
+    assert ((cnt >= 32) & (cnt <= 63)).sum() > 500 and (cnt >= 64).sum() > 500 and (cnt <= 31).sum() > 500
+    for R, alpha in ((64, 1.2), (20, 1.0), (96, 1.5)):
+        check(X, res, cnt, R, alpha)
