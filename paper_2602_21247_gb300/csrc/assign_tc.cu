@@ -572,7 +572,10 @@ int launch_as(const CUtensorMap &xmap, const CUtensorMap &lmap, const AsArgs &ar
 
 template <int KB>
 int launch_as_k(const CUtensorMap &xmap, const CUtensorMap &lmap, const AsArgs &args, uint64_t nunits, uint32_t F) {
-    if (F <= 2) return launch_as<KB, 2>(xmap, lmap, args, nunits);
+    // the smallest list that holds F: each column costs 2 KMAX - 1 min / max operations
+    if (F == 1) return launch_as<KB, 1>(xmap, lmap, args, nunits);
+    if (F == 2) return launch_as<KB, 2>(xmap, lmap, args, nunits);
+    if (F == 3) return launch_as<KB, 3>(xmap, lmap, args, nunits);
     if (F <= 4) return launch_as<KB, 4>(xmap, lmap, args, nunits);
     if (F <= 8) return launch_as<KB, 8>(xmap, lmap, args, nunits);
     return launch_as<KB, 16>(xmap, lmap, args, nunits);
