@@ -24,6 +24,8 @@
 // Waits are bounded like the leaf engine's (DERR_TIMEOUT, TMEM still released).
 #include "tc_common.cuh"
 
+#include <type_traits>
+
 namespace pipnn {
 
 namespace {
@@ -400,25 +402,36 @@ __global__ void __launch_bounds__(THREADS, 1)
                     uint32_t g[2][32];
                     const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + tb * C::NMAX;
                     const bool two = (half + 2) * 32 < nc;
+                    // the second chunk loads while the first is ranked
                     if (half * 32 < nc) tmem_ld32_async(tbase + half * 32, g[0]);
-                    if (two) tmem_ld32_async(tbase + (half + 2) * 32, g[1]);
                     tmem_wait_ld();
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        const uint32_t q = half + 2 * h;
-                        if (q * 32 >= nc) break;
+                    if (two) tmem_ld32_async(tbase + (half + 2) * 32, g[1]);
+                    auto rank = [&](uint32_t (&gc)[32], uint32_t q, auto full_tag) {
+                        constexpr bool FULL = decltype(full_tag)::value;
                         const uint32_t live = nc - q * 32;
 #pragma unroll
                         for (int jj = 0; jj < 32; jj += 2) {
-                            uint32_t k0 = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(g[h][jj]), nb23)) * 128u +
+                            uint32_t k0 = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(gc[jj]), nb23)) * 128u +
                                           (q * 32 + jj);
-                            uint32_t k1 = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(g[h][jj + 1]), nb23)) *
+                            uint32_t k1 = __float_as_uint(__fmaf_rn(-2.0f, __uint_as_float(gc[jj + 1]), nb23)) *
                                               128u + (q * 32 + jj + 1);
-                            k0 = (uint32_t)jj < live ? k0 : ~0u;
-                            k1 = (uint32_t)jj + 1 < live ? k1 : ~0u;
+                            if (!FULL) {
+                                k0 = (uint32_t)jj < live ? k0 : ~0u;
+                                k1 = (uint32_t)jj + 1 < live ? k1 : ~0u;
+                            }
                             key_insert<KMAX>(L0, k0);
                             key_insert<KMAX>(L1, k1);
                         }
+                    };
+                    // columns past the tile's leaders are masked only in a ragged last chunk
+                    if (half * 32 < nc) {
+                        if (nc - half * 32 >= 32) rank(g[0], half, std::true_type());
+                        else rank(g[0], half, std::false_type());
+                    }
+                    if (two) {
+                        tmem_wait_ld_regs(g[1]);
+                        if (nc - (half + 2) * 32 >= 32) rank(g[1], half + 2, std::true_type());
+                        else rank(g[1], half + 2, std::false_type());
                     }
 #pragma unroll
                     for (int p = 0; p < KMAX; p++) key_insert<KMAX>(L0, L1[p]);
