@@ -177,10 +177,22 @@ uint64_t auto_wave_members(uint64_t n, uint32_t d, int dtype, const pipnn_params
             fr += (size_t)(reserved - used);
     }
     cudaGetLastError();
+    // Device bytes a wave holds per leaf member: in the leaf step, the engine's staged operand row
+    // and per-member buffers plus the 2k candidate edges it writes (12 B each); in HashPrune, the
+    // edges and their 8-byte grouped slots.  The two steps do not overlap; the per-node arrays of
+    // HashPrune (12 B per node) are part of the fixed reserve.
     const uint64_t kp = ((uint64_t)d + 63) / 64 * 64;
-    const uint64_t per_member = kp * 2 + 64 + (uint64_t)bp->leaf_k * 2 * (12 + 8) * 2;
+    const uint64_t k2 = 2ull * bp->leaf_k;
+    uint64_t stage = 32;  // CUDA-core engines read the rows in place
+    if (bp->leaf_engine == PIPNN_LEAF_TC) {
+        if (dtype != PIPNN_F32) stage = kp * 2 + 12;
+        else if (bp->prec == PIPNN_PREC_BF16X3) stage = kp * 4 + 96;
+        else if (bp->prec == PIPNN_PREC_FP8) stage = 128 * ((kp + 127) / 128) + 96;
+        else stage = kp * 2 + 96;
+    }
+    const uint64_t leaf_step = stage + k2 * 12, hp_step = k2 * (12 + 8);
+    const uint64_t per_member = (leaf_step > hp_step ? leaf_step : hp_step) + 32;
     const uint64_t reserve = (2ull << 30) + 24 * n;
-    (void)dtype;
     uint64_t w = fr > reserve ? (fr - reserve) / per_member : (1ull << 20);
     if (w < (1ull << 20)) w = 1ull << 20;
     if (w > 0x7FF00000ull) w = 0x7FF00000ull;
