@@ -71,6 +71,7 @@ struct PtArgs {
     float alpha2, inv_alpha2;
     uint32_t *adj, *deg;
     unsigned *err;
+    uint32_t medium;  // largest candidate count that goes two to a tile (PT_SMALL: none do)
 };
 
 // Tile info, info warp -> gathers, MMA, epilogue: row ids (a packed node's rows start at 32q; the
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             if (cc <= PT_SMALL) {
                 dst = stage;
                 row0 = 32 * packed;
-            } else if (cc <= PT_MEDIUM) {
+            } else if (cc <= a.medium) {
                 dst = stage2;
                 row0 = 64 * paired;
             } else {
@@ -319,11 +320,11 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             }
             if (lane == 0) {
                 ids[row0 + cc] = (uint32_t)v;
-                const uint32_t q = cc <= PT_SMALL ? packed : cc <= PT_MEDIUM ? paired : 0;
+                const uint32_t q = cc <= PT_SMALL ? packed : cc <= a.medium ? paired : 0;
                 misc[M_NODE + 3 * q + 0] = cc;
                 misc[M_NODE + 3 * q + 1] = (uint32_t)v;
                 misc[M_NODE + 3 * q + 2] = (uint32_t)pnv;
-                if (cc > PT_MEDIUM) {
+                if (cc > a.medium) {
                     misc[M_KIND] = TK_LARGE;
                     misc[M_NODES] = 1;
                 }
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
             if (cc <= PT_SMALL) {
                 __syncwarp();
                 if (++packed == 4 && !flush_packed()) stop = true;
-            } else if (cc <= PT_MEDIUM) {
+            } else if (cc <= a.medium) {
                 __syncwarp();
                 if (++paired == 2 && !flush_paired()) stop = true;
             } else {
@@ -794,6 +795,8 @@ bool prune_tc_eligible(int dtype, uint32_t d, uint64_t n, uint32_t l_max) {
            l_max >= 1 && l_max <= PT_MAXC;
 }
 
+int reservoir_total(const uint32_t *cnt, uint64_t n, uint32_t l_max, uint64_t *total);
+
 int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32_t *sqn, const uint64_t *res,
                    const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha2, uint32_t *adj, uint32_t *deg,
                    float *ms_kernel, Workspace &ws) {
@@ -818,6 +821,12 @@ int final_prune_tc(const void *X, uint64_t n, uint32_t d, int dtype, const int32
     a.adj = adj;
     a.deg = deg;
     a.err = device_error_word();
+    // Two-node tiles pay off where reservoirs are full (average above 32 slots, as in builds of
+    // 100M points: 1.68 -> 1.11 s) and cost a little where most are small (1M points, average 21:
+    // 5.4 -> 6.1 ms), so they are used by that average.
+    uint64_t slots = 0;
+    PIPNN_TRY(reservoir_total(cnt, n, l_max, &slots));
+    a.medium = slots > 32 * n ? PT_MEDIUM : PT_SMALL;
     LaunchTimer lt(ms_kernel);
     PIPNN_TRY(kp == 64 ? launch_pt<1>(map, a) : launch_pt<2>(map, a));
     lt.stop();
