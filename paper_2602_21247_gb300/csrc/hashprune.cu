@@ -287,18 +287,23 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
             const uint32_t nn = (uint32_t)(b - a);
             uint64_t nk[1] = {(uint32_t)lane < nn ? slots[a + lane] : ~0ull};
             warp_sort_regs<1>(nk, lane);
-            // the old reservoir, in the upper half of the buffer for the new slots' rank search
+            // the old reservoir and the sorted new slots, in the upper half of the buffer, for the
+            // two rank searches (cur + nn <= HP_BUF / 2)
             uint64_t *old = buf + HP_BUF / 2;
+            uint64_t *fresh = old + cur;
             for (uint32_t t = lane; t < cur; t += 32) old[t] = res[v * l_max + t];
+            if ((uint32_t)lane < nn) fresh[lane] = nk[0];
             __syncwarp();
-            // each old slot's position: its index plus the new slots strictly below it (the loop
-            // is warp-uniform: every lane takes part in every shuffle)
-            for (uint32_t base = 0; base < cur; base += 32) {
-                const uint32_t t = base + lane;
-                const uint64_t x = t < cur ? old[t] : ~0ull;
-                uint32_t below = 0;
-                for (uint32_t q = 0; q < nn; q++) below += __shfl_sync(0xffffffffu, nk[0], q) < x ? 1u : 0u;
-                if (t < cur) buf[t + below] = x;
+            // each old slot's position: its index plus the new slots strictly below it (binary search)
+            for (uint32_t t = lane; t < cur; t += 32) {
+                const uint64_t x = old[t];
+                uint32_t lo = 0, hi = nn;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (fresh[mid] < x) lo = mid + 1;
+                    else hi = mid;
+                }
+                buf[t + lo] = x;
             }
             // each new slot's position: its rank plus the old slots at or below it (binary search)
             if ((uint32_t)lane < nn) {
