@@ -593,6 +593,8 @@ def main():
                     help="skip the float workload built at every leaf precision")
     ap.add_argument("--queries", type=int, default=None, help="queries of the recall measurement")
     ap.add_argument("--profile", action="store_true", help="timed steps only (for profiler launch lists)")
+    ap.add_argument("--profile-knn", action="store_true",
+                    help="with --profile: also one k-NN graph construction on the built graph (byte data)")
     args = ap.parse_args()
     w = dict(synth.WORKLOADS[args.workload])
     if args.impl == "reference":
@@ -639,10 +641,19 @@ def main():
     if args.profile:
         if rank == 0:
             st = stats[-1]
-            print(json.dumps({"profile_run": True, "ms_per_step": ms, "phases_ms": phases(stats),
-                              "leaf_pairs": st["leaf_pairs"], "leaf_members": st["leaf_members"],
-                              "leaves": st["leaves"], "candidates": st["candidates"],
-                              "waves": st["waves"]}), flush=True)
+            out = {"profile_run": True, "ms_per_step": ms, "phases_ms": phases(stats),
+                   "leaf_pairs": st["leaf_pairs"], "leaf_members": st["leaf_members"],
+                   "leaves": st["leaves"], "candidates": st["candidates"], "waves": st["waves"]}
+            if args.profile_knn and w["dtype"] != synth.F32:
+                # one k-NN graph construction (Sec. 5) on the built graph, L = 32, k = 10
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                _, nd = pk.pipnn_knn_graph(Xd, adj.view(torch.uint32), deg.view(torch.uint32), 32, k=10)
+                e1.record()
+                torch.cuda.synchronize()
+                out["knn_graph_ms"] = e0.elapsed_time(e1)
+                out["knn_evaluations_per_point"] = nd / n
+            print(json.dumps(out), flush=True)
         return 0
 
     # end to end through the public call: pinned host input, host output, copies inside the region
