@@ -70,7 +70,8 @@ def measured_peaks():
 
 
 def profiled_traffic(kernel_file, profile_file):
-    """DRAM bytes per launch recorded by an ncu capture, if that capture is of the current source."""
+    """DRAM bytes per build of a kernel recorded by an ncu capture (scaled to the bench's build),
+    if that capture is of the current source."""
     src = os.path.join(ROOT, "paper_2602_21247_gb300", "csrc", kernel_file)
     prof = os.path.join(ROOT, "profiles", profile_file)
     if not (os.path.exists(src) and os.path.exists(prof)):
@@ -78,7 +79,7 @@ def profiled_traffic(kernel_file, profile_file):
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     text = open(prof).read()
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    m_b = re.search(r"dram_bytes_per_build:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_b or m_sha.group(1) != sha:
         return None
     return float(m_b.group(1))
@@ -445,7 +446,9 @@ def leaf_roofline(stats, d, engine, kernel_file, profile_file):
     # the kernel runs for milliseconds to a second inside a build: the burst peak applies
     peak = peaks["bf16_tflops"]
     achieved = flops / (ms / 1e3) / 1e12
-    traffic = profiled_traffic(kernel_file, profile_file) if engine == "tc" else None
+    per_build = profiled_traffic(kernel_file, profile_file) if engine == "tc" else None
+    # DRAM bytes of the kernel per launch (a build launches it once per wave)
+    traffic = per_build / (launches / len(stats)) if per_build else None
     return {"kernel": "leaf all-pairs Gram + k-NN pick (" + engine + ")", "bound": "tensor", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": f"{peak_kind} bf16 burst",
             "traffic": traffic, "algorithmic_flops_per_build": flops / len(stats),
