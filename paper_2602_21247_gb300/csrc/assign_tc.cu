@@ -32,6 +32,10 @@ namespace {
 
 using namespace tc;
 
+// warps: 0 producer (B tiles), 1 MMA, 2 .. 9 epilogue, 10 .. 11 A-row gathers (one per A buffer:
+// a warp issues TMA gathers at a bounded rate, so two issuing warps double the rows in flight)
+constexpr int AS_GATHER_WARP0 = EPI_WARP0 + EPI_WARPS;
+constexpr int AS_THREADS = (AS_GATHER_WARP0 + 2) * 32;
 constexpr uint32_t AS_HIST = 1024;            // leaders per subproblem (max_leaders is at most 1024)
 constexpr uint32_t AS_SENT = 0xFFFFFFFEu;     // padding entry in front of the F live ones
 constexpr uint32_t AS_NONE = 0xFFFFFFFFu;     // live entry not filled yet
@@ -138,7 +142,7 @@ __device__ __forceinline__ void insert_lex(float (&kv)[KMAX], uint32_t (&ki)[KMA
 // B job j uses B stage j % S (phase (j / S) % 2) and accumulator buffer j % T (phase (j / T) % 2);
 // unit i uses A buffer i % 2 (phase (i / 2) % 2).
 template <int KB, int KMAX>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(AS_THREADS, 1)
     assign_tc_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap lmap,
                      const AsArgs a, uint32_t nunits) {
     using C = AsCfg<KB, KMAX>;
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (uint32_t i = threadIdx.x; i < AS_HIST; i += THREADS) hist[i] = 0;
+    for (uint32_t i = threadIdx.x; i < AS_HIST; i += AS_THREADS) hist[i] = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; i++) {
             mbar_init(bar(C::BAR_FULL_A + i), 1);
@@ -191,26 +195,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                          : "memory");
         }
         fence_proxy_async();
-        // Per unit i of this CTA (u = blockIdx.x + i gridDim.x): one A job (the gather of its
-        // instance rows), then one B job per 128 leaders.  The loads a job depends on are requested
-        // ahead, so the producer never waits on a chain of its own loads: unit descriptors two
-        // units ahead, instance ids (the rows of the copy) one unit ahead, and the leader norms of
-        // the next B job (of this unit or the next) during the current one.
+        // Per unit i of this CTA (u = blockIdx.x + i gridDim.x): one B job per 128 leaders (the A
+        // rows are the gather warps').  The leader norms of the next B job (of this unit or the
+        // next) are requested during the current one, unit descriptors a unit ahead.
         const uint32_t G = gridDim.x;
         auto desc = [&](uint32_t i) {
             const uint64_t u = blockIdx.x + (uint64_t)i * G;
             AsUnit x{};  // nrows = 0: past the last unit
             if (u < nunits) x = a.units[u];
             return x;
-        };
-        auto inst_ids = [&](const AsUnit &un, uint32_t (&v)[4]) {
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                // rows past the subproblem repeat its last instance; their results are unused
-                uint32_t r = un.row0 + 4 * lane + e;
-                r = r < un.nrows ? r : un.nrows - 1;
-                v[e] = un.nrows ? a.inst[un.inst0 + r] : 0u;
-            }
         };
         auto lead_norms = [&](const AsUnit &un, uint32_t t, uint32_t (&v)[4]) {
 #pragma unroll
@@ -219,32 +212,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                 v[e] = (un.nrows && c < un.ncols) ? (uint32_t)a.lead_norm[un.lead0 + c] : 0u;
             }
         };
-        AsUnit d0 = desc(0), d1 = desc(1), d2 = desc(2);
-        uint32_t rows0[4], rows1[4], nrm[4];
-        inst_ids(d0, rows0);
-        inst_ids(d1, rows1);
+        AsUnit d0 = desc(0), d1 = desc(1);
+        uint32_t nrm[4];
         lead_norms(d0, 0, nrm);
         uint32_t j = 0;
         bool ok = true;
         for (uint32_t i = 0; ok && blockIdx.x + (uint64_t)i * G < nunits; i++) {
-            // A job: lane L fetches tile rows 4L..4L+3 of every K block
-            const uint32_t ua = i & 1;
-            ok = __all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + ua), ((i >> 1) & 1) ^ 1, abort, a.err));
-            if (!ok) break;
-            {
-                const uint32_t fb = bar(C::BAR_FULL_A + ua);
-                if (lane == 0) mbar_arrive_tx(fb, KB * REGION);
-                __syncwarp();
-                const uint32_t dst = sbase + C::OFF_A0 + ua * KB * REGION + lane * 4 * 128;
-#pragma unroll
-                for (int kb = 0; kb < KB; kb++)
-                    tma_gather4(dst + kb * REGION, &xmap, kb * 64, (int32_t)rows0[0], (int32_t)rows0[1],
-                                (int32_t)rows0[2], (int32_t)rows0[3], fb);
-            }
-            uint32_t rows2[4];
-            const AsUnit d3 = desc(i + 3);
-            inst_ids(d2, rows2);
-            // B jobs
+            const AsUnit d2 = desc(i + 2);
             const uint32_t nct = (d0.ncols + C::NMAX - 1) / C::NMAX;
             for (uint32_t t = 0; t < nct; t++, j++) {
                 uint32_t nn[4];
@@ -281,12 +255,6 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             d0 = d1;
             d1 = d2;
-            d2 = d3;
-#pragma unroll
-            for (int e = 0; e < 4; e++) {
-                rows0[e] = rows1[e];
-                rows1[e] = rows2[e];
-            }
         }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
@@ -336,7 +304,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 mbar_wait(bar(C::BAR_TFULL + issued_j % C::T), (issued_j / C::T) & 1, abort, a.err);
         }
         __syncwarp();
-    } else {
+    } else if (warp < AS_GATHER_WARP0) {
         // ------------------------------------------------------------ epilogue
         const int ew = warp - EPI_WARP0;             // 0..7
         const int half = ew >> 2;                    // which column chunks
@@ -533,6 +501,52 @@ __global__ void __launch_bounds__(THREADS, 1)
             un1 = un2;
             nrm = nrm1;
         }
+    } else {
+        // ------------------------------------------------------------ A-row gathers (two warps)
+        // Gather warp g fills A buffer g with the instance rows of units g, g + 2, ...: lane L
+        // fetches tile rows 4L .. 4L + 3 of every K block.  Its unit descriptors are requested
+        // two own units ahead and the instance ids one own unit ahead.
+        const uint32_t g = (uint32_t)(warp - AS_GATHER_WARP0);
+        const uint32_t G = gridDim.x;
+        auto desc = [&](uint32_t i) {
+            const uint64_t u = blockIdx.x + (uint64_t)i * G;
+            AsUnit x{};  // nrows = 0: past the last unit
+            if (u < nunits) x = a.units[u];
+            return x;
+        };
+        auto inst_ids = [&](const AsUnit &un, uint32_t (&v)[4]) {
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                // rows past the subproblem repeat its last instance; their results are unused
+                uint32_t r = un.row0 + 4 * lane + e;
+                r = r < un.nrows ? r : un.nrows - 1;
+                v[e] = un.nrows ? a.inst[un.inst0 + r] : 0u;
+            }
+        };
+        AsUnit e1 = desc(g + 2), e2 = desc(g + 4);
+        uint32_t rows0[4], rows1[4];
+        inst_ids(desc(g), rows0);
+        inst_ids(e1, rows1);
+        for (uint32_t i = g; blockIdx.x + (uint64_t)i * G < nunits; i += 2) {
+            if (!__all_sync(0xffffffffu, mbar_wait(bar(C::BAR_EMPTY_A + g), ((i >> 1) & 1) ^ 1, abort, a.err))) break;
+            const uint32_t fb = bar(C::BAR_FULL_A + g);
+            if (lane == 0) mbar_arrive_tx(fb, KB * REGION);
+            __syncwarp();
+            const uint32_t dst = sbase + C::OFF_A0 + g * KB * REGION + lane * 4 * 128;
+#pragma unroll
+            for (int kb = 0; kb < KB; kb++)
+                tma_gather4(dst + kb * REGION, &xmap, kb * 64, (int32_t)rows0[0], (int32_t)rows0[1],
+                            (int32_t)rows0[2], (int32_t)rows0[3], fb);
+            uint32_t rows2[4];
+            inst_ids(e2, rows2);
+            const AsUnit e3 = desc(i + 6);
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                rows0[e] = rows1[e];
+                rows1[e] = rows2[e];
+            }
+            e2 = e3;
+        }
     }
 
     fence_before();
@@ -577,7 +591,7 @@ int launch_as(const CUtensorMap &xmap, const CUtensorMap &lmap, const AsArgs &ar
         AsArgs a = args;
         a.units += t0;
         const unsigned grid = (unsigned)(cnt < (uint64_t)sms ? cnt : (uint64_t)sms);
-        kern<<<grid, THREADS, C::SMEM, stream()>>>(xmap, lmap, a, (uint32_t)cnt);
+        kern<<<grid, AS_THREADS, C::SMEM, stream()>>>(xmap, lmap, a, (uint32_t)cnt);
         PIPNN_LAUNCH_CHECK();
     }
     return PIPNN_OK;
