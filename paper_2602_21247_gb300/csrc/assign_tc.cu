@@ -12,8 +12,9 @@
 // from a padded BF16 copy of all points made once per partition; B rows (the level's leaders, in
 // rank order) come from a small per-level BF16 copy with tiled TMA loads.
 //
-// Persistent CTA (one per SM, 10 warps) over units (subproblem, 128-instance tile):
-//   warp 0     producer: A gathers (each lane fetches four instance rows), B tiles + norm pieces
+// Persistent CTA (one per SM, 12 warps) over units (subproblem, 128-instance tile):
+//   warp 0     producer: B tiles + the leaders' norm pieces
+//   warps 10-11 A gathers, one warp per A buffer (each lane fetches four instance rows)
 //   warp 1     owns TMEM (4 x 128 accumulator columns); one thread issues the MMAs
 //   warps 2-9  epilogue: per row the F best (w, c) of its half of the columns, kept sorted in
 //              registers; columns that beat the current F-th are collected as a bit mask and
