@@ -511,9 +511,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                         }
                     }
                     const bool full = named_barrier_or(pair_id, 64, bad);
+                    uint32_t rk = 0;
                     if (lr < c) {
-                        gorder[base + candidate_rank(lr, c, DX, ids[r], dx + base, ids + base, bkey + base, full)] =
-                            (unsigned char)lr;
+                        rk = candidate_rank(lr, c, DX, ids[r], dx + base, ids + base, bkey + base, full);
+                        gorder[base + rk] = (unsigned char)lr;
                         gids[r] = ids[r];
                     }
                     uint32_t mw[2] = {0u, 0u};
@@ -538,7 +539,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                             mw[qq] = m;
                         }
                     }
-                    if (lr < c) reinterpret_cast<uint2 *>(gmask)[r] = make_uint2(mw[0], mw[1]);
+                    // masks stored by rank, so the walk reads them in order without a dependent lookup
+                    if (lr < c) reinterpret_cast<uint2 *>(gmask)[base + rk] = make_uint2(mw[0], mw[1]);
                 }
                 fence_before();
                 mbar_arrive(bar(C::BAR_TEMPTY + tb));
@@ -546,36 +548,33 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                 if (mine) {
                     named_barrier_or(pair_id, 64, false);  // masks, order and ids of the pair complete
                     if ((uint32_t)quarter == 2 * h) {
-                        // the walk, as for a large node, over at most 63 ranks
+                        // the walk, in one lane: rank i is admitted unless its mask (the candidates
+                        // that remove it) meets the admitted set, up to R admissions; then the
+                        // warp writes the admitted ids in rank order
                         const uint2 *mask = reinterpret_cast<const uint2 *>(gmask) + base;
-                        uint32_t A0 = 0, A1 = 0, e = 0;
-                        uint32_t out[2] = {0xFFFFFFFFu, 0xFFFFFFFFu};
-                        for (uint32_t b = 0; b * 32 < c && e < R; b++) {
-                            const uint32_t i = b * 32 + lane;
-                            const bool valid = i < c;
-                            const uint32_t tl = valid ? gorder[base + i] : 0u;
-                            const uint2 cm = valid ? mask[tl] : make_uint2(0, 0);
-                            unsigned U = __ballot_sync(0xffffffffu, valid && ((cm.x & A0) | (cm.y & A1)) == 0u);
-                            while (U != 0u && e < R) {
-                                const uint32_t u = __ffs(U) - 1;
-                                const uint32_t t = __shfl_sync(0xffffffffu, tl, u);
-                                const uint32_t wd = t >> 5, bit = 1u << (t & 31);
-                                A0 |= wd == 0 ? bit : 0u;
-                                A1 |= wd == 1 ? bit : 0u;
-                                const uint32_t id = gids[base + t];
-                                const uint32_t o = e >> 5;
-                                const bool slot = (e & 31) == (uint32_t)lane;
-                                out[0] = (slot && o == 0) ? id : out[0];
-                                out[1] = (slot && o == 1) ? id : out[1];
-                                e++;
-                                const uint32_t mwd = wd == 0 ? cm.x : cm.y;
-                                U &= ~__ballot_sync(0xffffffffu, (mwd >> (t & 31)) & 1u) & ~(1u << u);
+                        uint64_t adm = 0;
+                        if (lane == 0) {
+                            uint64_t A = 0;
+                            uint32_t e = 0;
+                            for (uint32_t i = 0; i < c && e < R; i++) {
+                                const uint2 mm = mask[i];
+                                const uint32_t t = gorder[base + i];
+                                if (((((uint64_t)mm.y << 32) | mm.x) & A) == 0ull) {
+                                    A |= 1ull << t;
+                                    adm |= 1ull << i;
+                                    e++;
+                                }
                             }
                         }
-                        for (uint32_t p = lane; p < R; p += 32) {
-                            const uint32_t o = p >> 5;
-                            a.adj[v * R + p] = p < e ? (o == 0 ? out[0] : o == 1 ? out[1] : 0xFFFFFFFFu) : 0xFFFFFFFFu;
+                        adm = __shfl_sync(0xffffffffu, adm, 0);
+                        const uint32_t e = (uint32_t)__popcll(adm);
+                        for (uint32_t i = lane; i < c; i += 32) {
+                            if ((adm >> i) & 1ull) {
+                                const uint32_t pos = (uint32_t)__popcll(adm & ((1ull << i) - 1ull));
+                                a.adj[v * R + pos] = gids[base + gorder[base + i]];
+                            }
                         }
+                        for (uint32_t p = e + lane; p < R; p += 32) a.adj[v * R + p] = 0xFFFFFFFFu;
                         if (lane == 0) a.deg[v] = e;
                     }
                 }
