@@ -25,15 +25,35 @@ constexpr int HP_BUF = 512;   // slots per warp buffer
 constexpr uint32_t HP_HT = 256;       // per-warp hash set of distinct slots
 constexpr uint32_t HP_DISTINCT = 128; // distinct slots the fast path sorts in registers
 
+// Four consecutive candidates per thread, grouped like hp_scatter below: a group (v, c1), (c1, v),
+// (v, c2), (c2, v) takes three atomics (v's two at once) instead of four.
 __global__ void hp_count(const uint32_t *dst, const uint32_t *src, uint64_t count, uint64_t n, unsigned *per_node,
                          unsigned *err) {
-    for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < count; e += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t v = dst[e], c = src[e];
-        if (v >= n || c >= n) {
-            atomicOr(err, DERR_RANGE);
+    const uint64_t ngroups = (count + 3) / 4;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < ngroups; g += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t e = 4 * g;
+        uint32_t v[4], c[4];
+        bool ok[4];
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const bool in = e + q < count;
+            v[q] = in ? dst[e + q] : 0u;
+            c[q] = in ? src[e + q] : 0u;
+            bad |= in && (v[q] >= n || c[q] >= n);
+            ok[q] = in && v[q] < n && c[q] < n && v[q] != c[q];
+        }
+        if (bad) atomicOr(err, DERR_RANGE);
+        if (ok[0] && ok[1] && ok[2] && ok[3] && v[2] == v[0] && v[1] == c[0] && c[1] == v[0] && v[3] == c[2] &&
+            c[3] == v[2]) {
+            atomicAdd(&per_node[v[0]], 2u);
+            atomicAdd(&per_node[v[1]], 1u);
+            atomicAdd(&per_node[v[3]], 1u);
             continue;
         }
-        if (v != c) atomicAdd(&per_node[v], 1u);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (ok[q]) atomicAdd(&per_node[v[q]], 1u);
     }
 }
 
@@ -483,7 +503,7 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
     PIPNN_TRY(ws.zeros(&fill, n));
     PIPNN_TRY(ws.alloc(&tot, 1));
     if (count) {
-        hp_count<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, count, n, fill, err);
+        hp_count<<<grid_for((count + 3) / 4, 256), 256, 0, stream()>>>(dst, src, count, n, fill, err);
         PIPNN_LAUNCH_CHECK();
         hp_widen<<<grid_for(n, 256), 256, 0, stream()>>>(fill, n, start);
         PIPNN_LAUNCH_CHECK();
@@ -604,7 +624,7 @@ int hashprune_noalloc_impl(const uint32_t *dst, const uint32_t *src, const float
     } restore;
 
     if (count) {
-        hp_count<<<grid_for(count, 256), 256, 0, stream()>>>(dst, src, count, n, fill, err);
+        hp_count<<<grid_for((count + 3) / 4, 256), 256, 0, stream()>>>(dst, src, count, n, fill, err);
         PIPNN_LAUNCH_CHECK();
         hp_widen<<<grid_for(n, 256), 256, 0, stream()>>>(fill, n, start);
         PIPNN_LAUNCH_CHECK();

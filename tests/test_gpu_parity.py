@@ -165,6 +165,34 @@ def test_hashprune_grouped_pick_stream_odd_sketch_width():
         assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
 
 
+def test_hashprune_grouped_stream_with_self_edges_and_bad_ids():
+    # the k = 2 pick stream with some groups broken by a self edge (skipped by both sides); then an
+    # id past the last node in each position of a group and in the ragged tail, which is an error
+    # (and the next call still works)
+    rng = np.random.default_rng(6)
+    X = synth.mixture(3000, 16, synth.U8, 15, 10.0, seed=37)
+    off_o, mem_o, _ = oracle.partition(X, oracle.params(**KW), seed=16)
+    dst, src, dist = oracle.leaf_pick(X, off_o, mem_o, k=2)
+    n = X.shape[0]
+    S = rng.standard_normal((n, 12)).astype(np.float32)
+    src = src.copy()
+    at = rng.choice(len(dst), size=len(dst) // 50, replace=False)
+    src[at] = dst[at]
+    res_o, cnt_o = oracle.hashprune_closed(dst, src, dist, S, n, 24)
+    res, cnt = pk.pipnn_hashprune(dev(dst), dev(src), dev(dist), dev(S), n, 24)
+    assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
+    tail = len(dst) - 1 - 4 * ((len(dst) - 1) // 4)
+    for pos in (28, 29, 30, 31, len(dst) - 1 - tail, len(dst) - 1):
+        for which in (0, 1):
+            bd, bs = dst.copy(), src.copy()
+            (bd if which == 0 else bs)[pos] = n
+            with pytest.raises(pk.PipnnError) as e:
+                pk.pipnn_hashprune(dev(bd), dev(bs), dev(dist), dev(S), n, 24)
+            assert e.value.code == -1
+    res, cnt = pk.pipnn_hashprune(dev(dst), dev(src), dev(dist), dev(S), n, 24)
+    assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
+
+
 @pytest.mark.parametrize("engine,dtype", [("tc", synth.U8), ("simt", synth.F32)])
 def test_build_replicas_parity(engine, dtype):
     # Sec. 4.1 replication: three independent RBC runs feed one set of reservoirs
