@@ -193,6 +193,60 @@ def test_hashprune_grouped_stream_with_self_edges_and_bad_ids():
     assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
 
 
+def _small_batches(n, batches, rng):
+    """Batches of 0..40 slots per node (in shuffled order): fresh random pairs, the same pair as an
+    earlier slot with its distance (an exact duplicate) or with another distance (the same bucket,
+    another slot); distances on a coarse grid, so that many tie in their 16-bit form."""
+    hist_s = [np.zeros(0, np.uint32) for _ in range(n)]
+    hist_w = [np.zeros(0, np.float32) for _ in range(n)]
+    out = []
+    for _ in range(batches):
+        D, Sx, W = [], [], []
+        for v in range(n):
+            c = int(rng.integers(0, 41))
+            if c == 0:
+                continue
+            s_ = rng.integers(0, n - 1, size=c).astype(np.uint32)
+            s_ += (s_ >= v).astype(np.uint32)
+            w_ = (rng.integers(0, 200, size=c) * 0.25).astype(np.float32)
+            if len(hist_s[v]):
+                pick = rng.integers(0, len(hist_s[v]), size=c)
+                r = rng.random(c)
+                dup, rebucket = r < 0.35, (r >= 0.35) & (r < 0.45)
+                s_[dup | rebucket] = hist_s[v][pick[dup | rebucket]]
+                w_[dup] = hist_w[v][pick[dup]]
+            D.append(np.full(c, v, np.uint32))
+            Sx.append(s_)
+            W.append(w_)
+            hist_s[v] = np.concatenate([hist_s[v], s_])
+            hist_w[v] = np.concatenate([hist_w[v], w_])
+        d, s_, w_ = (np.concatenate(z) for z in (D, Sx, W))
+        perm = rng.permutation(len(d))
+        out.append((d[perm], s_[perm], w_[perm]))
+    return out
+
+
+@pytest.mark.parametrize("m", [4, 12, 13])
+@pytest.mark.parametrize("l_max", [16, 96, 200])
+def test_hashprune_small_batches_into_filled_reservoirs(m, l_max):
+    # many batches merged into the same reservoirs: per node up to 32 new slots into up to 128 kept
+    # ones (with at most 12 hash bits) take the bucket-lookup path, the rest the sorting paths;
+    # after every batch the reservoirs equal the oracle's over the whole stream so far
+    rng = np.random.default_rng(100 + m + l_max)
+    n = 2000
+    S = rng.standard_normal((n, m)).astype(np.float32)
+    Sd = dev(S)
+    res = cnt = None
+    seen = []
+    for d, s_, w_ in _small_batches(n, 8, rng):
+        seen.append((d, s_, w_))
+        res, cnt = pk.pipnn_hashprune(dev(d), dev(s_), dev(w_), Sd, n, l_max, res, cnt)
+        res_o, cnt_o = oracle.hashprune_closed(*(np.concatenate(z) for z in zip(*seen)), S, n, l_max)
+        assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
+    if l_max > 128 and m >= 12:
+        assert (cnt_o > 128).any()   # some reservoirs outgrow the bucket-lookup path
+
+
 @pytest.mark.parametrize("engine,dtype", [("tc", synth.U8), ("simt", synth.F32)])
 def test_build_replicas_parity(engine, dtype):
     # Sec. 4.1 replication: three independent RBC runs feed one set of reservoirs
