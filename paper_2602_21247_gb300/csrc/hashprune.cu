@@ -12,7 +12,8 @@
 //      keeping a slot iff its hash bucket has not been seen yet (__match_any_sync within a chunk
 //      of 32, a bitmap of 2^m bits across chunks), until l_max are kept.  Nodes with more than
 //      128 distinct slots sort everything (in registers up to 256, else in shared memory, chunk
-//      by chunk for batches larger than the buffer).
+//      by chunk for batches larger than the buffer).  A node with at most 32 new slots and at
+//      most 128 kept ones (hash bits <= 12) skips the sort: see the small-batch path below.
 #include "internal.cuh"
 
 #include <type_traits>
