@@ -646,7 +646,8 @@ def main():
             st = stats[-1]
             out = {"profile_run": True, "ms_per_step": ms, "phases_ms": phases(stats),
                    "leaf_pairs": st["leaf_pairs"], "leaf_members": st["leaf_members"],
-                   "leaves": st["leaves"], "candidates": st["candidates"], "waves": st["waves"]}
+                   "leaves": st["leaves"], "candidates": st["candidates"], "waves": st["waves"],
+                   "hashprune_merges": st["hashprune_merges"]}
             if args.profile_knn and w["dtype"] != synth.F32:
                 # one k-NN graph construction (Sec. 5) on the built graph, L = 32, k = 10, after one
                 # untimed call
@@ -694,7 +695,8 @@ def main():
                 "roofline_prune": prune_roofline(stats, w, n), "e2e": e2e,
                 "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks,
                 "phases_ms": phases(stats), "leaves": st["leaves"], "candidates": st["candidates"],
-                "waves_per_build": st["waves"], "peak_device_bytes": st["peak_device_bytes"]}
+                "waves_per_build": st["waves"], "hashprune_merges_per_build": st["hashprune_merges"],
+                "peak_device_bytes": st["peak_device_bytes"]}
         if w["dtype"] == synth.F32:
             line["config"]["prec"] = args.prec or ("bf16x3" if args.engine == "tc" else "fp32")
         Xnp = Xh.numpy()

@@ -128,6 +128,12 @@ typedef struct pipnn_params {
                                choice: both edges of every picked pair), PIPNN_PICK_DIRECTED
                                (only member -> neighbour: the neighbour enters the member's
                                reservoir) or PIPNN_PICK_INVERTED (only neighbour -> member)  */
+    uint32_t merge_waves;   /* leaf waves whose candidates HashPrune merges into the reservoirs
+                               together (their candidate edges are kept until then): k = after
+                               every k waves, 0 = automatic (as many consecutive waves as the
+                               memory left beside the leaf step holds; with wave_members also
+                               0, the leaf waves are then sized a quarter of that).  Like the
+                               wave split, the grouping does not change the graph.            */
 } pipnn_params;
 
 /* Output graph: ids[v*R + j] for j < deg[v] are v's out-neighbours in prune order; the rest of
@@ -172,8 +178,9 @@ typedef struct pipnn_stats {
     uint64_t kernel_launches;    /* kernels this library launched during the build              */
     uint64_t leaf_full_rows;     /* reduced-precision leaf engine: rows whose error band did not
                                     fit the tracked candidates and were evaluated in full        */
-    uint32_t waves;              /* leaf / HashPrune waves of the build (summed over replicas)   */
-    uint32_t pad_;
+    uint32_t waves;              /* leaf waves of the build (summed over replicas)              */
+    uint32_t hashprune_merges;   /* HashPrune merges of the build (summed over replicas): one per
+                                    group of merge_waves leaf waves                            */
     uint64_t peak_device_bytes;  /* device memory in use (total minus free, so including memory
                                     the allocators hold in reserve) at the fullest point the
                                     build sampled: after the partition and inside every wave  */

@@ -51,7 +51,7 @@ class pipnn_params(C.Structure):
                 ("R", C.c_uint32), ("alpha", C.c_float), ("final_prune", C.c_int32),
                 ("dtype", C.c_int32), ("leaf_engine", C.c_int32), ("hyperplanes", C.c_void_p),
                 ("replicas", C.c_uint32), ("prec", C.c_int32), ("wave_members", C.c_uint64),
-                ("pick_direction", C.c_int32)]
+                ("pick_direction", C.c_int32), ("merge_waves", C.c_uint32)]
 
 
 class pipnn_graph(C.Structure):
@@ -75,7 +75,7 @@ class pipnn_stats(C.Structure):
                 ("leaves", C.c_uint64), ("leaf_members", C.c_uint64), ("candidates", C.c_uint64),
                 ("leaf_pairs", C.c_double), ("leaf_pairs_executed", C.c_double),
                 ("kernel_launches", C.c_uint64), ("leaf_full_rows", C.c_uint64), ("waves", C.c_uint32),
-                ("pad_", C.c_uint32), ("peak_device_bytes", C.c_uint64), ("ms_prune_kernel", C.c_float),
+                ("hashprune_merges", C.c_uint32), ("peak_device_bytes", C.c_uint64), ("ms_prune_kernel", C.c_float),
                 ("pad2_", C.c_uint32), ("reservoir_slots", C.c_uint64)]
 
 
@@ -165,7 +165,7 @@ def _take(ptr, count, typestr, view=None):
 def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.005, fanout=(2,), leaf_k=2,
            hash_bits=12, l_max=64, R=64, alpha=1.2, final_prune=True, leaf_engine=PIPNN_LEAF_SIMT,
            hyperplanes=None, replicas=1, prec=PIPNN_PREC_FP32, wave_members=0,
-           pick_direction=PIPNN_PICK_BIDIRECTED) -> pipnn_params:
+           pick_direction=PIPNN_PICK_BIDIRECTED, merge_waves=0) -> pipnn_params:
     """BP of Alg. 4.  `hyperplanes` (hash_bits x d float32, numpy or torch) must stay alive for the call."""
     p = pipnn_params()
     p.c_max = c_max
@@ -188,6 +188,7 @@ def params(dtype=PIPNN_F32, c_max=1024, c_min=None, max_leaders=1000, p_samp=0.0
     p.prec = prec
     p.wave_members = wave_members
     p.pick_direction = pick_direction
+    p.merge_waves = merge_waves
     p._keep = hyperplanes
     return p
 

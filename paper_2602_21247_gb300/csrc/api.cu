@@ -22,6 +22,8 @@ int leaf_pick(const void *X, uint64_t n, uint32_t d, int dtype, int metric, cons
               int direction, pipnn_edges *out, float *ms_kernel, uint32_t *launches, uint64_t *full_rows);
 int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
                     uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt, int padded);
+int hashprune_merge_segments(const EdgeSegment *seg, uint32_t nseg, const float *S, uint32_t m, uint64_t n,
+                             uint32_t l_max, uint64_t *res, uint32_t *cnt, int padded);
 int final_prune(const void *X, uint64_t n, uint32_t d, int dtype, int metric, const int32_t *sqnorm_bytes,
                 const uint64_t *res, const uint32_t *cnt, uint32_t l_max, uint32_t R, float alpha, int engine,
                 uint32_t *adj, uint32_t *deg, float *ms_kernel);
@@ -158,14 +160,23 @@ void note_peak(pipnn_stats *st) {
     if (used > st->peak_device_bytes) st->peak_device_bytes = used;
 }
 
-// Leaf members one wave may hold: the free device memory (less the per-node HashPrune arrays and
-// a reserve) divided by a member's share of the leaf step (staged operand row, member and key
-// arrays, candidate edges, grouped HashPrune slots), capped below the tensor maps' 2^31 rows.
-uint64_t auto_wave_members(uint64_t n, uint32_t d, int dtype, const pipnn_params *bp) {
+// Leaf waves per HashPrune merge when both are sized automatically: fewer merges mean fewer passes
+// over every node's reservoir, at the price of keeping the earlier waves' candidate edges while the
+// later ones run their leaf step.
+constexpr uint64_t kLeafWavesPerMerge = 4;
+
+// Members of one leaf wave (*wave) and of one HashPrune merge group (*group, consecutive waves whose
+// candidate edges are kept and merged together), from the free device memory less the per-node
+// HashPrune arrays and a reserve.  A member costs, in the leaf step, the engine's staged operand
+// row and per-member buffers plus the 2k candidate edges it writes (12 B each); while its group is
+// open, its edges; in the merge, its edges and their 8-byte grouped slots.  A group of G members
+// whose last wave has W members needs 12·2k·(G − W) + leaf·W in the leaf step and 20·2k·G in the
+// merge.  Waves stay below the tensor maps' 2^31 rows.
+void wave_plan(uint64_t n, uint32_t d, int dtype, const pipnn_params *bp, uint64_t *wave, uint64_t *group) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
         cudaGetLastError();
-        return 1ull << 26;
+        fr = 0;
     }
     // memory the stream-ordered pool holds but no allocation uses is available too
     int dev = 0;
@@ -177,10 +188,6 @@ uint64_t auto_wave_members(uint64_t n, uint32_t d, int dtype, const pipnn_params
             fr += (size_t)(reserved - used);
     }
     cudaGetLastError();
-    // Device bytes a wave holds per leaf member: in the leaf step, the engine's staged operand row
-    // and per-member buffers plus the 2k candidate edges it writes (12 B each); in HashPrune, the
-    // edges and their 8-byte grouped slots.  The two steps do not overlap; the per-node arrays of
-    // HashPrune (12 B per node) are part of the fixed reserve.
     const uint64_t kp = ((uint64_t)d + 63) / 64 * 64;
     const uint64_t k2 = 2ull * bp->leaf_k;
     uint64_t stage = 32;  // CUDA-core engines read the rows in place
@@ -190,13 +197,33 @@ uint64_t auto_wave_members(uint64_t n, uint32_t d, int dtype, const pipnn_params
         else if (bp->prec == PIPNN_PREC_FP8) stage = 128 * ((kp + 127) / 128) + 96;
         else stage = kp * 2 + 96;
     }
-    const uint64_t leaf_step = stage + k2 * 12, hp_step = k2 * (12 + 8);
-    const uint64_t per_member = (leaf_step > hp_step ? leaf_step : hp_step) + 32;
+    const uint64_t keep = k2 * 12, leaf_step = stage + keep + 32, hp_step = k2 * (12 + 8) + 16;
     const uint64_t reserve = (2ull << 30) + 24 * n;
-    uint64_t w = fr > reserve ? (fr - reserve) / per_member : (1ull << 20);
-    if (w < (1ull << 20)) w = 1ull << 20;
-    if (w > 0x7FF00000ull) w = 0x7FF00000ull;
-    return w;
+    const uint64_t F = fr > reserve ? fr - reserve : 0;
+    const uint64_t lo = 1ull << 20, cap = 0x7FF00000ull;
+    uint64_t W = bp->wave_members, G = 0;
+    if (!W) {
+        // one wave per merge: the larger step bounds it; several: the leaf step of the group's
+        // last wave beside the kept edges of the others
+        const uint64_t one = leaf_step > hp_step ? leaf_step : hp_step;
+        W = F / one;
+        if (bp->merge_waves != 1) {
+            const uint64_t s = bp->merge_waves ? bp->merge_waves : kLeafWavesPerMerge;
+            G = F / (keep + (leaf_step + s - 1) / s);
+            if (G > F / hp_step) G = F / hp_step;
+            W = G / s;
+        }
+        if (W < lo) W = lo;
+        if (W > cap) W = cap;
+    } else if (bp->merge_waves == 0) {
+        // caller-sized waves: as many per merge as fit beside one wave's leaf step
+        const uint64_t left = F > leaf_step * W ? F - leaf_step * W : 0;
+        G = W + left / keep;
+        if (G > F / hp_step) G = F / hp_step;
+    }
+    if (G < W) G = W;
+    *wave = W;
+    *group = G;
 }
 
 // Keeps freed stream-ordered allocations in the device's default pool (the build allocates and
@@ -341,22 +368,61 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
                 if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "memset: %s", cudaGetErrorString(e));
             }
         }
-        // A2 .. A5 in waves of consecutive leaves: every wave's candidates are merged into the
-        // reservoirs before the next wave's are formed (Alg. 3's history independence makes the
-        // result independent of the split)
+        // A2 .. A4 in waves of consecutive leaves, A5 once per group of consecutive waves: a group's
+        // candidate edges are kept until its last wave's leaf step is done and are then merged
+        // into the reservoirs before the next group's are formed (Alg. 3's history independence
+        // makes the result independent of both splits)
         std::vector<uint64_t> hoff;
-        uint64_t W = 0;
+        uint64_t W = 0, G = 0;
         if (rc == PIPNN_OK) rc = leaf_offsets_to_host(leaves.offsets, leaves.num_leaves, &hoff);
         if (rc == PIPNN_OK) {
             note_peak(&st);
-            W = bp->wave_members ? bp->wave_members : auto_wave_members(n, d, dtype, bp);
+            wave_plan(n, d, dtype, bp, &W, &G);
         }
-        for (uint64_t b0 = 0; rc == PIPNN_OK && b0 < leaves.num_leaves;) {
+        std::vector<uint64_t> wave_lo;  // first leaf of every wave, then num_leaves
+        for (uint64_t b0 = 0; b0 < leaves.num_leaves;) {
+            wave_lo.push_back(b0);
             uint64_t b1 = b0 + 1;
             while (b1 < leaves.num_leaves && hoff[b1 + 1] - hoff[b0] <= W) b1++;
-            const uint64_t Lw = b1 - b0;
+            b0 = b1;
+        }
+        wave_lo.push_back(leaves.num_leaves);
+        std::vector<pipnn_edges> group;  // the open group's candidate edges, one entry per wave
+        uint64_t group_members = 0;
+        auto free_group = [&]() {
+            for (auto &e : group) {
+                dev_free_raw(e.dst);
+                dev_free_raw(e.src);
+                dev_free_raw(e.dist);
+            }
+            group.clear();
+            group_members = 0;
+        };
+        auto merge_group = [&]() -> int {
+            Timer mt;
+            PIPNN_TRY(mt.init());
+            note_peak(&st);
+            std::vector<EdgeSegment> seg;
+            for (auto &e : group) seg.push_back(EdgeSegment{e.dst, e.src, e.dist, e.count});
+            mt.mark(0);
+            int r2 = hashprune_merge_segments(seg.data(), (uint32_t)seg.size(), S, m, n, bp->l_max, res, cnt, 1);
+            mt.mark(1);
+            free_group();
+            if (r2 == PIPNN_OK) {
+                cudaStreamSynchronize(stream());
+                st.ms_hashprune += mt.ms(0, 1);
+                st.hashprune_merges++;
+            }
+            return r2;
+        };
+        for (size_t wi = 0; rc == PIPNN_OK && wi + 1 < wave_lo.size(); wi++) {
+            const uint64_t b0 = wave_lo[wi], b1 = wave_lo[wi + 1], Lw = b1 - b0;
+            const uint64_t members = hoff[b1] - hoff[b0];
+            // close the open group first if this wave does not fit in it
+            if (!group.empty() && (bp->merge_waves ? group.size() >= bp->merge_waves : group_members + members > G))
+                rc = merge_group();
             Timer wt;
-            rc = wt.init();
+            if (rc == PIPNN_OK) rc = wt.init();
             uint64_t *off_w = nullptr;
             Workspace wave_ws;
             if (rc == PIPNN_OK) rc = wave_ws.alloc(&off_w, Lw + 1);
@@ -367,36 +433,31 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
                 if (e != cudaSuccess) rc = set_error(PIPNN_ECUDA, "rebase: %s", cudaGetErrorString(e));
                 count_launch();
             }
-            pipnn_edges edges{};
             if (rc == PIPNN_OK) {
+                pipnn_edges edges{};
                 float leaf_ms = 0.0f;
                 uint32_t leaf_launches = 0;
                 uint64_t full_rows = 0;
                 rc = leaf_pick(X, n, d, dtype, metric, sqn_bytes, off_w, leaves.members + hoff[b0], Lw, bp->leaf_k,
                                bp->leaf_engine, bp->prec, bp->pick_direction, &edges, &leaf_ms, &leaf_launches,
                                &full_rows);
-                st.leaf_full_rows += full_rows;
-                st.ms_leaf_kernel += leaf_ms;
-                st.leaf_kernel_launches += leaf_launches;
-                st.candidates += edges.count;
-                wt.mark(1);
+                if (rc == PIPNN_OK || edges.dst || edges.src || edges.dist) group.push_back(edges);
+                group_members += members;
+                if (rc == PIPNN_OK) {
+                    st.leaf_full_rows += full_rows;
+                    st.ms_leaf_kernel += leaf_ms;
+                    st.leaf_kernel_launches += leaf_launches;
+                    st.candidates += edges.count;
+                    wt.mark(1);
+                    note_peak(&st);
+                    cudaStreamSynchronize(stream());
+                    st.ms_leaf += wt.ms(0, 1);
+                    st.waves++;
+                }
             }
-            if (rc == PIPNN_OK) {
-                note_peak(&st);
-                rc = hashprune_merge(edges.dst, edges.src, edges.dist, edges.count, S, m, n, bp->l_max, res, cnt, 1);
-                wt.mark(2);
-            }
-            dev_free_raw(edges.dst);
-            dev_free_raw(edges.src);
-            dev_free_raw(edges.dist);
-            if (rc == PIPNN_OK) {
-                cudaStreamSynchronize(stream());
-                st.ms_leaf += wt.ms(0, 1);
-                st.ms_hashprune += wt.ms(1, 2);
-                st.waves++;
-            }
-            b0 = b1;
         }
+        if (rc == PIPNN_OK && !group.empty()) rc = merge_group();
+        free_group();
         dev_free_raw(leaves.offsets);
         dev_free_raw(leaves.members);
         if (rc != PIPNN_OK) return rc;

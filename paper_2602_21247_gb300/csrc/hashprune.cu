@@ -596,8 +596,10 @@ size_t hashprune_smem_bytes(uint32_t m) {
            (size_t)HP_WARPS * HP_HT * 8;
 }
 
-int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
-                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt, int padded) {
+// Several runs of candidate edges merged as one stream: counted and grouped run by run, then merged
+// per node once.
+int hashprune_merge_segments(const EdgeSegment *seg, uint32_t nseg, const float *S, uint32_t m, uint64_t n,
+                             uint32_t l_max, uint64_t *res, uint32_t *cnt, int padded) {
     if (m < 1 || m > 16) return set_error(PIPNN_EINVAL, "hash_bits %u outside 1..16", m);
     if (l_max < 1 || l_max > 256) return set_error(PIPNN_EINVAL, "l_max %u outside 1..256", l_max);
     Workspace ws;
@@ -605,13 +607,18 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
     uint64_t *start, *tot;
     unsigned *fill;
     uint64_t *slots;
-    uint64_t E = 0;
+    uint64_t E = 0, count = 0;
     PIPNN_TRY(ws.zeros(&start, n + 1));
     PIPNN_TRY(ws.zeros(&fill, n));
     PIPNN_TRY(ws.alloc(&tot, 1));
-    if (count) {
-        hp_count<<<grid_for((count + 3) / 4, 256), 256, 0, stream()>>>(dst, src, count, n, fill, err);
+    for (uint32_t i = 0; i < nseg; i++) {
+        if (!seg[i].count) continue;
+        hp_count<<<grid_for((seg[i].count + 3) / 4, 256), 256, 0, stream()>>>(seg[i].dst, seg[i].src, seg[i].count, n,
+                                                                               fill, err);
         PIPNN_LAUNCH_CHECK();
+        count += seg[i].count;
+    }
+    if (count) {
         hp_widen<<<grid_for(n, 256), 256, 0, stream()>>>(fill, n, start);
         PIPNN_LAUNCH_CHECK();
     }
@@ -619,10 +626,11 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
     PIPNN_CUDA(cudaMemcpyAsync(start + n, tot, 8, cudaMemcpyDeviceToDevice, stream()));
     PIPNN_TRY(read_u64(tot, &E));
     PIPNN_TRY(ws.alloc(&slots, E));
-    if (count) {
-        hp_scatter<<<grid_for((count + 3) / 4, 256), 256, 0, stream()>>>(dst, src, dist, count, n, S, m,
-                                                                          reinterpret_cast<unsigned long long *>(start),
-                                                                          slots);
+    for (uint32_t i = 0; i < nseg; i++) {
+        if (!seg[i].count) continue;
+        hp_scatter<<<grid_for((seg[i].count + 3) / 4, 256), 256, 0, stream()>>>(
+            seg[i].dst, seg[i].src, seg[i].dist, seg[i].count, n, S, m, reinterpret_cast<unsigned long long *>(start),
+            slots);
         PIPNN_LAUNCH_CHECK();
     }
     size_t smem = hashprune_smem_bytes(m);
@@ -631,6 +639,12 @@ int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist,
                                                                                    padded);
     PIPNN_LAUNCH_CHECK();
     return check_device_error("hashprune");
+}
+
+int hashprune_merge(const uint32_t *dst, const uint32_t *src, const float *dist, uint64_t count, const float *S,
+                    uint32_t m, uint64_t n, uint32_t l_max, uint64_t *res, uint32_t *cnt, int padded) {
+    const EdgeSegment seg{dst, src, dist, count};
+    return hashprune_merge_segments(&seg, 1, S, m, n, l_max, res, cnt, padded);
 }
 
 }  // namespace pipnn

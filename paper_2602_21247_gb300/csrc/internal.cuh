@@ -13,6 +13,14 @@
 
 namespace pipnn {
 
+// One run of candidate edges for HashPrune: dst[e] receives src[e] at dissimilarity dist[e].
+struct EdgeSegment {
+    const uint32_t *dst;
+    const uint32_t *src;
+    const float *dist;
+    uint64_t count;
+};
+
 // ---------------------------------------------------------------------------------------------
 // Errors.  Every host routine returns a PIPNN_* status; the message goes to a thread-local
 // buffer read by pipnn_last_error().

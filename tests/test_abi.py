@@ -53,6 +53,7 @@ def test_params_struct_matches_header_layout():
     assert pk.pipnn_params.prec.offset == 84
     assert pk.pipnn_params.wave_members.offset == 88
     assert pk.pipnn_params.pick_direction.offset == 96
+    assert pk.pipnn_params.merge_waves.offset == 100
     assert ctypes.sizeof(pk.pipnn_params) == 104
 
 

@@ -41,6 +41,8 @@ def test_wave_split_build_equals_oracle_bytes(engine, wave):
         assert st["waves"] > 10
     elif wave == 0:
         assert st["waves"] == 1
+    # caller-sized waves, merges sized by memory: this build's candidates fit in one merge
+    assert st["hashprune_merges"] == 1
     assert st["candidates"] == st_o["candidates"]
     assert np.array_equal(host_u32(deg), deg_o) and np.array_equal(host_u32(adj), adj_o)
 
@@ -66,3 +68,19 @@ def test_replicas_in_waves():
     adj, deg = pk.pipnn_build(torch.from_numpy(X).cuda(), bp, 7)
     assert pk.pipnn_get_stats()["waves"] > 3
     assert np.array_equal(host_u32(deg), want_deg) and np.array_equal(host_u32(adj), want_adj)
+
+
+@pytest.mark.parametrize("merge_waves", [1, 2, 7])
+def test_merge_groups_equal_oracle(merge_waves):
+    """HashPrune once per group of consecutive leaf waves (the candidate edges of a group kept until
+    its last wave is done): every grouping gives the oracle's graph."""
+    X = synth.mixture(20000, 128, synth.U8, 80, 10.0, seed=94)
+    H = synth.hyperplanes(12, 128, seed=4)
+    adj_o, deg_o, _ = oracle.build(X, oracle.params(**KW), H, 42)
+    bp = pk.params(dtype=pk.PIPNN_U8, hyperplanes=H, leaf_engine=pk.PIPNN_LEAF_TC, wave_members=3000,
+                   merge_waves=merge_waves, **KW)
+    adj, deg = pk.pipnn_build(torch.from_numpy(X).cuda(), bp, 42)
+    st = pk.pipnn_get_stats()
+    assert st["waves"] > 10
+    assert st["hashprune_merges"] == -(-st["waves"] // merge_waves)
+    assert np.array_equal(host_u32(deg), deg_o) and np.array_equal(host_u32(adj), adj_o)
