@@ -301,26 +301,29 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
             __syncwarp();
             return out < l_max ? out : l_max;
         };
-        // small-batch path (hash bits <= 12, at most 32 new slots, at most 128 kept): the kept slots
-        // have distinct buckets, so each new slot needs only the kept slot of its own bucket.  The
-        // smallest new slot of every bucket (exact duplicates: the lowest lane) is looked up in a
-        // bucket -> position byte table; it is dropped if the kept slot is not larger, else it
-        // replaces it (or enters a bucket not kept yet).  Every survivor's place in the merged
-        // order is its rank among the surviving old slots plus its rank among the entering ones;
-        // places from l_max on fall off.  A batch that changes nothing writes nothing.
-        if (m <= 12 && b - a <= 32 && cur <= 128) {
-            const uint32_t nn = (uint32_t)(b - a);
-            const bool valid = (uint32_t)lane < nn;
-            const uint64_t x = valid ? slots[a + lane] : ~0ull;
-            uint64_t o[4];
+        // small-batch path (hash bits <= 12, at most 128 new slots, at most 128 kept at any point):
+        // the kept slots have distinct buckets, so each new slot needs only the kept slot of its
+        // own bucket.  The new slots go 32 at a time: the smallest of every bucket in the chunk
+        // (exact duplicates: the lowest lane) is looked up in a bucket -> position byte table; it
+        // is dropped if the kept slot is not larger, else it replaces it (or enters a bucket not
+        // kept yet).  Every survivor's place in the merged order is its rank among the surviving
+        // kept slots plus its rank among the entering ones; places from l_max on fall off.  The
+        // merged order stays in shared memory and registers between chunks and is written once; a
+        // batch that changes nothing writes nothing.  (An empty reservoir with more than 32 new
+        // slots goes to the hash-set path below, which was faster there.)
+        if (m <= 12 && b - a <= (cur > 0 ? 128u : 32u) && cur <= 128 && (l_max <= 128 || cur + (b - a) <= 128)) {
+            const uint32_t nn_all = (uint32_t)(b - a);
+            uint64_t o[4];  // kept slot t = 32 q + lane in o[q]
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const uint32_t t = 32 * q + lane;
                 o[q] = t < cur ? res[v * l_max + t] : ~0ull;
             }
-            // the table (2^m bytes, position + 1, 0 = bucket not kept) in buf, the old slots in ht
+            uint64_t x = (uint32_t)lane < nn_all ? slots[a + lane] : ~0ull;
+            // the table (2^m bytes, position + 1, 0 = bucket not kept) in buf, the kept slots in ht
             unsigned char *tbl = reinterpret_cast<unsigned char *>(buf);
             uint64_t *oldsm = reinterpret_cast<uint64_t *>(ht);
+            const uint32_t hmask = (1u << m) - 1u;
             for (uint32_t i = lane; i < ((1u << m) + 15) / 16; i += 32)
                 reinterpret_cast<uint4 *>(buf)[i] = make_uint4(0u, 0u, 0u, 0u);
             __syncwarp();
@@ -328,81 +331,109 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
             for (int q = 0; q < 4; q++) {
                 const uint32_t t = 32 * q + lane;
                 if (t < cur) {
-                    tbl[(uint32_t)o[q] & ((1u << m) - 1u)] = (unsigned char)(t + 1);
+                    tbl[(uint32_t)o[q] & hmask] = (unsigned char)(t + 1);
                     oldsm[t] = o[q];
                 }
             }
-            const uint32_t h = (uint32_t)x & ((1u << m) - 1u);
-            const unsigned same = __match_any_sync(0xffffffffu, valid ? h : 0xFFFFFFFFu);
-            bool keep = valid;
-            if (valid) {
-                for (unsigned r = same; r; r &= r - 1) {
-                    const int j = __ffs(r) - 1;
-                    const uint64_t y = __shfl_sync(same, x, j);
-                    if (y < x || (y == x && j < lane)) keep = false;
-                }
-            }
-            __syncwarp();
-            const uint32_t p = keep ? tbl[h] : 0u;
-            const uint64_t ov = p ? oldsm[p - 1] : 0ull;
-            const bool ins = keep && (p == 0 || ov > x);
-            const bool repl = ins && p != 0;
-            const unsigned insm = __ballot_sync(0xffffffffu, ins);
-            unsigned dead[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-                dead[q] = __reduce_or_sync(0xffffffffu,
-                                           (repl && ((p - 1) >> 5) == (uint32_t)q) ? 1u << ((p - 1) & 31) : 0u);
-            // old slots below index s that were replaced
-            auto dead_below = [&](uint32_t s) {
-                uint32_t c = 0;
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const uint32_t lo = 32u * q;
-                    if (s >= lo + 32) c += __popc(dead[q]);
-                    else if (s > lo) c += __popc(dead[q] & ((1u << (s - lo)) - 1u));
-                }
-                return c;
-            };
-            uint32_t ncur = cur;
-            if (insm) {
-                uint32_t pos_x = 0;
-                if (ins) {
-                    uint32_t lo = 0, hi = cur;
-                    while (lo < hi) {
-                        const uint32_t mid = (lo + hi) >> 1;
-                        if (oldsm[mid] < x) lo = mid + 1;
-                        else hi = mid;
+            uint32_t kc = cur;
+            bool changed = false;
+            for (uint32_t c0 = 0; c0 < nn_all; c0 += 32) {
+                const bool valid = c0 + lane < nn_all;
+                const uint32_t h = (uint32_t)x & hmask;
+                const unsigned same = __match_any_sync(0xffffffffu, valid ? h : 0xFFFFFFFFu);
+                bool keep = valid;
+                if (valid) {
+                    for (unsigned r = same; r; r &= r - 1) {
+                        const int j = __ffs(r) - 1;
+                        const uint64_t y = __shfl_sync(same, x, j);
+                        if (y < x || (y == x && j < lane)) keep = false;
                     }
-                    pos_x = lo - dead_below(lo);
                 }
-                uint32_t pos_o[4];
+                __syncwarp();
+                const uint32_t p = keep ? tbl[h] : 0u;
+                const uint64_t ov = p ? oldsm[p - 1] : 0ull;
+                const bool ins = keep && (p == 0 || ov > x);
+                const bool repl = ins && p != 0;
+                const unsigned insm = __ballot_sync(0xffffffffu, ins);
+                // the next chunk is requested before this one is ranked
+                const uint64_t xn = c0 + 32 + lane < nn_all ? slots[a + c0 + 32 + lane] : ~0ull;
+                if (insm) {
+                    unsigned dead[4];
 #pragma unroll
-                for (int q = 0; q < 4; q++) pos_o[q] = 32u * q + lane - dead_below(32u * q + lane);
-                for (unsigned r = insm; r; r &= r - 1) {
-                    const uint64_t y = __shfl_sync(0xffffffffu, x, __ffs(r) - 1);
-                    pos_x += y < x ? 1u : 0u;
+                    for (int q = 0; q < 4; q++)
+                        dead[q] = __reduce_or_sync(0xffffffffu, (repl && ((p - 1) >> 5) == (uint32_t)q)
+                                                                    ? 1u << ((p - 1) & 31)
+                                                                    : 0u);
+                    // kept slots below index s that were replaced
+                    auto dead_below = [&](uint32_t s) {
+                        uint32_t c = 0;
 #pragma unroll
-                    for (int q = 0; q < 4; q++) pos_o[q] += y < o[q] ? 1u : 0u;
+                        for (int q = 0; q < 4; q++) {
+                            const uint32_t lo = 32u * q;
+                            if (s >= lo + 32) c += __popc(dead[q]);
+                            else if (s > lo) c += __popc(dead[q] & ((1u << (s - lo)) - 1u));
+                        }
+                        return c;
+                    };
+                    uint32_t pos_x = 0;
+                    if (ins) {
+                        uint32_t lo = 0, hi = kc;
+                        while (lo < hi) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if (oldsm[mid] < x) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        pos_x = lo - dead_below(lo);
+                    }
+                    uint32_t pos_o[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) pos_o[q] = 32u * q + lane - dead_below(32u * q + lane);
+                    for (unsigned r = insm; r; r &= r - 1) {
+                        const uint64_t y = __shfl_sync(0xffffffffu, x, __ffs(r) - 1);
+                        pos_x += y < x ? 1u : 0u;
+#pragma unroll
+                        for (int q = 0; q < 4; q++) pos_o[q] += y < o[q] ? 1u : 0u;
+                    }
+                    const uint32_t total =
+                        kc - (__popc(dead[0]) + __popc(dead[1]) + __popc(dead[2]) + __popc(dead[3])) + __popc(insm);
+                    const uint32_t nk = total < l_max ? total : l_max;  // >= kc: a replaced slot's successor enters
+                    __syncwarp();
+                    // the merged order into shared memory, then back into registers and the table
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (32u * q + lane < kc) tbl[(uint32_t)o[q] & hmask] = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint32_t t = 32 * q + lane;
+                        if (t < kc && !((dead[q] >> lane) & 1u) && pos_o[q] < l_max) oldsm[pos_o[q]] = o[q];
+                    }
+                    if (ins && pos_x < l_max) oldsm[pos_x] = x;
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const uint32_t t = 32 * q + lane;
+                        o[q] = t < nk ? oldsm[t] : ~0ull;
+                        if (t < nk) tbl[(uint32_t)o[q] & hmask] = (unsigned char)(t + 1);
+                    }
+                    kc = nk;
+                    changed = true;
+                    __syncwarp();
                 }
-                const uint32_t total = cur - (__popc(dead[0]) + __popc(dead[1]) + __popc(dead[2]) + __popc(dead[3])) +
-                                       __popc(insm);
-                ncur = total < l_max ? total : l_max;
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const uint32_t t = 32 * q + lane;
-                    if (t < cur && !((dead[q] >> lane) & 1u) && pos_o[q] < l_max) res[v * l_max + pos_o[q]] = o[q];
-                }
-                if (ins && pos_x < l_max) res[v * l_max + pos_x] = x;
+                x = xn;
             }
-            if (lane == 0 && ncur != cnt_in) cnt[v] = ncur;
+            if (changed) {
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (32u * q + lane < kc) res[v * l_max + 32 * q + lane] = o[q];
+            }
+            if (lane == 0 && kc != cnt_in) cnt[v] = kc;
             if (!padded)
-                for (uint32_t t = ncur + lane; t < l_max; t += 32) res[v * l_max + t] = ~0ull;
+                for (uint32_t t = kc + lane; t < l_max; t += 32) res[v * l_max + t] = ~0ull;
             __syncwarp();
             // ht is all ones again for the next node's hash set
 #pragma unroll
             for (int q = 0; q < 4; q++)
-                if (32u * q + lane < cur) oldsm[32 * q + lane] = ~0ull;
+                if (32u * q + lane < kc) oldsm[32 * q + lane] = ~0ull;
             __syncwarp();
             continue;
         }

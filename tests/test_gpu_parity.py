@@ -193,8 +193,8 @@ def test_hashprune_grouped_stream_with_self_edges_and_bad_ids():
     assert np.array_equal(host(cnt), cnt_o) and np.array_equal(host(res), res_o)
 
 
-def _small_batches(n, batches, rng):
-    """Batches of 0..40 slots per node (in shuffled order): fresh random pairs, the same pair as an
+def _small_batches(n, batches, rng, most=40):
+    """Batches of 0..most slots per node (in shuffled order): fresh random pairs, the same pair as an
     earlier slot with its distance (an exact duplicate) or with another distance (the same bucket,
     another slot); distances on a coarse grid, so that many tie in their 16-bit form."""
     hist_s = [np.zeros(0, np.uint32) for _ in range(n)]
@@ -203,7 +203,7 @@ def _small_batches(n, batches, rng):
     for _ in range(batches):
         D, Sx, W = [], [], []
         for v in range(n):
-            c = int(rng.integers(0, 41))
+            c = int(rng.integers(0, most + 1))
             if c == 0:
                 continue
             s_ = rng.integers(0, n - 1, size=c).astype(np.uint32)
@@ -228,17 +228,18 @@ def _small_batches(n, batches, rng):
 
 @pytest.mark.parametrize("m", [4, 12, 13])
 @pytest.mark.parametrize("l_max", [16, 96, 200])
-def test_hashprune_small_batches_into_filled_reservoirs(m, l_max):
-    # many batches merged into the same reservoirs: per node up to 32 new slots into up to 128 kept
-    # ones (with at most 12 hash bits) take the bucket-lookup path, the rest the sorting paths;
-    # after every batch the reservoirs equal the oracle's over the whole stream so far
-    rng = np.random.default_rng(100 + m + l_max)
+@pytest.mark.parametrize("most", [40, 140])
+def test_hashprune_small_batches_into_filled_reservoirs(m, l_max, most):
+    # many batches merged into the same reservoirs: per node up to 128 new slots (in chunks of 32)
+    # into up to 128 kept ones (with at most 12 hash bits) take the bucket-lookup path, the rest
+    # the sorting paths; after every batch the reservoirs equal the oracle's over the whole stream
+    rng = np.random.default_rng(100 + m + l_max + most)
     n = 2000
     S = rng.standard_normal((n, m)).astype(np.float32)
     Sd = dev(S)
     res = cnt = None
     seen = []
-    for d, s_, w_ in _small_batches(n, 8, rng):
+    for d, s_, w_ in _small_batches(n, 8 if most < 100 else 4, rng, most):
         seen.append((d, s_, w_))
         res, cnt = pk.pipnn_hashprune(dev(d), dev(s_), dev(w_), Sd, n, l_max, res, cnt)
         res_o, cnt_o = oracle.hashprune_closed(*(np.concatenate(z) for z in zip(*seen)), S, n, l_max)
