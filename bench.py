@@ -4,7 +4,8 @@
 One step = one full build (sketches, partition, leaf all-pairs + pick, HashPrune, final prune) of
 the spacev-like-i8 workload: 100,000,000 points x 128 int8 (10,000-cluster mixture, the largest
 workload that fits one GPU), squared L2, C_max 2048, l_max 64, R 64, multi-level fanout [10, 3],
-k = 2, m = 12 hash bits, alpha 1.2, the leaf and HashPrune steps in memory-bounded waves.  The
+k = 2, m = 12 hash bits, alpha 1.2, the leaf step in memory-bounded waves and HashPrune once per
+group of waves.  The
 input is resident in HBM when a step starts (and far larger than L2); L2 is also flushed (256 MB
 write) before every step, outside the timed events.  Each rank builds its own independently
 seeded instance (independent indexes: no collective on the data path), so the job's throughput is

@@ -117,13 +117,14 @@ typedef struct pipnn_params {
                                seed + r * 0x9E3779B97F4A7C15 (mod 2^64), so replica 0 is the
                                single-replica build.                                          */
     int32_t prec;           /* PIPNN_PREC_*: operand precision of the tensor-core leaf Gram      */
-    uint64_t wave_members;  /* A2..A5 run in waves of consecutive leaves holding at most this many
-                               members (a larger leaf forms a wave of its own); each wave's
-                               candidates are merged into the reservoirs before the next wave's
-                               are formed, which bounds the candidate and staging memory.  By
-                               the history independence of Alg. 3 (Sec. 3) the graph does not
-                               depend on the split.  0: as many members as the free device
-                               memory holds (one wave whenever everything fits).              */
+    uint64_t wave_members;  /* A2..A4 run in waves of consecutive leaves holding at most this many
+                               members (a larger leaf forms a wave of its own), which bounds the
+                               staging memory; A5 merges the candidates of a group of waves
+                               (merge_waves) into the reservoirs before the next group's are
+                               formed, which bounds the candidate memory.  By the history
+                               independence of Alg. 3 (Sec. 3) the graph does not depend on the
+                               split.  0: sized from the free device memory (one wave whenever
+                               everything fits).                                              */
     int32_t pick_direction; /* App. A.3 leaf-pick variant: PIPNN_PICK_BIDIRECTED (Sec. 4.2's
                                choice: both edges of every picked pair), PIPNN_PICK_DIRECTED
                                (only member -> neighbour: the neighbour enters the member's

@@ -379,14 +379,14 @@ int build_impl(const void *points, uint64_t n, uint32_t d, int metric, const pip
             note_peak(&st);
             wave_plan(n, d, dtype, bp, &W, &G);
         }
-        std::vector<uint64_t> wave_lo;  // first leaf of every wave, then num_leaves
-        for (uint64_t b0 = 0; b0 < leaves.num_leaves;) {
+        std::vector<uint64_t> wave_lo;  // first leaf of every wave, then num_leaves (none after an error)
+        for (uint64_t b0 = 0; rc == PIPNN_OK && b0 < leaves.num_leaves;) {
             wave_lo.push_back(b0);
             uint64_t b1 = b0 + 1;
             while (b1 < leaves.num_leaves && hoff[b1 + 1] - hoff[b0] <= W) b1++;
             b0 = b1;
         }
-        wave_lo.push_back(leaves.num_leaves);
+        if (rc == PIPNN_OK) wave_lo.push_back(leaves.num_leaves);
         std::vector<pipnn_edges> group;  // the open group's candidate edges, one entry per wave
         uint64_t group_members = 0;
         auto free_group = [&]() {
