@@ -597,6 +597,10 @@ def main():
                     help="skip the float workload built at every leaf precision")
     ap.add_argument("--queries", type=int, default=None, help="queries of the recall measurement")
     ap.add_argument("--profile", action="store_true", help="timed steps only (for profiler launch lists)")
+    ap.add_argument("--wave-members", type=int, default=0,
+                    help="with --profile: leaf members per wave (0: sized from free memory)")
+    ap.add_argument("--merge-waves", type=int, default=0,
+                    help="with --profile: leaf waves per HashPrune merge (0: sized from free memory)")
     ap.add_argument("--profile-knn", action="store_true",
                     help="with --profile: also one k-NN graph construction on the built graph (byte data)")
     args = ap.parse_args()
@@ -630,7 +634,8 @@ def main():
     prec = prec_names[args.prec] if args.prec else (
         pk.PIPNN_PREC_BF16X3 if (w["dtype"] == synth.F32 and args.engine == "tc") else pk.PIPNN_PREC_FP32)
     dt_code = {synth.F32: pk.PIPNN_F32, synth.U8: pk.PIPNN_U8, synth.I8: pk.PIPNN_I8}[w["dtype"]]
-    bp = pk.params(dtype=dt_code, hyperplanes=Hd, leaf_engine=engine, prec=prec, **workload_params(w))
+    split = dict(wave_members=args.wave_members, merge_waves=args.merge_waves) if args.profile else {}
+    bp = pk.params(dtype=dt_code, hyperplanes=Hd, leaf_engine=engine, prec=prec, **split, **workload_params(w))
     R = w["R"]
     adj = torch.empty((n, R), dtype=torch.int32, device="cuda")
     deg = torch.empty(n, dtype=torch.int32, device="cuda")
