@@ -364,17 +364,16 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
                         dead[q] = __reduce_or_sync(0xffffffffu, (repl && ((p - 1) >> 5) == (uint32_t)q)
                                                                     ? 1u << ((p - 1) & 31)
                                                                     : 0u);
-                    // kept slots below index s that were replaced
+                    // kept slots below index s (0 .. 128) that were replaced
+                    const uint32_t dc0 = __popc(dead[0]), dc1 = dc0 + __popc(dead[1]), dc2 = dc1 + __popc(dead[2]),
+                                   dc3 = dc2 + __popc(dead[3]);
                     auto dead_below = [&](uint32_t s) {
-                        uint32_t c = 0;
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const uint32_t lo = 32u * q;
-                            if (s >= lo + 32) c += __popc(dead[q]);
-                            else if (s > lo) c += __popc(dead[q] & ((1u << (s - lo)) - 1u));
-                        }
-                        return c;
+                        const uint32_t q = s >> 5;
+                        const uint32_t base = q == 0 ? 0u : q == 1 ? dc0 : q == 2 ? dc1 : q == 3 ? dc2 : dc3;
+                        const unsigned w = q == 0 ? dead[0] : q == 1 ? dead[1] : q == 2 ? dead[2] : q == 3 ? dead[3] : 0u;
+                        return base + __popc(w & ((1u << (s & 31)) - 1u));
                     };
+                    const bool wide = kc > 64;  // kept slots in o[2], o[3] too
                     uint32_t pos_x = 0;
                     if (ins) {
                         uint32_t lo = 0, hi = kc;
@@ -391,11 +390,14 @@ __global__ void __launch_bounds__(HP_WARPS * 32, 4) hp_merge(uint64_t n, uint32_
                     for (unsigned r = insm; r; r &= r - 1) {
                         const uint64_t y = __shfl_sync(0xffffffffu, x, __ffs(r) - 1);
                         pos_x += y < x ? 1u : 0u;
-#pragma unroll
-                        for (int q = 0; q < 4; q++) pos_o[q] += y < o[q] ? 1u : 0u;
+                        pos_o[0] += y < o[0] ? 1u : 0u;
+                        pos_o[1] += y < o[1] ? 1u : 0u;
+                        if (wide) {
+                            pos_o[2] += y < o[2] ? 1u : 0u;
+                            pos_o[3] += y < o[3] ? 1u : 0u;
+                        }
                     }
-                    const uint32_t total =
-                        kc - (__popc(dead[0]) + __popc(dead[1]) + __popc(dead[2]) + __popc(dead[3])) + __popc(insm);
+                    const uint32_t total = kc - dc3 + __popc(insm);
                     const uint32_t nk = total < l_max ? total : l_max;  // >= kc: a replaced slot's successor enters
                     __syncwarp();
                     // the merged order into shared memory, then back into registers and the table
