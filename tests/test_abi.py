@@ -71,3 +71,33 @@ def test_batched_build_argument_checks_need_no_gpu():
         pk.pipnn_build_batched([a, np.zeros((10, 9), np.uint8)], bp, [1, 2])    # one dimension
     with pytest.raises(ValueError):
         pk.pipnn_build_batched([a, np.zeros((10, 8), np.int8)], bp, [1, 2])     # one dtype
+
+
+def test_every_struct_matches_the_header_compiled_by_the_c_compiler(tmp_path):
+    """Field offsets and sizes of the header's structs, as a C compiler lays them out, equal the
+    binding's ctypes mirrors."""
+    import shutil
+    import subprocess
+
+    import paper_2602_21247_gb300 as pk
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = [pk.pipnn_params, pk.pipnn_stats, pk.pipnn_leaves, pk.pipnn_edges, pk.pipnn_graph]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pipnn.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'printf("%s size %zu\\n", "{s.__name__}", sizeof({s.__name__}));')
+        for f, _ in s._fields_:
+            lines.append(f'printf("%s %s %zu\\n", "{s.__name__}", "{f}", offsetof({s.__name__}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line}
+    for s in structs:
+        assert got[(s.__name__, "size")] == ctypes.sizeof(s), s.__name__
+        for f, _ in s._fields_:
+            assert got[(s.__name__, f)] == getattr(s, f).offset, (s.__name__, f)
