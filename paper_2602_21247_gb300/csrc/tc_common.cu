@@ -28,9 +28,12 @@ __global__ void stage_rows_kernel(const void *X, uint32_t d, uint32_t kp, const 
     const uint32_t per_row = kp / 8;
     const uint64_t total = M * per_row;
     const uint8_t *Xb = static_cast<const uint8_t *>(X);
+    // chunks per row: a power of two (d <= 128: 8 or 16) splits the index with a shift and a mask
+    const bool pow2 = (per_row & (per_row - 1)) == 0;
+    const uint32_t shift = __ffs(per_row) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t row = i / per_row;
-        const uint32_t c = (uint32_t)(i % per_row);
+        const uint64_t row = pow2 ? i >> shift : i / per_row;
+        const uint32_t c = (uint32_t)(i - row * per_row);
         const uint64_t src = (uint64_t)(ids ? ids[row] : row) * d;
         uint32_t w[4] = {0u, 0u, 0u, 0u};
         if (WIDE) {
